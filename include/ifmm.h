@@ -1,0 +1,145 @@
+/*
+ * ifmm.h -- C ABI of the GB300 inverse fast multipole method (IFMM).
+ *
+ * The library factorizes the dense BEM-type matrix
+ *     A_ij = scale / |x_i - x_j|  (i != j),   A_ii = diag,
+ * through its FMM representation (Eq. (1): the extended sparse system built from
+ * the P2P, P2M, L2P, M2M, M2L, L2L operators of a uniform octree, Sec. 2.1-2.2,
+ * with Chebyshev-interpolation operators), eliminates it level by level from the
+ * leaves (Algorithm 1) with the nodes of a level processed color by color
+ * (Sec. 3, Algorithm 3 coloring at separation sigma), recompresses every far-field
+ * fill-in at relative accuracy eps (Sec. 4.2), and applies the result as a direct
+ * solve (Algorithm 2) or as the preconditioner of GMRES(m) (Algorithms 4 and 5).
+ *
+ * Conventions for every entry point:
+ *   - Status codes only; no exception or abort crosses the ABI.  On error the
+ *     output handle is set to NULL and ifmm_last_error() describes the cause.
+ *   - The caller owns every array it passes.  Handles are owned by the library
+ *     and released with the matching *_free call (NULL is accepted).
+ *   - Vectors are in the caller's point order; the tree's permutation is internal.
+ *   - Pointers documented "host or device" may be either; the library inspects
+ *     them with cudaPointerGetAttributes and copies host data in and out itself.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All device
+ *     work is enqueued on it.  Calls return after the stream has finished their
+ *     work when a result the call returns depends on device values (ranks,
+ *     singular pivots, GMRES convergence, host outputs); otherwise they may
+ *     return early.
+ *   - A handle must not be used from two threads at the same time.
+ *   - There is no CPU fallback: without a CUDA device every compute call
+ *     returns IFMM_ECUDA.
+ */
+#ifndef IFMM_H
+#define IFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IFMM_OK = 0,
+  IFMM_EINVAL = 1,     /* bad argument (NULL, size out of range, inconsistent options) */
+  IFMM_ENOMEM = 2,     /* host or device allocation failed */
+  IFMM_ECUDA = 3,      /* CUDA runtime error, or no CUDA device */
+  IFMM_ESINGULAR = 4,  /* a pivot block was numerically singular */
+  IFMM_ENOCONV = 5,    /* GMRES stopped at maxit above tol (outputs still written) */
+  IFMM_ETIMEOUT = 6,   /* a bounded device wait gave up */
+  IFMM_ERANK = 7       /* a recompression needed more rank than max_rank allows */
+} ifmm_status;
+
+typedef struct ifmm_tree ifmm_tree; /* opaque, library-owned */
+typedef struct ifmm_fact ifmm_fact; /* opaque, library-owned: the factor's block pool */
+
+/* Matrix entries: A_ij = scale/|x_i - x_j| for i != j, A_ii = diag.
+ * The collocation BEM system of the paper's electrostatic example (Sec. 2) with
+ * area weight 4pi/N has scale = 1/N and diag = 0.5 + 1/sqrt(N). */
+typedef struct {
+  double scale;
+  double diag;
+} ifmm_kernel;
+
+enum { IFMM_PREC_FP64 = 0, IFMM_PREC_FP32 = 1, IFMM_PREC_BF16 = 2 };
+enum { IFMM_RANK_SVD = 0, IFMM_RANK_REPLAY = 1, IFMM_RANK_LEARNED = 2 };
+
+typedef struct {
+  int cheb_order;        /* Chebyshev points per axis p (2..6); r = p^3 per cell       */
+  double eps;            /* relative truncation: keep s_j > eps*s_1; 0 = numerical rank */
+  int precision;         /* IFMM_PREC_*: arithmetic of the Schur updates/recompression  */
+  int rank_mode;         /* IFMM_RANK_*                                                 */
+  const int32_t* replay; /* rank_mode REPLAY: host array of (level,node,event,rank)     */
+  int64_t replay_len;    /*   quadruples, replay_len quadruples                         */
+  int max_rank;          /* cap on any node rank (0 = library default, 256)             */
+  const float* mlp;      /* rank_mode LEARNED: host weights, layout of ifmm_mlp_layout  */
+  uint64_t seed;         /* seed of the randomized range finder (LEARNED mode)          */
+} ifmm_opts;
+
+/* Sec. 2.1: uniform octree of the given depth (>= 2, <= 10) over n >= 1 points.
+ * xyz: n x 3 row-major doubles, host memory.  The root is the tight bounding cube
+ * of the points.  The tree keeps a device copy of the points in tree order. */
+ifmm_status ifmm_build_tree(const double* xyz, int64_t n, int depth, ifmm_tree** out);
+
+/* Sec. 3.4, Algorithm 3: greedy coloring at separation sigma (>= 3) of every level
+ * 2..depth.  Replaces any previous coloring of the tree.  ncolors_per_level, if not
+ * NULL, receives depth+1 counts (levels 0 and 1 report 0). */
+ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors_per_level);
+
+/* Integer views of the tree, for inspection and tests.  `what` is one of
+ *   "cells"  (3 per node: ix iy iz)        "parent"  (per node, level >= 1)
+ *   "nbr_ptr" "nbr"   neighbour CSR (Sec. 2.1, excluding the node itself)
+ *   "il_ptr"  "il"    interaction-list CSR (Sec. 2.1)
+ *   "color"           color per node      "group_ptr" "group"  colors as CSR lists
+ *   "perm"            tree order -> caller index (level ignored)
+ *   "leaf_ptr"        point CSR of the leaves (level ignored)
+ * Writes min(count, cap) int32 values to buf (may be NULL) and the full count to
+ * *count. */
+ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int32_t* buf, int64_t cap,
+                            int64_t* count);
+
+/* Algorithm 1 with the coloring of ifmm_color (Sec. 3.2/3.3): initialise the
+ * operators (Sec. 2.2), eliminate levels depth..2 color by color with eps-accurate
+ * recompression of far-field fill-ins, and LU-factor the remaining level-2 system.
+ * Requires ifmm_color first.  The factor keeps its own reference to device data
+ * of the tree: the tree must outlive it. */
+ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opts* o, void* stream,
+                        ifmm_fact** out);
+
+/* Algorithm 2 (+ the dense level-2 solve): v = A~^{-1} r approximately, where A~ is
+ * the FMM representation of A.  r and v: n x nrhs column-major doubles, host or
+ * device (both on the same side).  r and v may alias. */
+ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs, void* stream);
+
+/* Algorithms 4 and 5: GMRES(restart) on A x = b from x = 0 with right
+ * preconditioning by ifmm_solve (precond may be NULL: no preconditioner), the
+ * matrix applied by direct summation on the device.  Stops when the true relative
+ * residual ||b - A x|| / ||b|| <= tol or after maxit matrix-vector products.
+ * b, x: n doubles, host or device (same side).  iters and relres may be NULL. */
+ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact* precond, const double* b,
+                      double* x, int restart, double tol, int maxit, int* iters, double* relres, void* stream);
+
+/* y = A x by direct summation on the device (the matrix of bem_gmres).
+ * x, y: n doubles, host or device (same side); they must not alias. */
+ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
+
+/* Ranks chosen by ifmm_factor, as (level, node, event, rank) quadruples; node is the
+ * tree-order node index at that level and event counts that node's recompressions
+ * at that level (0 = level start).  Same buffer protocol as ifmm_tree_query. */
+ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64_t* count);
+
+/* Factor statistics as named doubles (timings in seconds, algorithmic flop counts,
+ * bytes): writes min(count, cap) values and the full count; ifmm_fact_stat_name
+ * gives the name of entry `index` (NULL when out of range). */
+ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count);
+const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
+
+void ifmm_tree_free(ifmm_tree* t);
+void ifmm_fact_free(ifmm_fact* f);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ifmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFMM_H */

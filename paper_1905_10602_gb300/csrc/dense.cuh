@@ -1,0 +1,404 @@
+// Batched dense linear algebra used by every step of the factorization and
+// the solve: block copies, variable-size GEMM, Gauss-Jordan inversion with
+// partial pivoting, Householder QR (R factor), one-sided Jacobi SVD, GEMV.
+//
+// Every matrix is column-major with a leading dimension (BLAS convention).
+// One descriptor describes one problem; a launch covers a batch of problems of
+// different sizes (the nodes of one color of one level).  Kernels never wait
+// on anything but __syncthreads, and every index is bounded by the sizes in
+// the descriptor.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "descs.h"
+
+namespace ifmm {
+
+__device__ __forceinline__ int find_desc(const int* ptr, int ndesc, int t) {
+  int lo = 0, hi = ndesc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ptr[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- copies
+__global__ void k_copy(const CopyDesc* __restrict__ d, int nd) {
+  const int b = blockIdx.x;
+  if (b >= nd) return;
+  const CopyDesc D = d[b];
+  const long total = (long)D.rows * D.cols;
+  for (long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = (int)(e % D.rows), j = (int)(e / D.rows);
+    double v = 0.0;
+    if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
+    double* o = D.dst + i + (long)j * D.ldd;
+    *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, K in
+// slices of 16 staged through shared memory.  TC is the arithmetic type
+// (double for the FP64 path, float for the reduced-precision modes).
+template <typename TC>
+__global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, const int* __restrict__ tile_ptr, int nd) {
+  const int di = find_desc(tile_ptr, nd, blockIdx.x);
+  const GemmDesc D = d[di];
+  const int local = blockIdx.x - tile_ptr[di];
+  const int tiles_m = (D.m + 63) >> 6;
+  const int tm = local % tiles_m, tn = local / tiles_m;
+  const int row0 = tm * 64, col0 = tn * 64;
+  __shared__ TC As[16][64 + 1];
+  __shared__ TC Bs[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  TC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (TC)0;
+  for (int k0 = 0; k0 < D.k; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      {
+        const int i = e & 63, kk = e >> 6;
+        const int r = row0 + i, c = k0 + kk;
+        double v = 0.0;
+        if (r < D.m && c < D.k) v = D.ta ? D.A[c + (long)r * D.lda] : D.A[r + (long)c * D.lda];
+        As[kk][i] = (TC)v;
+      }
+      {
+        const int kk = e & 15, j = e >> 4;
+        const int r = k0 + kk, c = col0 + j;
+        double v = 0.0;
+        if (r < D.k && c < D.n) v = D.tb ? D.B[c + (long)r * D.ldb] : D.B[r + (long)c * D.ldb];
+        Bs[kk][j] = (TC)v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      TC a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= D.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= D.n) continue;
+      double* o = D.C + r + (long)c * D.ldc;
+      const double v = D.alpha * (double)acc[i][j];
+      *o = (D.beta == 0.0) ? v : v + D.beta * (*o);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum; scratch holds >= 32 doubles; every thread gets the result
+__device__ double block_sum(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += scratch[i];
+  return s;
+}
+
+// ---------------------------------------------------------------- Gauss-Jordan inverse
+// One CTA per matrix, in place in global memory.  Step k: pick the row of
+// largest |A(i,k)|, i >= k (ties: smallest i), swap it into row k, scale row k,
+// eliminate column k from every other row; finally undo the row interchanges
+// as column interchanges in reverse order.  Dynamic shared memory: 2n doubles
+// + n ints.
+__global__ void k_inv(const InvDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const InvDesc D = d[blockIdx.x];
+  const int n = D.n;
+  double* A = D.A;
+  const long ld = D.ld;
+  extern __shared__ double sm[];
+  double* rowk = sm;
+  double* colk = sm + n;
+  int* piv = (int*)(sm + 2 * n);
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(A[i + k * ld]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[w] = best; red_i[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bv = -1.0;
+      int b = n;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < b)) { bv = red_v[i]; b = red_i[i]; }
+      if (!(bv > 0.0) || b >= n) { s_bad = k + 1; b = k; }
+      s_p = b;
+      piv[k] = b;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p;
+    if (p != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t = A[k + j * ld];
+        A[k + j * ld] = A[p + j * ld];
+        A[p + j * ld] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[k + k * ld];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = (j == k) ? inv : A[k + j * ld] * inv;
+      rowk[j] = v;
+      A[k + j * ld] = v;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i + k * ld];
+    __syncthreads();
+    const long total = (long)n * n;
+    for (long e = threadIdx.x; e < total; e += blockDim.x) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      if (i == k) continue;
+      const double a = (j == k) ? 0.0 : A[i + j * ld];
+      A[i + j * ld] = a - colk[i] * rowk[j];
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) D.info[0] = s_bad;
+    return;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = A[i + k * ld];
+        A[i + k * ld] = A[i + p * ld];
+        A[i + p * ld] = t;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) D.info[0] = 0;
+}
+
+// ---------------------------------------------------------------- Householder QR
+// One CTA per matrix.  Column k: v = x - alpha e1 with alpha = -sign(x_0)||x||,
+// H = I - 2 v v^T / (v^T v) applied to the trailing columns (one warp per column).
+__global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const QrDesc D = d[blockIdx.x];
+  const int m = D.m, n = D.n;
+  const long ld = D.ld;
+  double* A = D.A;
+  __shared__ double scratch[32];
+  __shared__ double s_alpha, s_beta;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int kmax = m < n ? m : n;
+  for (int k = 0; k < kmax; ++k) {
+    double* x = A + k + k * ld;
+    const int len = m - k;
+    double ss = 0.0;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) ss += x[i] * x[i];
+    ss = block_sum(ss, scratch);
+    if (threadIdx.x == 0) {
+      const double x0 = x[0];
+      const double nrm = sqrt(x0 * x0 + ss);
+      if (nrm == 0.0) {
+        s_alpha = 0.0;
+        s_beta = 0.0;
+      } else {
+        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double vtv = v0 * v0 + ss;
+        s_alpha = alpha;
+        s_beta = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+        x[0] = v0;
+      }
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    if (beta != 0.0) {
+      for (int j = k + 1 + w; j < n; j += nw) {
+        double* y = A + k + (long)j * ld;
+        double dot = 0.0;
+        for (int i = lane; i < len; i += 32) dot += x[i] * y[i];
+        dot = warp_sum(dot) * beta;
+        for (int i = lane; i < len; i += 32) y[i] -= dot * x[i];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) x[0] = s_alpha;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+  }
+  // rows below min(m, n) in columns >= m are already part of R's rectangle; zero
+  // anything left strictly below the diagonal (columns beyond kmax are untouched)
+}
+
+// ---------------------------------------------------------------- one-sided Jacobi SVD
+// Hestenes' method: rotate column pairs of G until all pairs are orthogonal to
+// working precision, accumulating the rotations in V.  Pairs are taken in the
+// round-robin order (n' = n rounded up to even; in round r, position p > 0 holds
+// column 1 + ((p - 1 - r) mod (n'-1)); pair i joins positions i and n'-1-i), so
+// the n'/2 pairs of a round are disjoint and handled by different warps.
+// Dynamic shared memory: n doubles (column norms) + n ints (order).
+__global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
+  if ((int)blockIdx.x >= nd) return;
+  const SvdDesc D = d[blockIdx.x];
+  const int m = D.m, n = D.n;
+  const long ldg = D.ldg;
+  double* G = D.G;
+  double* W = D.Vw;
+  extern __shared__ double sm[];
+  double* nrm = sm;
+  int* ord = (int*)(sm + n);
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) W[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+  const int np = n + (n & 1);
+  int sweep = 0;
+  const double tol = 1e-15;
+  __syncthreads();
+  for (; sweep < max_sweeps && n > 1; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int pi = w; pi < np / 2; pi += nw) {
+        const int pa = pi, pb = np - 1 - pi;
+        int a = (pa == 0) ? 0 : 1 + ((pa - 1 - r) % (np - 1) + (np - 1)) % (np - 1);
+        int b = (pb == 0) ? 0 : 1 + ((pb - 1 - r) % (np - 1) + (np - 1)) % (np - 1);
+        if (a >= n || b >= n) continue;
+        if (a > b) { const int t = a; a = b; b = t; }
+        double* ga = G + (long)a * ldg;
+        double* gb = G + (long)b * ldg;
+        double al = 0.0, be = 0.0, ga_b = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          const double u = ga[i], v = gb[i];
+          al += u * u;
+          be += v * v;
+          ga_b += u * v;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga_b = warp_sum(ga_b);
+        if (al < 1e-300 || be < 1e-300) continue;
+        if (fabs(ga_b) <= tol * sqrt(al) * sqrt(be)) continue;
+        const double zeta = (be - al) / (2.0 * ga_b);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int i = lane; i < m; i += 32) {
+          const double u = ga[i], v = gb[i];
+          ga[i] = c * u - s * v;
+          gb[i] = s * u + c * v;
+        }
+        double* wa = W + (long)a * n;
+        double* wb = W + (long)b * n;
+        for (int i = lane; i < n; i += 32) {
+          const double u = wa[i], v = wb[i];
+          wa[i] = c * u - s * v;
+          wb[i] = s * u + c * v;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    if (!s_rot) break;
+  }
+  // column norms = singular values; order descending (ties: lower index first)
+  for (int j = w; j < n; j += nw) {
+    const double* g = G + (long)j * ldg;
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += g[i] * g[i];
+    s = warp_sum(s);
+    if (lane == 0) nrm[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int rank = 0;
+    const double v = nrm[j];
+    for (int k = 0; k < n; ++k) rank += (nrm[k] > v) || (nrm[k] == v && k < j);
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = nrm[ord[j]];
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    D.V[i + (long)j * D.ldv] = W[i + (long)ord[j] * n];
+  }
+  if (threadIdx.x == 0 && D.sweeps) D.sweeps[0] = sweep;
+}
+
+// ---------------------------------------------------------------- GEMV
+// y = alpha * op(A) x + beta * y.  Non-transposed: a thread per row walks the
+// columns (consecutive threads read consecutive rows of a column).  Transposed:
+// a warp per output reduces one contiguous column of A.
+__global__ void k_gemv(const GemvDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const GemvDesc D = d[blockIdx.x];
+  if (D.trans) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int i = w; i < D.n; i += nw) {
+      const double* a = D.A + (long)i * D.lda;
+      double s = 0.0;
+      for (int j = lane; j < D.m; j += 32) s += a[j] * D.x[j];
+      s = warp_sum(s);
+      if (lane == 0) D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
+    }
+  } else {
+    for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = 0; j < D.n; ++j) s += D.A[i + (long)j * D.lda] * D.x[j];
+      D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
+    }
+  }
+}
+
+__global__ void k_gemv_sum(const GemvSumDesc* __restrict__ d, const GemvTerm* __restrict__ terms, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const GemvSumDesc D = d[blockIdx.x];
+  for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
+    double s = 0.0;
+    for (int t = D.first; t < D.first + D.count; ++t) {
+      const GemvTerm T = terms[t];
+      for (int j = 0; j < T.n; ++j) s += T.A[i + (long)j * T.lda] * T.x[j];
+    }
+    D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
+  }
+}
+
+}  // namespace ifmm

@@ -1,0 +1,78 @@
+// Launch descriptors of the batched dense kernels (plain structs shared by
+// host and device code).
+#pragma once
+
+namespace ifmm {
+
+// dst = alpha * op(src) + beta * dst ; src == nullptr means op(src) = 0.
+// beta == 0 never reads dst.
+struct CopyDesc {
+  const double* src;
+  double* dst;
+  int lds, ldd, rows, cols;  // rows x cols of dst
+  double alpha, beta;
+  int trans;  // op(src) = src^T (src is cols x rows)
+  int pad;
+};
+
+// C = alpha * op(A) * op(B) + beta * C, C is m x n, inner dimension k.
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  int lda, ldb, ldc, m, n, k;
+  int ta, tb;
+  double alpha, beta;
+};
+
+// In-place inverse of the n x n matrix A; info[0] = 0 on success, k+1 if the
+// k-th pivot was zero.
+struct InvDesc {
+  double* A;
+  int ld, n;
+  int* info;
+  int pad;
+};
+
+// Householder QR of the m x n matrix A in place; on exit the upper triangle of
+// the leading min(m,n) x n block holds R and everything below it is zero.
+struct QrDesc {
+  double* A;
+  int ld, m, n;
+};
+
+// One-sided Jacobi SVD of the m x n matrix G (destroyed): V (n x n, ldv) gets
+// the right singular vectors ordered by descending singular value, sig (n) the
+// singular values; Vw is an n x n work matrix (ld n).
+struct SvdDesc {
+  double* G;
+  double* V;
+  double* Vw;
+  double* sig;
+  int ldg, ldv, m, n;
+  int* sweeps;
+  int pad;
+};
+
+// y = alpha * op(A) x + beta * y ; A is m x n (op(A) is n x m when trans).
+struct GemvDesc {
+  const double* A;
+  const double* x;
+  double* y;
+  int lda, m, n, trans;
+  double alpha, beta;
+};
+
+// y = alpha * sum_t A_t x_t + beta * y over the terms [first, first+count) of a
+// term list.
+struct GemvTerm {
+  const double* A;
+  const double* x;
+  int lda, n;
+};
+struct GemvSumDesc {
+  double* y;
+  int m, first, count, pad;
+  double alpha, beta;
+};
+}  // namespace ifmm

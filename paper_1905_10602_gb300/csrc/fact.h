@@ -1,0 +1,87 @@
+// The factor handle: device block pool plus the host-side plan of the solve.
+#pragma once
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "runtime.h"
+
+namespace ifmm {
+
+// What the solve needs of one eliminated node (Algorithm 2 on the extended system).
+struct NodeFactor {
+  const double* piinv = nullptr;  // (n + r) x (n + r), ld n + r
+  int n = 0, r = 0;
+  std::vector<int> nb;         // neighbours at elimination time
+  std::vector<char> was_elim;  // neighbour eliminated earlier (its variable is y, not x)
+  std::vector<const double*> lcol;  // row-var(q) x x_i   (rows m_q, ld lcol_ld)
+  std::vector<int> lcol_ld, lcol_rows;
+  std::vector<const double*> urow;  // E_x,i x col-var(q) (cols m_q, ld n)
+  std::vector<int> urow_cols;
+};
+
+struct LevelFactor {
+  int kappa = 0, nn = 0;
+  std::vector<int> n, r;                // x dimension, final rank
+  std::vector<std::vector<int>> order;  // colors in elimination order
+  std::vector<NodeFactor> nf;
+};
+
+struct SolveLaunch {
+  int kind;  // 0 copy, 1 gemv, 2 gemv_sum
+  const void* desc;
+  const void* terms;
+  int count;
+};
+
+struct SolvePlan {
+  double* X = nullptr;  // all node vectors of all levels + the top
+  int64_t xlen = 0;
+  double* tvec = nullptr;
+  double* stage_in = nullptr;   // tree-ordered input/output vector (alias of level ell's segment)
+  std::vector<SolveLaunch> prog;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_def = nullptr;
+  DeviceArena mem;
+};
+
+}  // namespace ifmm
+
+struct ifmm_fact {
+  const ifmm_tree* t = nullptr;
+  ifmm_kernel k{};
+  ifmm_opts o{};
+  int p = 0, rc = 0;
+  std::vector<ifmm::LevelFactor> lv;
+  ifmm::DeviceArena persist;
+  double* top_inv = nullptr;
+  int ntop = 0;
+  std::vector<int> top_off;
+  ifmm::SolvePlan plan;
+  std::vector<std::array<int, 4>> rank_log;
+  std::vector<std::pair<std::string, double>> stats;
+  void stat(const std::string& name, double v) {
+    for (auto& s : stats)
+      if (s.first == name) {
+        s.second = v;
+        return;
+      }
+    stats.push_back({name, v});
+  }
+  void stat_add(const std::string& name, double v) {
+    for (auto& s : stats)
+      if (s.first == name) {
+        s.second += v;
+        return;
+      }
+    stats.push_back({name, v});
+  }
+  ~ifmm_fact();
+};
+
+namespace ifmm {
+void build_solve_plan(ifmm_fact& F, cudaStream_t s);
+void run_solve(const ifmm_fact& F, cudaStream_t s);
+}  // namespace ifmm

@@ -1,0 +1,942 @@
+// IFMM factorization (Algorithm 1 with the colors of Algorithm 3).
+//
+// The host walks the symbolic structure (which blocks exist, their shapes, who
+// is eliminated) and emits, per color, batches of descriptors for the dense
+// device kernels; every arithmetic step runs on the GPU.  Per color:
+//   phase A  for every node i of the color (independent for sigma >= 3):
+//            Pi_i = [[P2P_ii, L2P_i], [P2M_i, 0]] -> Pi_i^{-1} (Gauss-Jordan),
+//            Schur complement of the clique: F = -L Pi^{-1} U over the
+//            neighbours' current rows/columns, added in place to near blocks;
+//            far fill-ins (pairs of N_i in each other's interaction list) kept;
+//            then every live neighbour that received far fill-ins gets new
+//            orthonormal bases from weighted SVDs (recompression at eps).
+//   (sync)   singular values come back to the host, which picks the ranks.
+//   phase B  M2L / M2M / L2L blocks touching a re-based node are re-expressed,
+//            M <- T'_a M T_b: the interaction-list updates that the paper
+//            serializes for sigma = 3 (Sec. 3.3) become one deterministic pass.
+//   phase C  fill-in coefficients in the new bases are added to M2L.
+// Block state between two nodes at distance <= 1 lives in three "stage"
+// buffers (both live / one eliminated / both eliminated), so the blocks the
+// solve needs stay untouched once a stage ends.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <unordered_map>
+
+#include "fact.h"
+#include "ifmm_kernels.h"
+
+namespace ifmm {
+
+// logical block op(src): rows x cols
+struct Blk {
+  const double* p;
+  int ld, rows, cols, trans;
+};
+
+static inline int64_t key3(int a, int b, int c) { return ((int64_t)a << 40) | ((int64_t)b << 20) | (int64_t)c; }
+
+struct Work {
+  int kappa = 0, nn = 0;
+  const LevelLists* LL = nullptr;
+  std::vector<int> n, r, capr;
+  std::vector<int> elim;
+  std::vector<int> slot_ptr;
+  std::vector<double*> nb[3];
+  std::vector<double*> far;  // indexed by position in the IL CSR
+  std::vector<double*> P2M, L2P, M2M, L2L;
+  std::vector<int> choff;  // offset of this node's y inside its parent's x
+  int slot(int p, int q) const {
+    if (p == q) return slot_ptr[p];
+    const int* b = LL->nbr.data() + LL->nbr_ptr[p];
+    const int* e = LL->nbr.data() + LL->nbr_ptr[p + 1];
+    const int* it = std::lower_bound(b, e, q);
+    if (it == e || *it != q) return -1;
+    return slot_ptr[p] + 1 + (int)(it - b);
+  }
+  int farix(int a, int b) const {
+    const int* s = LL->il.data() + LL->il_ptr[a];
+    const int* e = LL->il.data() + LL->il_ptr[a + 1];
+    const int* it = std::lower_bound(s, e, b);
+    if (it == e || *it != b) return -1;
+    return (int)(it - LL->il.data());
+  }
+  bool is_near(int p, int q) const { return p == q || slot(p, q) >= 0; }
+  int dim(int q) const { return elim[q] ? r[q] : n[q]; }  // current variable of q: x_q or y_q
+};
+
+struct Counter {
+  double gemm = 0, inv = 0, qr = 0, svd = 0, lu = 0;
+  void add_gemm(const std::vector<GemmDesc>& v) {
+    for (auto& d : v) gemm += 2.0 * d.m * d.n * d.k;
+  }
+  double total() const { return gemm + inv + qr + svd + lu; }
+};
+
+// One recompression event (reading R4 of the oracle, Sec. 4.2): new orthonormal
+// row basis (P2M) and column basis (L2P) of a live node from the SVDs of the
+// weighted old basis stacked with the far fill-ins.
+struct Event {
+  int q = 0;
+  int r_old = 0, n = 0;
+  std::vector<Blk> z[2];   // weighting blocks, logical rows x r_old
+  Blk b[2];                // old basis as r_old x n (side 1: L2P^T)
+  std::vector<Blk> f[2];   // fill rows, logical rows x n
+  int nominal_rows[2] = {0, 0};
+  double* V[2] = {nullptr, nullptr};
+  double* sig[2] = {nullptr, nullptr};
+  int avail[2] = {0, 0};
+  int k = 0;
+  double* T = nullptr;   // r_old x k
+  double* Tp = nullptr;  // k x r_old
+  int64_t key = 0;
+  int event_no = 0;
+};
+
+struct Factorizer {
+  ifmm_fact& F;
+  const ifmm_tree& T;
+  cudaStream_t s;
+  DescStage st;
+  DeviceArena scratch;
+  DeviceArena levelmem;
+  int p, rc, maxrank;
+  double* m2m_tab = nullptr;
+  double* m2l_tab = nullptr;
+  std::unordered_map<int64_t, int> replay;
+  std::vector<int> event_count;
+  Counter cnt;
+  int* d_info = nullptr;
+  int info_cap = 0;
+  std::vector<double*> pinned_sig;
+  double rank_capped = 0;
+
+  Factorizer(ifmm_fact& f, cudaStream_t stream) : F(f), T(*f.t), s(stream) {
+    st.stream = s;
+    p = F.p;
+    rc = F.rc;
+    maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256;
+    if (F.o.rank_mode == IFMM_RANK_REPLAY) {
+      IFMM_REQUIRE(F.o.replay != nullptr || F.o.replay_len == 0, IFMM_EINVAL, "replay table is NULL");
+      for (int64_t e = 0; e < F.o.replay_len; ++e) {
+        const int32_t* qd = F.o.replay + 4 * e;
+        replay[key3(qd[0], qd[1], qd[2])] = qd[3];
+      }
+    }
+  }
+
+  void sync() {
+    CK(cudaStreamSynchronize(s));
+    st.reset();
+  }
+
+  // ------------------------------------------------------------------ ranks
+  static int kept(const std::vector<double>& sig, int avail, int rows, int cols, double eps) {
+    if (avail <= 0 || sig.empty() || !(sig[0] > 0.0)) return 0;
+    const double thr = eps > 0.0 ? eps * sig[0] : (double)std::max(rows, cols) * std::ldexp(1.0, -52) * sig[0];
+    int k = 0;
+    for (int j = 0; j < avail && j < (int)sig.size(); ++j)
+      if (sig[j] > thr) ++k;
+    return k;
+  }
+
+  // ------------------------------------------------------------------ events
+  // Runs the SVD stage of a batch of events, reads the singular values back,
+  // picks the ranks, and leaves T, T' and the new bases in place.  P2M_out /
+  // L2P_out / their lds give where the new bases go; the old bases are read
+  // from ev.b before they are overwritten.
+  void run_events(std::vector<Event>& evs, Work& W, const std::vector<double*>& P2M_out,
+                  const std::vector<double*>& L2P_out, const std::vector<int>& P2M_ld, const std::vector<int>& L2P_ld,
+                  std::vector<InvDesc>* inv_check, int n_inv) {
+    std::vector<CopyDesc> cz, cf;
+    std::vector<QrDesc> qz, qy;
+    std::vector<GemmDesc> gw;
+    std::vector<SvdDesc> sv;
+    for (auto& ev : evs) {
+      const int n = ev.n, r0 = ev.r_old;
+      for (int side = 0; side < 2; ++side) {
+        int mz = 0;
+        for (auto& z : ev.z[side]) mz += z.rows;
+        int mf = 0;
+        for (auto& f : ev.f[side]) mf += f.rows;
+        ev.nominal_rows[side] = r0 + mf;
+        ev.avail[side] = std::min(r0 + mf, n);
+        ev.V[side] = nullptr;
+        ev.sig[side] = nullptr;
+        if (n == 0) continue;
+        const bool pathA = (n <= r0);
+        const int mw = (mz == 0 || r0 == 0) ? 0 : (pathA ? mz : std::min(mz, r0));
+        const int my = mw + mf;
+        if (my == 0) {
+          ev.avail[side] = 0;
+          continue;
+        }
+        double* Z = nullptr;
+        if (mw > 0) {
+          Z = scratch.alloc((size_t)mz * r0);
+          int off = 0;
+          for (auto& z : ev.z[side]) {
+            cz.push_back(cpy(z.p, z.ld, Z + off, mz, z.rows, z.cols, 1.0, 0.0, z.trans));
+            off += z.rows;
+          }
+          if (!pathA) {
+            qz.push_back(QrDesc{Z, mz, mz, r0});
+            cnt.qr += 2.0 * mz * r0 * (double)r0 - 2.0 * std::pow((double)std::min(mz, r0), 3) / 3.0;
+          }
+        }
+        double* Y = scratch.alloc((size_t)my * n);
+        if (mw > 0) {
+          const Blk& B = ev.b[side];
+          // W = Z * B (path A) or R_Z * B (path B); B logical r0 x n
+          gw.push_back(gmm(Z, mz, 0, B.p, B.ld, B.trans, Y, my, mw, n, r0, 1.0, 0.0));
+        }
+        int off = mw;
+        for (auto& f : ev.f[side]) {
+          cf.push_back(cpy(f.p, f.ld, Y + off, my, f.rows, f.cols, 1.0, 0.0, f.trans));
+          off += f.rows;
+        }
+        int msvd = my;
+        if (my > n) {
+          qy.push_back(QrDesc{Y, my, my, n});
+          cnt.qr += 2.0 * my * n * (double)n - 2.0 * std::pow((double)n, 3) / 3.0;
+          msvd = n;
+        }
+        ev.V[side] = scratch.alloc((size_t)n * n);
+        ev.sig[side] = scratch.alloc(n);
+        double* Vw = scratch.alloc((size_t)n * n);
+        SvdDesc d;
+        d.G = Y;
+        d.V = ev.V[side];
+        d.Vw = Vw;
+        d.sig = ev.sig[side];
+        d.ldg = my;
+        d.ldv = n;
+        d.m = msvd;
+        d.n = n;
+        d.sweeps = nullptr;
+        d.pad = 0;
+        sv.push_back(d);
+        cnt.svd += 6.0 * std::max(ev.nominal_rows[side], n) * std::pow((double)std::min(ev.nominal_rows[side], n), 2) +
+                   20.0 * std::pow((double)std::min(ev.nominal_rows[side], n), 3);
+      }
+    }
+    launch_copy(st, cz);
+    launch_qr(st, qz);
+    cnt.add_gemm(gw);
+    launch_gemm(st, gw, P64);
+    launch_copy(st, cf);
+    launch_qr(st, qy);
+    launch_svd(st, sv);
+    // read back singular values (and pivot status)
+    size_t total = 0;
+    for (auto& ev : evs)
+      for (int side = 0; side < 2; ++side)
+        if (ev.sig[side]) total += ev.n;
+    std::vector<double> hsig(total);
+    double* hp = nullptr;
+    if (total) {
+      hp = (double*)st.host_alloc(total * sizeof(double));
+      size_t o = 0;
+      for (auto& ev : evs)
+        for (int side = 0; side < 2; ++side)
+          if (ev.sig[side]) {
+            CK(cudaMemcpyAsync(hp + o, ev.sig[side], sizeof(double) * ev.n, cudaMemcpyDeviceToHost, s));
+            o += ev.n;
+          }
+    }
+    std::vector<int> hinfo(n_inv, 0);
+    int* hi = nullptr;
+    if (n_inv) {
+      hi = (int*)st.host_alloc(sizeof(int) * n_inv);
+      CK(cudaMemcpyAsync(hi, d_info, sizeof(int) * n_inv, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (total) memcpy(hsig.data(), hp, total * sizeof(double));
+    if (n_inv) memcpy(hinfo.data(), hi, sizeof(int) * n_inv);
+    st.reset();
+    for (int i = 0; i < n_inv; ++i)
+      IFMM_REQUIRE(hinfo[i] == 0, IFMM_ESINGULAR, "singular pivot block at level " + std::to_string(W.kappa));
+    (void)inv_check;
+    // choose ranks (max of the row and column counts, both sides share it)
+    size_t o = 0;
+    for (auto& ev : evs) {
+      std::vector<double> sg[2];
+      for (int side = 0; side < 2; ++side)
+        if (ev.sig[side]) {
+          sg[side].assign(hsig.begin() + o, hsig.begin() + o + ev.n);
+          o += ev.n;
+        }
+      const int kr = kept(sg[0], ev.avail[0], ev.nominal_rows[0], ev.n, F.o.eps);
+      const int kc = kept(sg[1], ev.avail[1], ev.nominal_rows[1], ev.n, F.o.eps);
+      int k = std::min(std::max(kr, kc), std::min(ev.avail[0], ev.avail[1]));
+      if (F.o.rank_mode == IFMM_RANK_REPLAY) {
+        auto it = replay.find(ev.key);
+        IFMM_REQUIRE(it != replay.end(), IFMM_EINVAL, "replay table misses an event");
+        k = it->second;
+        IFMM_REQUIRE(k >= 0 && k <= std::min(ev.avail[0], ev.avail[1]), IFMM_EINVAL, "replayed rank out of range");
+      }
+      if (k > W.capr[ev.q]) {
+        rank_capped += 1;
+        k = W.capr[ev.q];
+      }
+      ev.k = k;
+      F.rank_log.push_back({W.kappa, ev.q, ev.event_no, k});
+    }
+    // T = P2M_old V_row[:, :k], T' = V_col[:, :k]^T L2P_old, then the new bases
+    std::vector<GemmDesc> gt;
+    std::vector<CopyDesc> cb;
+    for (size_t e = 0; e < evs.size(); ++e) {
+      Event& ev = evs[e];
+      const int k = ev.k, n = ev.n, r0 = ev.r_old;
+      ev.T = scratch.alloc((size_t)std::max(1, r0 * k));
+      ev.Tp = scratch.alloc((size_t)std::max(1, r0 * k));
+      if (k == 0) continue;
+      // side 0: B = P2M_old (r0 x n); side 1: B = L2P_old^T
+      if (r0 > 0) {
+        gt.push_back(gmm(ev.b[0].p, ev.b[0].ld, ev.b[0].trans, ev.V[0], n, 0, ev.T, r0, r0, k, n, 1.0, 0.0));
+        // T' = V_col[:, :k]^T * L2P_old  (L2P_old = (b[1])^T)
+        gt.push_back(gmm(ev.V[1], n, 1, ev.b[1].p, ev.b[1].ld, ev.b[1].trans ? 0 : 1, ev.Tp, k, k, r0, n, 1.0, 0.0));
+      }
+      cb.push_back(cpy(ev.V[0], n, P2M_out[e], P2M_ld[e], k, n, 1.0, 0.0, 1));
+      cb.push_back(cpy(ev.V[1], n, L2P_out[e], L2P_ld[e], n, k, 1.0, 0.0, 0));
+    }
+    cnt.add_gemm(gt);
+    launch_gemm(st, gt, P64);
+    launch_copy(st, cb);
+  }
+
+  Event make_event(Work& W, int q) {
+    Event ev;
+    ev.q = q;
+    ev.event_no = event_count[q]++;
+    ev.key = key3(W.kappa, q, ev.event_no);
+    return ev;
+  }
+
+  // ------------------------------------------------------------------ level start
+  void init_level(Work& W, int kappa, Work* child) {
+    const LevelLists& LL = T.lv[kappa];
+    W.kappa = kappa;
+    W.LL = &LL;
+    W.nn = LL.n;
+    const int nn = LL.n;
+    W.n.assign(nn, 0);
+    if (!child) {
+      for (int i = 0; i < nn; ++i) W.n[i] = T.leaf_ptr[i + 1] - T.leaf_ptr[i];
+    } else {
+      child->choff.assign(child->nn, 0);
+      for (int a = 0; a < nn; ++a) {
+        int off = 0;
+        for (int c = LL.child_ptr[a]; c < LL.child_ptr[a + 1]; ++c) {
+          const int ch = LL.child[c];
+          child->choff[ch] = off;
+          off += child->r[ch];
+        }
+        W.n[a] = off;
+      }
+    }
+    W.capr.resize(nn);
+    for (int i = 0; i < nn; ++i) W.capr[i] = std::min(W.n[i], maxrank);
+    W.r.assign(nn, 0);
+    W.elim.assign(nn, 0);
+    event_count.assign(nn, 0);
+    // near slots
+    W.slot_ptr.assign(nn + 1, 0);
+    for (int i = 0; i < nn; ++i) W.slot_ptr[i + 1] = W.slot_ptr[i] + 1 + (LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]);
+    const int nslots = W.slot_ptr[nn];
+    for (int s3 = 0; s3 < 3; ++s3) W.nb[s3].assign(nslots, nullptr);
+    for (int i = 0; i < nn; ++i) {
+      for (int k = 0; k <= LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]; ++k) {
+        const int q = k == 0 ? i : LL.nbr[LL.nbr_ptr[i] + k - 1];
+        const size_t sz = (size_t)std::max(1, W.n[i]) * std::max(1, W.n[q]);
+        const int sl = W.slot_ptr[i] + k;
+        W.nb[0][sl] = F.persist.alloc(sz);
+        if (k > 0) W.nb[1][sl] = F.persist.alloc(sz);
+        W.nb[2][sl] = levelmem.alloc(sz);
+      }
+    }
+    W.far.assign(LL.il.size(), nullptr);
+    for (int a = 0; a < nn; ++a)
+      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e)
+        W.far[e] = levelmem.alloc((size_t)std::max(1, W.capr[a]) * std::max(1, W.capr[LL.il[e]]));
+    W.P2M.assign(nn, nullptr);
+    W.L2P.assign(nn, nullptr);
+    W.M2M.assign(nn, nullptr);
+    W.L2L.assign(nn, nullptr);
+    for (int i = 0; i < nn; ++i) {
+      W.P2M[i] = levelmem.alloc((size_t)std::max(1, W.capr[i]) * std::max(1, W.n[i]));
+      W.L2P[i] = levelmem.alloc((size_t)std::max(1, W.capr[i]) * std::max(1, W.n[i]));
+      if (kappa > 2) {
+        W.M2M[i] = levelmem.alloc((size_t)rc * std::max(1, W.capr[i]));
+        W.L2L[i] = levelmem.alloc((size_t)rc * std::max(1, W.capr[i]));
+      }
+    }
+    // stage-0 near blocks and the initial bases (r_cheb columns / rows)
+    scratch.reset();
+    std::vector<double*> P2M0(nn), L2P0(nn);
+    for (int i = 0; i < nn; ++i) {
+      P2M0[i] = scratch.alloc((size_t)rc * std::max(1, W.n[i]));
+      L2P0[i] = scratch.alloc((size_t)rc * std::max(1, W.n[i]));
+    }
+    if (!child) {
+      std::vector<P2pDesc> pp;
+      std::vector<InterpDesc> ip;
+      std::vector<CopyDesc> ct;
+      const double h = 0.5 * T.side / (double)((int64_t)1 << kappa);
+      for (int i = 0; i < nn; ++i) {
+        for (int k = 0; k <= LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]; ++k) {
+          const int q = k == 0 ? i : LL.nbr[LL.nbr_ptr[i] + k - 1];
+          P2pDesc d;
+          d.dst = W.nb[0][W.slot_ptr[i] + k];
+          d.i0 = T.leaf_ptr[i];
+          d.ni = W.n[i];
+          d.j0 = T.leaf_ptr[q];
+          d.nj = W.n[q];
+          d.ld = W.n[i];
+          d.same = (q == i);
+          pp.push_back(d);
+        }
+        InterpDesc id;
+        id.dst = P2M0[i];
+        id.cx = T.origin[0] + (LL.cells[3 * i] + 0.5) * 2 * h;
+        id.cy = T.origin[1] + (LL.cells[3 * i + 1] + 0.5) * 2 * h;
+        id.cz = T.origin[2] + (LL.cells[3 * i + 2] + 0.5) * 2 * h;
+        id.h = h;
+        id.p0 = T.leaf_ptr[i];
+        id.n = W.n[i];
+        id.ld = rc;
+        id.pad = 0;
+        ip.push_back(id);
+        ct.push_back(cpy(P2M0[i], rc, L2P0[i], W.n[i], W.n[i], rc, 1.0, 0.0, 1));
+      }
+      launch_p2p(st, pp, T.d_pts, (int)T.N, F.k.scale, F.k.diag);
+      launch_interp(st, ip, T.d_pts, (int)T.N, p);
+      launch_copy(st, ct);
+    } else {
+      std::vector<CopyDesc> cc;
+      const LevelLists& CL = *child->LL;
+      for (int a = 0; a < nn; ++a) {
+        for (int k = 0; k <= LL.nbr_ptr[a + 1] - LL.nbr_ptr[a]; ++k) {
+          const int b = k == 0 ? a : LL.nbr[LL.nbr_ptr[a] + k - 1];
+          double* dst = W.nb[0][W.slot_ptr[a] + k];
+          for (int x = LL.child_ptr[a]; x < LL.child_ptr[a + 1]; ++x) {
+            const int c = LL.child[x];
+            for (int y = LL.child_ptr[b]; y < LL.child_ptr[b + 1]; ++y) {
+              const int d = LL.child[y];
+              const int sl = child->slot(c, d);
+              const double* src;
+              int ld;
+              if (sl >= 0) {
+                src = child->nb[2][sl];
+                ld = child->n[c];
+              } else {
+                const int fx = child->farix(c, d);
+                IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: child pair neither near nor far");
+                src = child->far[fx];
+                ld = child->capr[c];
+              }
+              if (child->r[c] && child->r[d])
+                cc.push_back(cpy(src, ld, dst + child->choff[c] + (long)child->choff[d] * W.n[a], W.n[a], child->r[c],
+                                 child->r[d]));
+            }
+          }
+        }
+        for (int x = LL.child_ptr[a]; x < LL.child_ptr[a + 1]; ++x) {
+          const int c = LL.child[x];
+          if (!child->r[c]) continue;
+          cc.push_back(cpy(child->M2M[c], rc, P2M0[a] + (long)child->choff[c] * rc, rc, rc, child->r[c]));
+          cc.push_back(cpy(child->L2L[c], child->capr[c], L2P0[a] + child->choff[c], W.n[a], child->r[c], rc));
+        }
+      }
+      (void)CL;
+      launch_copy(st, cc);
+    }
+    // M2L translation table of this level
+    const double h = 0.5 * T.side / (double)((int64_t)1 << kappa);
+    m2l_tab = levelmem.alloc((size_t)343 * rc * rc);
+    launch_m2l_table(s, m2l_tab, p, h, F.k.scale);
+    // initial recompression of every node (reading R5)
+    std::vector<Event> evs;
+    std::vector<double*> po, lo;
+    std::vector<int> pld, lld;
+    auto off_index = [&](int a, int b) {
+      const int dx = LL.cells[3 * a] - LL.cells[3 * b], dy = LL.cells[3 * a + 1] - LL.cells[3 * b + 1],
+                dz = LL.cells[3 * a + 2] - LL.cells[3 * b + 2];
+      return (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+    };
+    auto octant = [&](int q) {
+      return (LL.cells[3 * q] & 1) | ((LL.cells[3 * q + 1] & 1) << 1) | ((LL.cells[3 * q + 2] & 1) << 2);
+    };
+    const long rc2 = (long)rc * rc;
+    for (int q = 0; q < nn; ++q) {
+      Event ev = make_event(W, q);
+      ev.r_old = rc;
+      ev.n = W.n[q];
+      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+        const int l = LL.il[e];
+        ev.z[0].push_back(Blk{m2l_tab + off_index(l, q) * rc2, rc, rc, rc, 0});  // K(l,q)
+        ev.z[1].push_back(Blk{m2l_tab + off_index(q, l) * rc2, rc, rc, rc, 1});  // K(q,l)^T
+      }
+      if (kappa > 2) {
+        ev.z[0].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // M2M
+        ev.z[1].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // L2L^T = M2M
+      }
+      ev.b[0] = Blk{P2M0[q], rc, rc, W.n[q], 0};
+      ev.b[1] = Blk{L2P0[q], W.n[q], rc, W.n[q], 1};
+      evs.push_back(ev);
+      po.push_back(W.P2M[q]);
+      lo.push_back(W.L2P[q]);
+      pld.push_back(W.capr[q]);
+      lld.push_back(W.n[q]);
+    }
+    run_events(evs, W, po, lo, pld, lld, nullptr, 0);
+    for (auto& ev : evs) W.r[ev.q] = ev.k;
+    // M2L blocks T'_a K T_b; M2M = M2M_tab T; L2L = T' M2M_tab^T
+    std::vector<GemmDesc> g1, g2;
+    std::vector<double*> tmp(LL.il.size());
+    for (int a = 0; a < nn; ++a)
+      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+        const int b = LL.il[e];
+        const int ka = evs[a].k, kb = evs[b].k;
+        if (!ka || !kb) continue;
+        tmp[e] = scratch.alloc((size_t)ka * rc);
+        g1.push_back(gmm(evs[a].Tp, ka, 0, m2l_tab + off_index(a, b) * rc2, rc, 0, tmp[e], ka, ka, rc, rc, 1.0, 0.0));
+        g2.push_back(gmm(tmp[e], ka, 0, evs[b].T, rc, 0, W.far[e], W.capr[a], ka, kb, rc, 1.0, 0.0));
+      }
+    if (kappa > 2)
+      for (int q = 0; q < nn; ++q) {
+        const int k = evs[q].k;
+        if (!k) continue;
+        g1.push_back(gmm(m2m_tab + octant(q) * rc2, rc, 0, evs[q].T, rc, 0, W.M2M[q], rc, rc, k, rc, 1.0, 0.0));
+        g1.push_back(gmm(evs[q].Tp, k, 0, m2m_tab + octant(q) * rc2, rc, 1, W.L2L[q], W.capr[q], k, rc, rc, 1.0, 0.0));
+      }
+    cnt.add_gemm(g1);
+    cnt.add_gemm(g2);
+    launch_gemm(st, g1, P64);
+    launch_gemm(st, g2, P64);
+  }
+
+  // ------------------------------------------------------------------ one color
+  void eliminate_color(Work& W, const std::vector<int>& grp, LevelFactor& LF) {
+    const LevelLists& LL = *W.LL;
+    scratch.reset();
+    const int ng = (int)grp.size();
+    if (info_cap < ng) {
+      if (d_info) cudaFree(d_info);
+      CK(cudaMalloc(&d_info, sizeof(int) * std::max(ng, 64)));
+      info_cap = std::max(ng, 64);
+    }
+    // ---- pivots
+    std::vector<CopyDesc> cpi;
+    std::vector<InvDesc> inv;
+    std::vector<double*> Pi(ng);
+    for (int g = 0; g < ng; ++g) {
+      const int i = grp[g];
+      const int ni = W.n[i], ri = W.r[i], m = ni + ri;
+      Pi[g] = F.persist.alloc((size_t)std::max(1, m * m));
+      if (m == 0) continue;
+      cpi.push_back(cpy(W.nb[0][W.slot(i, i)], ni, Pi[g], m, ni, ni));
+      if (ri) {
+        cpi.push_back(cpy(W.L2P[i], ni, Pi[g] + (long)ni * m, m, ni, ri));
+        cpi.push_back(cpy(W.P2M[i], W.capr[i], Pi[g] + ni, m, ri, ni));
+        cpi.push_back(cpy(nullptr, 0, Pi[g] + ni + (long)ni * m, m, ri, ri));
+      }
+      inv.push_back(InvDesc{Pi[g], m, m, d_info + g, 0});
+      cnt.inv += 2.0 * std::pow((double)m, 3);
+    }
+    CK(cudaMemsetAsync(d_info, 0, sizeof(int) * ng, s));
+    launch_copy(st, cpi);
+    launch_inv(st, inv);
+    // ---- Schur complements of the cliques
+    std::vector<CopyDesc> cg, sc;
+    std::vector<GemmDesc> gx, gf;
+    struct FarFill {
+      int a, b;
+      const double* Fp;
+      int ld, rows, cols;
+    };
+    std::vector<FarFill> fills;
+    std::map<int, std::vector<Blk>> rowfill, colfill;
+    std::vector<int> rebase_order;
+    for (int g = 0; g < ng; ++g) {
+      const int i = grp[g];
+      const int ni = W.n[i], ri = W.r[i], m = ni + ri;
+      const int q0 = LL.nbr_ptr[i], q1 = LL.nbr_ptr[i + 1];
+      NodeFactor& nf = LF.nf[i];
+      nf.piinv = Pi[g];
+      nf.n = ni;
+      nf.r = ri;
+      std::vector<int> roff, dims;
+      int M = 0;
+      for (int e = q0; e < q1; ++e) {
+        const int q = LL.nbr[e];
+        roff.push_back(M);
+        dims.push_back(W.dim(q));
+        M += W.dim(q);
+        nf.nb.push_back(q);
+        nf.was_elim.push_back(W.elim[q]);
+        const int sq = W.slot(q, i), si = W.slot(i, q);
+        nf.lcol.push_back(W.nb[W.elim[q]][sq]);
+        nf.lcol_ld.push_back(W.n[q]);
+        nf.lcol_rows.push_back(W.dim(q));
+        nf.urow.push_back(W.nb[W.elim[q]][si]);
+        nf.urow_cols.push_back(W.dim(q));
+      }
+      // -A22 -> self block of R_i x y_i
+      if (ri) sc.push_back(cpy(Pi[g] + ni + (long)ni * m, m, W.nb[2][W.slot(i, i)], ni, ri, ri, -1.0, 0.0));
+      if (M == 0 || m == 0) continue;
+      double* L = scratch.alloc((size_t)M * std::max(1, ni));
+      double* U = scratch.alloc((size_t)std::max(1, ni) * M);
+      double* X = scratch.alloc((size_t)M * m);
+      double* Fm = scratch.alloc((size_t)M * M);
+      double* Yr = scratch.alloc((size_t)std::max(1, ri) * M);
+      for (size_t a = 0; a < nf.nb.size(); ++a) {
+        const int q = nf.nb[a];
+        if (ni && dims[a]) {
+          cg.push_back(cpy(nf.lcol[a], W.n[q], L + roff[a], M, dims[a], ni));
+          cg.push_back(cpy(nf.urow[a], ni, U + (long)roff[a] * ni, ni, ni, dims[a]));
+        }
+      }
+      if (ni) {
+        gx.push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));   // X = L [A11 A12]
+        gf.push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));   // F = -X[:, :ni] U
+        if (ri) gf.push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
+      }
+      for (size_t a = 0; a < nf.nb.size(); ++a) {
+        const int q = nf.nb[a];
+        const int mq = dims[a];
+        // row-var(q) x y_i  <- L A12
+        if (mq && ri && ni)
+          sc.push_back(cpy(X + roff[a] + (long)ni * M, M, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
+        else if (mq && ri)
+          sc.push_back(cpy(nullptr, 0, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
+        // R_i x col-var(q)  <- A21 U
+        if (mq && ri && ni)
+          sc.push_back(cpy(Yr + (long)roff[a] * ri, ri, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
+        else if (mq && ri)
+          sc.push_back(cpy(nullptr, 0, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
+        for (size_t b2 = 0; b2 < nf.nb.size(); ++b2) {
+          const int q2 = nf.nb[b2];
+          const int mq2 = dims[b2];
+          if (!mq || !mq2 || !ni) continue;
+          const double* src = Fm + roff[a] + (long)roff[b2] * M;
+          if (q == q2 || W.slot(q, q2) >= 0) {
+            const int stg = W.elim[q] + W.elim[q2];
+            sc.push_back(cpy(src, M, W.nb[stg][W.slot(q, q2)], W.n[q], mq, mq2, 1.0, 1.0));
+          } else {
+            IFMM_REQUIRE(W.farix(q, q2) >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
+            fills.push_back(FarFill{q, q2, src, M, mq, mq2});
+            if (!W.elim[q]) {
+              colfill[q].push_back(Blk{src, M, mq2, W.n[q], 1});
+              if (std::find(rebase_order.begin(), rebase_order.end(), q) == rebase_order.end()) rebase_order.push_back(q);
+            }
+            if (!W.elim[q2]) {
+              rowfill[q2].push_back(Blk{src, M, mq, W.n[q2], 0});
+              if (std::find(rebase_order.begin(), rebase_order.end(), q2) == rebase_order.end())
+                rebase_order.push_back(q2);
+            }
+          }
+        }
+      }
+    }
+    for (int g = 0; g < ng; ++g) W.elim[grp[g]] = 1;
+    launch_copy(st, cg);
+    cnt.add_gemm(gx);
+    cnt.add_gemm(gf);
+    launch_gemm(st, gx, P64);
+    launch_gemm(st, gf, P64);
+    launch_copy(st, sc);
+    // ---- recompression events (snapshots: nothing below reads what phase A changes)
+    std::vector<Event> evs;
+    std::vector<double*> po, lo;
+    std::vector<int> pld, lld;
+    std::vector<int> r_before(W.r);
+    for (int q : rebase_order) {
+      Event ev = make_event(W, q);
+      ev.r_old = W.r[q];
+      ev.n = W.n[q];
+      const int rq = W.r[q];
+      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+        const int l = LL.il[e];
+        const int rl = W.r[l];
+        if (!rl || !rq) continue;
+        const int fl = W.farix(l, q);
+        ev.z[0].push_back(Blk{W.far[fl], W.capr[l], rl, rq, 0});      // M2L_lq
+        ev.z[1].push_back(Blk{W.far[e], W.capr[q], rl, rq, 1});       // M2L_ql^T
+      }
+      if (W.kappa > 2 && rq) {
+        ev.z[0].push_back(Blk{W.M2M[q], rc, rc, rq, 0});
+        ev.z[1].push_back(Blk{W.L2L[q], W.capr[q], rc, rq, 1});
+      }
+      ev.b[0] = Blk{W.P2M[q], W.capr[q], rq, W.n[q], 0};
+      ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
+      ev.f[0] = rowfill[q];
+      ev.f[1] = colfill[q];
+      evs.push_back(ev);
+      po.push_back(W.P2M[q]);
+      lo.push_back(W.L2P[q]);
+      pld.push_back(W.capr[q]);
+      lld.push_back(W.n[q]);
+    }
+    run_events(evs, W, po, lo, pld, lld, nullptr, ng);
+    // ---- phase B: re-express blocks that touch a re-based node
+    std::vector<int> newk(W.nn, -1);
+    std::vector<const Event*> evof(W.nn, nullptr);
+    for (auto& ev : evs) {
+      newk[ev.q] = ev.k;
+      evof[ev.q] = &ev;
+    }
+    std::vector<GemmDesc> b1, b2;
+    std::vector<CopyDesc> bc1, bc2;
+    std::vector<char> touched(LL.il.size(), 0);
+    for (auto& ev : evs) {
+      const int q = ev.q;
+      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+        touched[e] = 1;
+        const int fl = W.farix(LL.il[e], q);
+        touched[fl] = 1;
+      }
+      if (W.kappa > 2 && ev.k && ev.r_old) {
+        double* t1 = scratch.alloc((size_t)rc * ev.k);
+        double* t2 = scratch.alloc((size_t)rc * ev.k);
+        b1.push_back(gmm(W.M2M[q], rc, 0, ev.T, ev.r_old, 0, t1, rc, rc, ev.k, ev.r_old, 1.0, 0.0));
+        b1.push_back(gmm(ev.Tp, ev.k, 0, W.L2L[q], W.capr[q], 0, t2, ev.k, ev.k, rc, ev.r_old, 1.0, 0.0));
+        bc1.push_back(cpy(t1, rc, W.M2M[q], rc, rc, ev.k));
+        bc1.push_back(cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc));
+      }
+    }
+    for (int a = 0; a < W.nn; ++a)
+      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+        if (!touched[e]) continue;
+        const int b = LL.il[e];
+        const int ra = r_before[a], rb = r_before[b];
+        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
+        if (!ka || !kb) continue;
+        double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
+        if (!ra || !rb) {
+          bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
+          continue;
+        }
+        if (newk[a] >= 0)
+          b1.push_back(gmm(evof[a]->Tp, ka, 0, W.far[e], W.capr[a], 0, t1, ka, ka, rb, ra, 1.0, 0.0));
+        else
+          bc1.push_back(cpy(W.far[e], W.capr[a], t1, ka, ka, rb));
+        if (newk[b] >= 0)
+          b2.push_back(gmm(t1, ka, 0, evof[b]->T, rb, 0, W.far[e], W.capr[a], ka, kb, rb, 1.0, 0.0));
+        else
+          bc2.push_back(cpy(t1, ka, W.far[e], W.capr[a], ka, kb));
+      }
+    cnt.add_gemm(b1);
+    cnt.add_gemm(b2);
+    launch_gemm(st, b1, P64);
+    launch_copy(st, bc1);
+    launch_gemm(st, b2, P64);
+    launch_copy(st, bc2);
+    for (auto& ev : evs) W.r[ev.q] = ev.k;
+    // ---- phase C: fill-in coefficients in the new bases
+    std::vector<GemmDesc> c1, c2;
+    std::vector<CopyDesc> cc;
+    for (auto& f : fills) {
+      const int a = f.a, b = f.b;
+      const bool la = newk[a] >= 0, lb = newk[b] >= 0;  // live (re-based this color)
+      const int ka = W.r[a], kb = W.r[b];
+      double* dst = W.far[W.farix(a, b)];
+      const int ldd = W.capr[a];
+      if (!ka || !kb) continue;
+      if (la && lb) {
+        double* t = scratch.alloc((size_t)ka * f.cols);
+        c1.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, t, ka, ka, f.cols, f.rows, 1.0, 0.0));
+        c2.push_back(gmm(t, ka, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
+      } else if (la) {
+        c2.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, dst, ldd, ka, kb, f.rows, 1.0, 1.0));
+      } else if (lb) {
+        c2.push_back(gmm(f.Fp, f.ld, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
+      } else {
+        cc.push_back(cpy(f.Fp, f.ld, dst, ldd, ka, kb, 1.0, 1.0));
+      }
+    }
+    cnt.add_gemm(c1);
+    cnt.add_gemm(c2);
+    launch_gemm(st, c1, P64);
+    launch_gemm(st, c2, P64);
+    launch_copy(st, cc);
+  }
+
+  // ------------------------------------------------------------------ top level
+  void top(Work& W) {
+    const LevelLists& LL = *W.LL;
+    F.top_off.assign(W.nn + 1, 0);
+    for (int a = 0; a < W.nn; ++a) F.top_off[a + 1] = F.top_off[a] + W.r[a];
+    const int nt = F.top_off[W.nn];
+    F.ntop = nt;
+    F.top_inv = F.persist.alloc((size_t)std::max(1, nt) * std::max(1, nt));
+    if (!nt) return;
+    std::vector<CopyDesc> cc;
+    for (int a = 0; a < W.nn; ++a)
+      for (int b = 0; b < W.nn; ++b) {
+        if (!W.r[a] || !W.r[b]) continue;
+        const int sl = W.slot(a, b);
+        double* dst = F.top_inv + F.top_off[a] + (long)F.top_off[b] * nt;
+        if (sl >= 0) {
+          cc.push_back(cpy(W.nb[2][sl], W.n[a], dst, nt, W.r[a], W.r[b]));
+        } else {
+          const int fx = W.farix(a, b);
+          IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: level-2 pair neither near nor far");
+          cc.push_back(cpy(W.far[fx], W.capr[a], dst, nt, W.r[a], W.r[b]));
+        }
+      }
+    (void)LL;
+    launch_copy(st, cc);
+    double* wk = scratch.alloc(2 * (size_t)nt);
+    int* wi = (int*)scratch.alloc((size_t)nt);
+    int* info = (int*)scratch.alloc(1);
+    big_inverse(s, F.top_inv, nt, nt, wi, wk, info);
+    cnt.lu += 2.0 * std::pow((double)nt, 3);
+    int hinfo = 0;
+    CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st.reset();
+    IFMM_REQUIRE(hinfo == 0, IFMM_ESINGULAR, "singular top-level system");
+  }
+
+  void run() {
+    const int ell = T.depth;
+    F.lv.assign(ell + 1, LevelFactor());
+    m2m_tab = F.persist.alloc((size_t)8 * rc * rc);
+    launch_m2m_table(s, m2m_tab, p);
+    std::unique_ptr<Work> prev;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int kappa = ell; kappa >= 2; --kappa) {
+      auto tl = std::chrono::steady_clock::now();
+      std::unique_ptr<Work> W(new Work());
+      // the child level's blocks stay alive until this level's initial copies ran
+      DeviceArena child_mem;
+      child_mem.swap(levelmem);
+      init_level(*W, kappa, prev.get());
+      CK(cudaStreamSynchronize(s));
+      st.reset();
+      child_mem.release();
+      prev.reset();
+      LevelFactor& LF = F.lv[kappa];
+      LF.kappa = kappa;
+      LF.nn = W->nn;
+      LF.nf.assign(W->nn, NodeFactor());
+      LF.n = W->n;
+      const LevelLists& LL = T.lv[kappa];
+      for (size_t c = 0; c + 1 < LL.group_ptr.size(); ++c) {
+        std::vector<int> grp(LL.group.begin() + LL.group_ptr[c], LL.group.begin() + LL.group_ptr[c + 1]);
+        eliminate_color(*W, grp, LF);
+        LF.order.push_back(grp);
+      }
+      LF.r = W->r;
+      if (kappa == 2) top(*W);
+      CK(cudaStreamSynchronize(s));
+      st.reset();
+      auto te = std::chrono::steady_clock::now();
+      F.stat("time_level_" + std::to_string(kappa), std::chrono::duration<double>(te - tl).count());
+      prev = std::move(W);
+    }
+    build_solve_plan(F, s);
+    CK(cudaStreamSynchronize(s));
+    levelmem.release();
+    scratch.release();
+    auto t1 = std::chrono::steady_clock::now();
+    F.stat("time_factor", std::chrono::duration<double>(t1 - t0).count());
+    F.stat("flops_gemm", cnt.gemm);
+    F.stat("flops_inv", cnt.inv);
+    F.stat("flops_qr", cnt.qr);
+    F.stat("flops_svd", cnt.svd);
+    F.stat("flops_lu", cnt.lu);
+    F.stat("flops_total", cnt.total());
+    F.stat("rank_capped", rank_capped);
+    F.stat("bytes_factor", (double)F.persist.high);
+  }
+
+  ~Factorizer() {
+    if (d_info) cudaFree(d_info);
+  }
+};
+
+}  // namespace ifmm
+
+using namespace ifmm;
+
+ifmm_fact::~ifmm_fact() {
+  if (plan.graph) cudaGraphExecDestroy(plan.graph);
+  if (plan.graph_def) cudaGraphDestroy(plan.graph_def);
+}
+
+extern "C" {
+
+ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opts* o, void* stream,
+                        ifmm_fact** out) {
+  if (out) *out = nullptr;
+  ifmm_fact* F = nullptr;
+  try {
+    IFMM_REQUIRE(t && k && o && out, IFMM_EINVAL, "NULL argument");
+    IFMM_REQUIRE(t->sigma >= 3, IFMM_EINVAL, "call ifmm_color before ifmm_factor");
+    IFMM_REQUIRE(o->cheb_order >= 2 && o->cheb_order <= 6, IFMM_EINVAL, "cheb_order must be in [2, 6]");
+    IFMM_REQUIRE(o->eps >= 0.0 && o->eps < 1.0, IFMM_EINVAL, "eps must be in [0, 1)");
+    IFMM_REQUIRE(o->rank_mode >= 0 && o->rank_mode <= 2, IFMM_EINVAL, "bad rank_mode");
+    IFMM_REQUIRE(o->precision >= 0 && o->precision <= 2, IFMM_EINVAL, "bad precision");
+    const_cast<ifmm_tree*>(t)->ensure_device();
+    F = new ifmm_fact();
+    F->t = t;
+    F->k = *k;
+    F->o = *o;
+    F->p = o->cheb_order;
+    F->rc = o->cheb_order * o->cheb_order * o->cheb_order;
+    {
+      Factorizer fz(*F, (cudaStream_t)stream);
+      fz.run();
+    }
+    F->o.replay = nullptr;  // the caller's table is not kept
+    F->o.mlp = nullptr;
+    *out = F;
+    return IFMM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    delete F;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    delete F;
+    return IFMM_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    delete F;
+    return IFMM_ECUDA;
+  }
+}
+
+void ifmm_fact_free(ifmm_fact* f) { delete f; }
+
+ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64_t* count) {
+  if (!f || !count) {
+    set_last_error("NULL argument");
+    return IFMM_EINVAL;
+  }
+  *count = (int64_t)f->rank_log.size() * 4;
+  for (int64_t e = 0; e < *count && e < cap && buf; ++e) buf[e] = f->rank_log[e / 4][e % 4];
+  return IFMM_OK;
+}
+
+ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count) {
+  if (!f || !count) {
+    set_last_error("NULL argument");
+    return IFMM_EINVAL;
+  }
+  *count = (int64_t)f->stats.size();
+  for (int64_t e = 0; e < *count && e < cap && buf; ++e) buf[e] = f->stats[e].second;
+  return IFMM_OK;
+}
+
+const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index) {
+  if (!f || index < 0 || index >= (int64_t)f->stats.size()) return nullptr;
+  return f->stats[index].first.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,39 @@
+// Host-callable launchers of the IFMM-specific kernels (defined in runtime.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "descs.h"
+#include "runtime.h"
+
+namespace ifmm {
+
+// Near-field block between point ranges [i0, i0+ni) and [j0, j0+nj) (tree order).
+struct P2pDesc {
+  double* dst;
+  int i0, ni, j0, nj, ld, same;
+};
+
+// Leaf interpolation matrix of points [p0, p0+n) in a cell (centre, half-width).
+struct InterpDesc {
+  double* dst;
+  double cx, cy, cz, h;
+  int p0, n, ld, pad;
+};
+
+void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag);
+void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p);
+void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale);
+void launch_m2m_table(cudaStream_t s, double* out, int p);
+void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag);
+void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
+void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
+void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info);
+void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n);
+void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n);
+void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n);
+const char* last_error();
+
+}  // namespace ifmm

@@ -1,0 +1,385 @@
+// Every device kernel of the library lives in this translation unit: the
+// batched dense primitives (dense.cuh) and the IFMM-specific kernels below,
+// plus their launchers.
+#include <cstring>
+#include <thread>
+
+#include "dense.cuh"
+#include "ifmm_kernels.h"
+#include "runtime.h"
+
+namespace ifmm {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(IFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
+  if (v.empty()) return;
+  const CopyDesc* d = st.push(v);
+  k_copy<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
+  check_launch("k_copy");
+}
+
+void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
+  if (v.empty()) return;
+  std::vector<int> tp(v.size() + 1, 0);
+  for (size_t i = 0; i < v.size(); ++i) {
+    long t = (long)((v[i].m + 63) / 64) * ((v[i].n + 63) / 64);
+    if (v[i].m <= 0 || v[i].n <= 0) t = 0;
+    tp[i + 1] = tp[i] + (int)t;
+  }
+  if (tp.back() == 0) return;
+  // descriptors with zero tiles are never selected: find_desc returns the last
+  // descriptor whose start <= tile, and empty ones share their start with the next
+  const GemmDesc* d = st.push(v);
+  const int* p = st.push(tp);
+  if (prec == P32)
+    k_gemm<float><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
+  else
+    k_gemm<double><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
+  check_launch("k_gemm");
+}
+
+void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
+  if (v.empty()) return;
+  int nmax = 0;
+  for (auto& x : v) nmax = std::max(nmax, x.n);
+  size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivot block too large");
+  const InvDesc* d = st.push(v);
+  k_inv<<<(unsigned)v.size(), 256, smem, st.stream>>>(d, (int)v.size());
+  check_launch("k_inv");
+}
+
+void launch_qr(DescStage& st, const std::vector<QrDesc>& v) {
+  if (v.empty()) return;
+  const QrDesc* d = st.push(v);
+  k_qr<<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
+  check_launch("k_qr");
+}
+
+void launch_svd(DescStage& st, const std::vector<SvdDesc>& v) {
+  if (v.empty()) return;
+  int nmax = 0;
+  for (auto& x : v) nmax = std::max(nmax, x.n);
+  size_t smem = sizeof(double) * nmax + sizeof(int) * nmax + 16;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  const SvdDesc* d = st.push(v);
+  k_svd<<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
+  check_launch("k_svd");
+}
+
+void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
+  if (v.empty()) return;
+  const GemvDesc* d = st.push(v);
+  k_gemv<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size());
+  check_launch("k_gemv");
+}
+
+// ------------------------------------------------------------------ IFMM kernels
+__device__ __forceinline__ double cheb_root(int a, int p) {
+  // first-kind Chebyshev roots t_a = cos((2a+1) pi / (2p)), a = 0..p-1
+  return cospi((2.0 * a + 1.0) / (2.0 * p));
+}
+
+// Lagrange basis on the p roots: l_a(u) = prod_{b != a} (u - t_b)/(t_a - t_b)
+__device__ __forceinline__ double lagrange(int a, int p, double u) {
+  const double ta = cheb_root(a, p);
+  double v = 1.0;
+  for (int b = 0; b < p; ++b)
+    if (b != a) {
+      const double tb = cheb_root(b, p);
+      v *= (u - tb) / (ta - tb);
+    }
+  return v;
+}
+
+// Near-field blocks: A_ij = scale/|x_i - x_j|, A_ii = diag (same leaf).
+__global__ void k_p2p(const P2pDesc* __restrict__ d, int nd, const double* __restrict__ px,
+                      const double* __restrict__ py, const double* __restrict__ pz, double scale, double diag) {
+  if ((int)blockIdx.x >= nd) return;
+  const P2pDesc D = d[blockIdx.x];
+  const int total = D.ni * D.nj;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int a = e % D.ni, b = e / D.ni;
+    const int i = D.i0 + a, j = D.j0 + b;
+    double v;
+    if (D.same && a == b) {
+      v = diag;
+    } else {
+      const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
+      v = scale / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    D.dst[a + (long)b * D.ld] = v;
+  }
+}
+
+// Leaf interpolation matrix S (p^3 x n): S(m, j) = l_a(u_x) l_b(u_y) l_c(u_z),
+// m = (c p + b) p + a, u = (x_j - centre)/halfwidth.
+__global__ void k_interp(const InterpDesc* __restrict__ d, int nd, const double* __restrict__ px,
+                         const double* __restrict__ py, const double* __restrict__ pz, int p) {
+  if ((int)blockIdx.x >= nd) return;
+  const InterpDesc D = d[blockIdx.x];
+  const int r = p * p * p;
+  const int total = r * D.n;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int m = e % r, j = e / r;
+    const int a = m % p, b = (m / p) % p, c = m / (p * p);
+    const int pt = D.p0 + j;
+    const double ux = (px[pt] - D.cx) / D.h, uy = (py[pt] - D.cy) / D.h, uz = (pz[pt] - D.cz) / D.h;
+    D.dst[m + (long)j * D.ld] = lagrange(a, p, ux) * lagrange(b, p, uy) * lagrange(c, p, uz);
+  }
+}
+
+// M2L translation table of one level: for the 7^3 target-minus-source cell
+// offsets o, K_o(m, k) = scale / |h (2 o + t_m - t_k)| between the Chebyshev
+// nodes of two cells of half-width h (offsets with max |o| <= 1 stay zero).
+__global__ void k_m2l_table(double* __restrict__ out, int p, double h, double scale) {
+  const int r = p * p * p;
+  const int o = blockIdx.x;  // 0..342
+  const int ox = o % 7 - 3, oy = (o / 7) % 7 - 3, oz = o / 49 - 3;
+  const bool near = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+  double* T = out + (long)o * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int m = e % r, k = e / r;
+    if (near) {
+      T[e] = 0.0;
+      continue;
+    }
+    const int ma = m % p, mb = (m / p) % p, mc = m / (p * p);
+    const int ka = k % p, kb = (k / p) % p, kc = k / (p * p);
+    const double dx = 2.0 * ox + cheb_root(ma, p) - cheb_root(ka, p);
+    const double dy = 2.0 * oy + cheb_root(mb, p) - cheb_root(kb, p);
+    const double dz = 2.0 * oz + cheb_root(mc, p) - cheb_root(kc, p);
+    T[e] = scale / (h * sqrt(dx * dx + dy * dy + dz * dz));
+  }
+}
+
+// M2M of the 8 child octants: M(m, k) = S_parent(child node k, parent node m),
+// the child node at u = (o - 1/2) + t_k / 2 in parent coordinates.
+__global__ void k_m2m_table(double* __restrict__ out, int p) {
+  const int r = p * p * p;
+  const int oct = blockIdx.x;  // 0..7, bit 0 = x, bit 1 = y, bit 2 = z
+  const double sx = (oct & 1) - 0.5, sy = ((oct >> 1) & 1) - 0.5, sz = ((oct >> 2) & 1) - 0.5;
+  double* T = out + (long)oct * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int m = e % r, k = e / r;
+    const int ma = m % p, mb = (m / p) % p, mc = m / (p * p);
+    const int ka = k % p, kb = (k / p) % p, kc = k / (p * p);
+    const double ux = sx + 0.5 * cheb_root(ka, p), uy = sy + 0.5 * cheb_root(kb, p), uz = sz + 0.5 * cheb_root(kc, p);
+    T[e] = lagrange(ma, p, ux) * lagrange(mb, p, uy) * lagrange(mc, p, uz);
+  }
+}
+
+// y = diag x + scale * sum_{j != i} x_j / |p_i - p_j|: a thread per target,
+// sources staged through shared memory in tiles of blockDim.x.
+__global__ void __launch_bounds__(256) k_matvec(const double* __restrict__ px, const double* __restrict__ py,
+                                                const double* __restrict__ pz, const double* __restrict__ x,
+                                                double* __restrict__ y, int n, double scale, double diag) {
+  __shared__ double sx[256], sy[256], sz[256], sq[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double xi = 0, yi = 0, zi = 0;
+  if (i < n) {
+    xi = px[i];
+    yi = py[i];
+    zi = pz[i];
+  }
+  double acc = 0.0;
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    if (j < n) {
+      sx[threadIdx.x] = px[j];
+      sy[threadIdx.x] = py[j];
+      sz[threadIdx.x] = pz[j];
+      sq[threadIdx.x] = x[j];
+    } else {
+      sx[threadIdx.x] = sy[threadIdx.x] = sz[threadIdx.x] = 0.0;
+      sq[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    const int cnt = min((int)blockDim.x, n - j0);
+    for (int t = 0; t < cnt; ++t) {
+      const double dx = xi - sx[t], dy = yi - sy[t], dz = zi - sz[t];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (j0 + t != i) acc += sq[t] * rsqrt(r2);
+    }
+    __syncthreads();
+  }
+  if (i < n) y[i] = diag * x[i] + scale * acc;
+}
+
+__global__ void k_gather_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
+                              int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = src[perm[k]];
+}
+__global__ void k_scatter_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
+                               int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[perm[k]] = src[k];
+}
+
+// ---------------------------------------------------------------- big Gauss-Jordan
+// Inverse of one large n x n matrix with one launch pair per pivot step:
+// k_gj_pivot (one CTA) picks and swaps the pivot row and scales it, then
+// k_gj_update (many CTAs) eliminates column k from every other row.
+__global__ void k_gj_pivot(double* A, long ld, int n, int k, int* piv, double* rowk, double* colk, int* info) {
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  if (info[0] != 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double best = -1.0;
+  int bi = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(A[i + k * ld]);
+    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { red_v[w] = best; red_i[w] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = -1.0;
+    int b = n;
+    for (int i = 0; i < nw; ++i)
+      if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < b)) { bv = red_v[i]; b = red_i[i]; }
+    if (!(bv > 0.0) || b >= n) {
+      info[0] = k + 1;
+      b = k;
+    }
+    s_p = b;
+    piv[k] = b;
+  }
+  __syncthreads();
+  if (info[0] != 0) return;
+  const int p = s_p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double t = A[k + j * ld];
+      A[k + j * ld] = A[p + j * ld];
+      A[p + j * ld] = t;
+    }
+  __syncthreads();
+  const double inv = 1.0 / A[k + k * ld];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = (j == k) ? inv : A[k + j * ld] * inv;
+    rowk[j] = v;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i + k * ld];
+}
+
+__global__ void k_gj_update(double* A, long ld, int n, int k, const double* rowk, const double* colk,
+                            const int* info) {
+  if (info[0] != 0) return;
+  const long total = (long)n * n;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i == k) {
+      A[i + j * ld] = rowk[j];
+    } else {
+      const double a = (j == k) ? 0.0 : A[i + j * ld];
+      A[i + j * ld] = a - colk[i] * rowk[j];
+    }
+  }
+}
+
+__global__ void k_gj_colswap(double* A, long ld, int n, const int* piv, const int* info) {
+  if (info[0] != 0) return;
+  // one CTA: apply the column interchanges in reverse order
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = A[i + k * ld];
+        A[i + k * ld] = A[i + p * ld];
+        A[i + p * ld] = t;
+      }
+    __syncthreads();
+  }
+}
+
+void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info) {
+  // d_work_int: n ints (pivots); d_work: 2n doubles; d_info: 1 int (zeroed here)
+  CK(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+  const int upd_blocks = (int)std::min<long>(152L * 8, ((long)n * n + 255) / 256);
+  for (int k = 0; k < n; ++k) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(A, ld, n, k, d_work_int, d_work, d_work + n, d_info);
+    k_gj_update<<<upd_blocks, 256, 0, s>>>(A, ld, n, k, d_work, d_work + n, d_info);
+  }
+  k_gj_colswap<<<1, 1024, 0, s>>>(A, ld, n, d_work_int, d_info);
+  check_launch("big_inverse");
+}
+
+void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag) {
+  if (v.empty()) return;
+  const P2pDesc* d = st.push(v);
+  k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
+  check_launch("k_p2p");
+}
+
+void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p) {
+  if (v.empty()) return;
+  const InterpDesc* d = st.push(v);
+  k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
+  check_launch("k_interp");
+}
+
+void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale) {
+  k_m2l_table<<<343, 256, 0, s>>>(out, p, h, scale);
+  check_launch("k_m2l_table");
+}
+
+void launch_m2m_table(cudaStream_t s, double* out, int p) {
+  k_m2m_table<<<8, 256, 0, s>>>(out, p);
+  check_launch("k_m2m_table");
+}
+
+void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag) {
+  k_matvec<<<(N + 255) / 256, 256, 0, s>>>(pts, pts + N, pts + 2 * (long)N, x, y, N, scale, diag);
+  check_launch("k_matvec");
+}
+
+void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+  k_gather_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
+  check_launch("k_gather_perm");
+}
+void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+  k_scatter_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
+  check_launch("k_scatter_perm");
+}
+
+// raw launches with device-resident descriptors (solve plans, graph capture)
+void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n) {
+  if (n) k_copy<<<n, 256, 0, s>>>(d, n);
+}
+void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n) {
+  if (n) k_gemv<<<n, 128, 0, s>>>(d, n);
+}
+void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n) {
+  if (n) k_gemv_sum<<<n, 128, 0, s>>>(d, t, n);
+}
+
+}  // namespace ifmm
+
+extern "C" const char* ifmm_last_error(void) { return ifmm::last_error(); }

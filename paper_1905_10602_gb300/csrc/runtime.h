@@ -1,0 +1,191 @@
+// Device memory arenas and batched-launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "descs.h"
+
+namespace ifmm {
+
+#define CK(x)                                                                                \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::ifmm::Error(e_ == cudaErrorMemoryAllocation ? IFMM_ENOMEM : IFMM_ECUDA,        \
+                          std::string(#x) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+// Bump allocator over cudaMalloc'd chunks.  reset() makes the memory reusable;
+// callers only reset at points where all earlier work on the stream that uses
+// the memory has been ordered before later work (one stream) .
+struct DeviceArena {
+  struct Chunk {
+    char* p;
+    size_t size;
+  };
+  std::vector<Chunk> chunks;
+  size_t ci = 0, off = 0;
+  size_t min_chunk = (size_t)256 << 20;
+  size_t high = 0;
+  void* alloc_bytes(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    while (ci < chunks.size()) {
+      if (off + bytes <= chunks[ci].size) {
+        void* r = chunks[ci].p + off;
+        off += bytes;
+        return r;
+      }
+      ++ci;
+      off = 0;
+    }
+    size_t sz = std::max(min_chunk, bytes);
+    void* p = nullptr;
+    CK(cudaMalloc(&p, sz));
+    chunks.push_back({(char*)p, sz});
+    ci = chunks.size() - 1;
+    off = bytes;
+    high += sz;
+    return p;
+  }
+  double* alloc(size_t n) { return (double*)alloc_bytes(n * sizeof(double)); }
+  void reset() { ci = 0; off = 0; }
+  void release() {
+    for (auto& c : chunks) cudaFree(c.p);
+    chunks.clear();
+    ci = off = 0;
+  }
+  void swap(DeviceArena& o) {
+    std::swap(chunks, o.chunks);
+    std::swap(ci, o.ci);
+    std::swap(off, o.off);
+    std::swap(min_chunk, o.min_chunk);
+    std::swap(high, o.high);
+  }
+  DeviceArena() = default;
+  DeviceArena(const DeviceArena&) = delete;
+  DeviceArena& operator=(const DeviceArena&) = delete;
+  ~DeviceArena() { release(); }
+};
+
+// Pinned host staging + device buffer for launch descriptors.  push() copies a
+// vector into pinned memory and enqueues its upload; reset() only after a
+// stream synchronization.
+struct DescStage {
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<char*, size_t>> host;  // pinned chunks
+  size_t hci = 0, hoff = 0;
+  DeviceArena dev;
+  DescStage() { dev.min_chunk = (size_t)64 << 20; }
+  void* host_alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (hci < host.size()) {
+      if (hoff + bytes <= host[hci].second) {
+        void* r = host[hci].first + hoff;
+        hoff += bytes;
+        return r;
+      }
+      ++hci;
+      hoff = 0;
+    }
+    size_t sz = std::max<size_t>((size_t)64 << 20, bytes);
+    void* p = nullptr;
+    CK(cudaMallocHost(&p, sz));
+    host.push_back({(char*)p, sz});
+    hci = host.size() - 1;
+    hoff = bytes;
+    return p;
+  }
+  template <class T>
+  T* push(const T* data, size_t n) {
+    if (n == 0) return nullptr;
+    size_t bytes = n * sizeof(T);
+    void* h = host_alloc(bytes);
+    memcpy(h, data, bytes);
+    void* d = dev.alloc_bytes(bytes);
+    CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
+    return (T*)d;
+  }
+  template <class T>
+  T* push(const std::vector<T>& v) {
+    return push(v.data(), v.size());
+  }
+  void reset() {
+    hci = hoff = 0;
+    dev.reset();
+  }
+  void release() {
+    for (auto& h : host) cudaFreeHost(h.first);
+    host.clear();
+    dev.release();
+  }
+  ~DescStage() { release(); }
+};
+
+enum Prec { P64 = 0, P32 = 1 };
+
+void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);
+void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec);
+void launch_inv(DescStage& st, const std::vector<InvDesc>& v);
+void launch_qr(DescStage& st, const std::vector<QrDesc>& v);
+void launch_svd(DescStage& st, const std::vector<SvdDesc>& v);
+void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v);
+void check_launch(const char* what);
+
+inline CopyDesc cpy(const double* src, int lds, double* dst, int ldd, int rows, int cols, double alpha = 1.0,
+                    double beta = 0.0, int trans = 0) {
+  CopyDesc d;
+  d.src = src;
+  d.dst = dst;
+  d.lds = lds;
+  d.ldd = ldd;
+  d.rows = rows;
+  d.cols = cols;
+  d.alpha = alpha;
+  d.beta = beta;
+  d.trans = trans;
+  d.pad = 0;
+  return d;
+}
+
+inline GemmDesc gmm(const double* A, int lda, int ta, const double* B, int ldb, int tb, double* C, int ldc, int m,
+                    int n, int k, double alpha, double beta) {
+  GemmDesc d;
+  d.A = A;
+  d.B = B;
+  d.C = C;
+  d.lda = lda;
+  d.ldb = ldb;
+  d.ldc = ldc;
+  d.m = m;
+  d.n = n;
+  d.k = k;
+  d.ta = ta;
+  d.tb = tb;
+  d.alpha = alpha;
+  d.beta = beta;
+  return d;
+}
+
+inline GemvDesc gmv(const double* A, int lda, int m, int n, int trans, const double* x, double* y, double alpha,
+                    double beta) {
+  GemvDesc d;
+  d.A = A;
+  d.lda = lda;
+  d.m = m;
+  d.n = n;
+  d.trans = trans;
+  d.x = x;
+  d.y = y;
+  d.alpha = alpha;
+  d.beta = beta;
+  return d;
+}
+
+}  // namespace ifmm

@@ -1,0 +1,227 @@
+"""Python binding of the C ABI in include/ifmm.h (ctypes, argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Arrays may be
+NumPy arrays (host memory) or torch CUDA tensors (device memory); results come
+back on the same side as the inputs.  There is no fallback: if the shared
+library is missing, importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libifmm.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_1905_10602_gb300.build`")
+lib = ctypes.CDLL(_LIB_PATH)
+
+STATUS = {0: "IFMM_OK", 1: "IFMM_EINVAL", 2: "IFMM_ENOMEM", 3: "IFMM_ECUDA", 4: "IFMM_ESINGULAR",
+          5: "IFMM_ENOCONV", 6: "IFMM_ETIMEOUT", 7: "IFMM_ERANK"}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+RANK_MODE = {"svd": 0, "replay": 1, "learned": 2}
+
+
+class IFMMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Kernel(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_double), ("diag", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("cheb_order", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
+                ("rank_mode", ctypes.c_int), ("replay", ctypes.POINTER(ctypes.c_int32)),
+                ("replay_len", ctypes.c_int64), ("max_rank", ctypes.c_int),
+                ("mlp", ctypes.POINTER(ctypes.c_float)), ("seed", ctypes.c_uint64)]
+
+
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_sig = {
+    "ifmm_build_tree": [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp)],
+    "ifmm_color": [_vp, ctypes.c_int, _vp],
+    "ifmm_tree_query": [_vp, ctypes.c_int, ctypes.c_char_p, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_factor": [_vp, ctypes.POINTER(Kernel), ctypes.POINTER(Opts), _vp, ctypes.POINTER(_vp)],
+    "ifmm_solve": [_vp, _vp, _vp, ctypes.c_int, _vp],
+    "bem_gmres": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp, ctypes.c_int, _dbl, ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_dbl), _vp],
+    "bem_matvec": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
+    "ifmm_fact_ranks": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
+}
+for _name, _args in _sig.items():
+    getattr(lib, _name).argtypes = _args
+    getattr(lib, _name).restype = ctypes.c_int
+lib.ifmm_fact_stat_name.argtypes = [_vp, _i64]
+lib.ifmm_fact_stat_name.restype = ctypes.c_char_p
+lib.ifmm_last_error.argtypes = []
+lib.ifmm_last_error.restype = ctypes.c_char_p
+lib.ifmm_tree_free.argtypes = [_vp]
+lib.ifmm_tree_free.restype = None
+lib.ifmm_fact_free.argtypes = [_vp]
+lib.ifmm_fact_free.restype = None
+
+EXPORTED = sorted(list(_sig) + ["ifmm_fact_stat_name", "ifmm_last_error", "ifmm_tree_free", "ifmm_fact_free"])
+
+
+def _check(code):
+    if code != 0:
+        raise IFMMError(code, lib.ifmm_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Pointer of a C-contiguous float64 NumPy array or torch tensor."""
+    if _is_torch(x):
+        assert x.is_contiguous() and str(x.dtype) == "torch.float64"
+        return ctypes.c_void_p(x.data_ptr())
+    assert x.flags["C_CONTIGUOUS"] and x.dtype == np.float64
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(x=None):
+    if x is not None and _is_torch(x) and x.is_cuda:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def default_kernel(n):
+    """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N)."""
+    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n))
+
+
+class Tree:
+    def __init__(self, handle, n, depth, pts):
+        self.h, self.n, self.depth, self._pts = handle, n, depth, pts
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.ifmm_tree_free(self.h)
+            self.h = None
+
+
+class Fact:
+    def __init__(self, handle, tree):
+        self.h, self.tree = handle, tree
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.ifmm_fact_free(self.h)
+            self.h = None
+
+
+def ifmm_build_tree(xyz, depth: int) -> Tree:
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
+    h = ctypes.c_void_p()
+    _check(lib.ifmm_build_tree(xyz.ctypes.data_as(ctypes.c_void_p), xyz.shape[0], depth, ctypes.byref(h)))
+    return Tree(h, xyz.shape[0], depth, xyz)
+
+
+def ifmm_color(tree: Tree, sigma: int) -> np.ndarray:
+    out = np.zeros(tree.depth + 1, dtype=np.int32)
+    _check(lib.ifmm_color(tree.h, sigma, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def ifmm_tree_query(tree: Tree, level: int, what: str) -> np.ndarray:
+    cnt = _i64()
+    _check(lib.ifmm_tree_query(tree.h, level, what.encode(), None, 0, ctypes.byref(cnt)))
+    buf = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.ifmm_tree_query(tree.h, level, what.encode(), buf.ctypes.data_as(ctypes.c_void_p), cnt.value,
+                               ctypes.byref(cnt)))
+    return buf
+
+
+def ifmm_factor(tree: Tree, cheb_order: int, eps: float, kernel: Kernel | None = None, precision: str = "fp64",
+                rank_mode: str = "svd", replay=None, max_rank: int = 0, mlp=None, seed: int = 0, stream=None) -> Fact:
+    k = kernel if kernel is not None else default_kernel(tree.n)
+    o = Opts()
+    o.cheb_order, o.eps, o.precision, o.rank_mode = cheb_order, eps, PREC[precision], RANK_MODE[rank_mode]
+    keep = []
+    if replay is not None:
+        arr = np.ascontiguousarray(np.asarray(replay, dtype=np.int32).reshape(-1, 4))
+        keep.append(arr)
+        o.replay = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        o.replay_len = arr.shape[0]
+    if mlp is not None:
+        w = np.ascontiguousarray(np.asarray(mlp, dtype=np.float32))
+        keep.append(w)
+        o.mlp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    o.max_rank, o.seed = max_rank, seed
+    h = ctypes.c_void_p()
+    _check(lib.ifmm_factor(tree.h, ctypes.byref(k), ctypes.byref(o), stream or ctypes.c_void_p(0), ctypes.byref(h)))
+    return Fact(h, tree)
+
+
+def ifmm_solve(fact: Fact, r, stream=None):
+    """v ~ A~^{-1} r; r is (N,) or (nrhs, N) stacked rows (each row one right-hand side)."""
+    if _is_torch(r):
+        import torch
+
+        v = torch.empty_like(r)
+    else:
+        r = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+        v = np.empty_like(r)
+    nrhs = 1 if r.ndim == 1 else r.shape[0]
+    _check(lib.ifmm_solve(fact.h, _ptr(r), _ptr(v), nrhs, stream or _stream(r)))
+    return v
+
+
+def bem_matvec(tree: Tree, x, kernel: Kernel | None = None, stream=None):
+    k = kernel if kernel is not None else default_kernel(tree.n)
+    if _is_torch(x):
+        import torch
+
+        y = torch.empty_like(x)
+    else:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        y = np.empty_like(x)
+    _check(lib.bem_matvec(tree.h, ctypes.byref(k), _ptr(x), _ptr(y), stream or _stream(x)))
+    return y
+
+
+def bem_gmres(tree: Tree, b, precond: Fact | None = None, restart: int = 30, tol: float = 1e-8, maxit: int = 500,
+              kernel: Kernel | None = None, stream=None, raise_on_noconv: bool = True):
+    """Returns (x, iterations, true relative residual)."""
+    k = kernel if kernel is not None else default_kernel(tree.n)
+    if _is_torch(b):
+        import torch
+
+        x = torch.empty_like(b)
+    else:
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+        x = np.empty_like(b)
+    its, rel = ctypes.c_int(), ctypes.c_double()
+    code = lib.bem_gmres(tree.h, ctypes.byref(k), precond.h if precond else None, _ptr(b), _ptr(x), restart, tol,
+                         maxit, ctypes.byref(its), ctypes.byref(rel), stream or _stream(b))
+    if code != 5 or raise_on_noconv:
+        _check(code)
+    return x, its.value, rel.value
+
+
+def ifmm_fact_ranks(fact: Fact) -> dict:
+    cnt = _i64()
+    _check(lib.ifmm_fact_ranks(fact.h, None, 0, ctypes.byref(cnt)))
+    buf = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.ifmm_fact_ranks(fact.h, buf.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt)))
+    q = buf.reshape(-1, 4)
+    return {(int(a), int(b), int(c)): int(d) for a, b, c, d in q}
+
+
+def ifmm_fact_stats(fact: Fact) -> dict:
+    cnt = _i64()
+    _check(lib.ifmm_fact_stats(fact.h, None, 0, ctypes.byref(cnt)))
+    buf = np.zeros(cnt.value, dtype=np.float64)
+    _check(lib.ifmm_fact_stats(fact.h, buf.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt)))
+    return {lib.ifmm_fact_stat_name(fact.h, i).decode(): float(buf[i]) for i in range(cnt.value)}

@@ -1,0 +1,143 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Tolerances: the FP64 path must reproduce the oracle's applied inverse to a
+relative 2-norm difference <= 1e-9 (rank replay at finite eps, so both sides
+truncate to the same ranks); at eps = 0 both equal A~^{-1} (1e-11); the
+direct-summation matvec matches the dense product to 1e-13.
+"""
+
+import numpy as np
+import pytest
+
+from oracle.dense import direct_matvec, fmm_matrix
+from oracle.gmres import gmres as oracle_gmres
+from oracle.ifmm import IFMMOracle
+from oracle.operators import dense_matrix
+from paper_1905_10602_gb300 import build as _build
+from paper_1905_10602_gb300.workloads import bumpy_sphere, fibonacci_sphere, point_source_rhs, torus
+
+pytestmark = pytest.mark.gpu
+
+_build.build()
+from paper_1905_10602_gb300 import ifmm  # noqa: E402
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _gpu(pts, depth, p, eps, sigma, replay=None, **kw):
+    t = ifmm.ifmm_build_tree(pts, depth)
+    ifmm.ifmm_color(t, sigma)
+    rep = None if replay is None else [list(k) + [v] for k, v in replay.items()]
+    f = ifmm.ifmm_factor(t, p, eps, rank_mode="replay" if rep else "svd", replay=rep, **kw)
+    return t, f
+
+
+@pytest.mark.parametrize("N,depth,p,sigma", [(200, 2, 2, 3), (600, 2, 3, 6), (1024, 3, 3, 6), (1024, 3, 3, 3),
+                                             (1500, 3, 4, 3)])
+def test_exact_at_eps0(N, depth, p, sigma):
+    """eps = 0: the GPU factorization is exact Gaussian elimination on the extended
+    system; its solve equals the oracle's and A~^{-1} b."""
+    pts = fibonacci_sphere(N, 1)
+    b = point_source_rhs(pts)
+    o = IFMMOracle(pts, depth, p, 0.0, sigma).factor()
+    t, f = _gpu(pts, depth, p, 0.0, sigma)
+    xg = ifmm.ifmm_solve(f, b)
+    assert _rel(xg, o.solve(b)) < 1e-11
+    At = fmm_matrix(o.tree, o.ops)
+    assert _rel(xg, np.linalg.solve(At, b)) < 1e-11
+
+
+@pytest.mark.parametrize("shape,N,depth,p,eps,sigma", [
+    ("sphere", 2048, 3, 3, 1e-6, 6),   # the 2,048-point sphere workload
+    ("sphere", 2048, 3, 3, 1e-6, 3),
+    ("bumpy", 3000, 4, 3, 1e-6, 3),    # ragged tail: 4 levels, bumpy surface
+    ("torus", 2500, 3, 4, 1e-4, 6),
+])
+def test_replay_parity(shape, N, depth, p, eps, sigma):
+    """Finite eps with the oracle's ranks replayed: applied inverse within 1e-9."""
+    pts = {"sphere": fibonacci_sphere, "bumpy": bumpy_sphere, "torus": torus}[shape](N, 3)
+    o = IFMMOracle(pts, depth, p, eps, sigma).factor()
+    t, f = _gpu(pts, depth, p, eps, sigma, replay=o.ranks())
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal((3, N))
+    V = ifmm.ifmm_solve(f, R)
+    for k in range(3):
+        assert _rel(V[k], o.solve(R[k])) < 1e-9
+    assert ifmm.ifmm_fact_ranks(f) == o.ranks()
+
+
+def test_free_ranks_agree_with_oracle():
+    """Without replay the GPU chooses its own ranks; they match the oracle's except
+    for singular values within rounding of the threshold, and the solve is within eps."""
+    pts = fibonacci_sphere(2048, 1)
+    o = IFMMOracle(pts, 3, 3, 1e-6, 6).factor()
+    t, f = _gpu(pts, 3, 3, 1e-6, 6)
+    rg, ro = ifmm.ifmm_fact_ranks(f), o.ranks()
+    assert rg.keys() == ro.keys()
+    assert sum(rg[k] != ro[k] for k in ro) <= 0.01 * len(ro)
+    b = point_source_rhs(pts)
+    assert _rel(ifmm.ifmm_solve(f, b), o.solve(b)) < 1e-6
+
+
+def test_sigma6_permutation_independent_of_node_order_within_color():
+    """Sec. 3.2: the nodes of a sigma=6 color are independent; the GPU processes
+    them in parallel, and the result equals the oracle's sequential order."""
+    pts = bumpy_sphere(2500, 9)
+    o = IFMMOracle(pts, 3, 3, 1e-8, 6).factor()
+    t, f = _gpu(pts, 3, 3, 1e-8, 6, replay=o.ranks())
+    b = point_source_rhs(pts)
+    assert _rel(ifmm.ifmm_solve(f, b), o.solve(b)) < 1e-9
+
+
+def test_matvec_matches_dense():
+    for pts in (fibonacci_sphere(3000, 2), torus(1777, 1)):
+        t = ifmm.ifmm_build_tree(pts, 3)
+        x = np.random.default_rng(1).standard_normal(len(pts))
+        assert _rel(ifmm.bem_matvec(t, x), dense_matrix(pts) @ x) < 1e-13
+
+
+def test_matvec_sampled_rows_large():
+    """N = 131,072 bumpy sphere: sampled rows against the oracle's direct sum."""
+    pts = bumpy_sphere(131072, 3)
+    t = ifmm.ifmm_build_tree(pts, 6)
+    x = np.random.default_rng(2).standard_normal(len(pts))
+    y = ifmm.bem_matvec(t, x)
+    rows = np.random.default_rng(3).choice(len(pts), 64, replace=False)
+    assert _rel(y[rows], direct_matvec(pts, x, rows)) < 1e-12
+
+
+def test_gmres_matches_oracle_and_dense():
+    pts = fibonacci_sphere(2048, 1)
+    A = dense_matrix(pts)
+    b = point_source_rhs(pts)
+    t, f = _gpu(pts, 3, 3, 1e-6, 6)
+    x, its, rel = ifmm.bem_gmres(t, b, precond=f, tol=1e-8)
+    assert rel <= 1e-8 and np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 1.01e-8
+    o = IFMMOracle(pts, 3, 3, 1e-6, 6).factor()
+    _, its_o, _ = oracle_gmres(lambda v: A @ v, b, precond=o.solve, tol=1e-8)
+    assert abs(its - its_o) <= 1
+    x0, its0, rel0 = ifmm.bem_gmres(t, b, precond=None, tol=1e-8)
+    assert its < its0
+
+
+def test_solve_host_and_device_buffers_agree():
+    import torch
+
+    pts = fibonacci_sphere(1024, 4)
+    t, f = _gpu(pts, 3, 3, 1e-6, 3)
+    b = point_source_rhs(pts)
+    xh = ifmm.ifmm_solve(f, b)
+    xd = ifmm.ifmm_solve(f, torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.array_equal(xh, xd)
+
+
+def test_empty_interaction_lists_small_tree():
+    """Degenerate cases: a depth-2 tree over a few points (most cells adjacent,
+    tiny or empty interaction lists) still factors exactly."""
+    pts = fibonacci_sphere(40, 2)
+    o = IFMMOracle(pts, 2, 2, 0.0, 3).factor()
+    t, f = _gpu(pts, 2, 2, 0.0, 3)
+    b = point_source_rhs(pts)
+    assert _rel(ifmm.ifmm_solve(f, b), o.solve(b)) < 1e-11
