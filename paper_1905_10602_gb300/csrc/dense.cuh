@@ -219,6 +219,15 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd) {
 // ---------------------------------------------------------------- Householder QR
 // One CTA per matrix.  Column k: v = x - alpha e1 with alpha = -sign(x_0)||x||,
 // H = I - 2 v v^T / (v^T v) applied to the trailing columns (one warp per column).
+// Storage is double; TC is the arithmetic type of the dot products and updates.
+template <typename TC>
+__device__ __forceinline__ TC warp_sum_t(TC v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename TC>
 __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
   if ((int)blockIdx.x >= nd) return;
   const QrDesc D = d[blockIdx.x];
@@ -226,7 +235,7 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
   const long ld = D.ld;
   double* A = D.A;
   __shared__ double scratch[32];
-  __shared__ double s_alpha, s_beta;
+  __shared__ double s_alpha, s_beta, s_scale;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   const int kmax = m < n ? m : n;
   for (int k = 0; k < kmax; ++k) {
@@ -235,30 +244,35 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
     double ss = 0.0;
     for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) ss += x[i] * x[i];
     ss = block_sum(ss, scratch);
+    // reflector in the normalised form H = I - tau v v^T, v_0 = 1,
+    // v_i = x_i / (x_0 - alpha), tau = (alpha - x_0) / alpha in [1, 2]
     if (threadIdx.x == 0) {
       const double x0 = x[0];
       const double nrm = sqrt(x0 * x0 + ss);
-      if (nrm == 0.0) {
-        s_alpha = 0.0;
+      if (nrm == 0.0 || ss == 0.0) {
+        s_alpha = x0;
         s_beta = 0.0;
       } else {
         const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-        const double v0 = x0 - alpha;
-        const double vtv = v0 * v0 + ss;
         s_alpha = alpha;
-        s_beta = (vtv > 0.0) ? 2.0 / vtv : 0.0;
-        x[0] = v0;
+        s_beta = (alpha - x0) / alpha;
+        s_scale = 1.0 / (x0 - alpha);
       }
     }
     __syncthreads();
-    const double beta = s_beta;
-    if (beta != 0.0) {
+    const double tau = s_beta;
+    if (tau != 0.0) {
+      const double sc = s_scale;
+      for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] *= sc;
+      __syncthreads();
+      const TC t = (TC)tau;
       for (int j = k + 1 + w; j < n; j += nw) {
         double* y = A + k + (long)j * ld;
-        double dot = 0.0;
-        for (int i = lane; i < len; i += 32) dot += x[i] * y[i];
-        dot = warp_sum(dot) * beta;
-        for (int i = lane; i < len; i += 32) y[i] -= dot * x[i];
+        TC dot = (lane == 0) ? (TC)y[0] : (TC)0;  // v_0 = 1
+        for (int i = 1 + lane; i < len; i += 32) dot += (TC)x[i] * (TC)y[i];
+        dot = warp_sum_t<TC>(dot) * t;
+        if (lane == 0) y[0] = (double)((TC)y[0] - dot);
+        for (int i = 1 + lane; i < len; i += 32) y[i] = (double)((TC)y[i] - dot * (TC)x[i]);
       }
     }
     __syncthreads();
@@ -266,8 +280,6 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
     for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = 0.0;
     __syncthreads();
   }
-  // rows below min(m, n) in columns >= m are already part of R's rectangle; zero
-  // anything left strictly below the diagonal (columns beyond kmax are untouched)
 }
 
 // ---------------------------------------------------------------- one-sided Jacobi SVD
@@ -277,6 +289,7 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
 // column 1 + ((p - 1 - r) mod (n'-1)); pair i joins positions i and n'-1-i), so
 // the n'/2 pairs of a round are disjoint and handled by different warps.
 // Dynamic shared memory: n doubles (column norms) + n ints (order).
+template <typename TC>
 __global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
   if ((int)blockIdx.x >= nd) return;
   const SvdDesc D = d[blockIdx.x];
@@ -290,9 +303,28 @@ __global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
   __shared__ int s_rot;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) W[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+  // scale G to max |G_ij| = 1 so that sums of squares neither overflow nor
+  // underflow in the arithmetic type; singular values are scaled back at the end
+  __shared__ double s_gmax[32];
+  double gmax = 0.0;
+  for (long e = threadIdx.x; e < (long)m * n; e += blockDim.x) {
+    const double v = fabs(G[(e % m) + (e / m) * ldg]);
+    gmax = (v > gmax || v != v) ? v : gmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, gmax, o);
+    gmax = (ov > gmax || ov != ov) ? ov : gmax;
+  }
+  if (lane == 0) s_gmax[w] = gmax;
+  __syncthreads();
+  gmax = 0.0;
+  for (int i = 0; i < nw; ++i) gmax = (s_gmax[i] > gmax || s_gmax[i] != s_gmax[i]) ? s_gmax[i] : gmax;
+  const double gscale = (gmax > 0.0 && gmax < 1e300) ? 1.0 / gmax : 1.0;
+  for (long e = threadIdx.x; e < (long)m * n; e += blockDim.x) G[(e % m) + (e / m) * ldg] *= gscale;
   const int np = n + (n & 1);
   int sweep = 0;
-  const double tol = 1e-15;
+  const TC tol = sizeof(TC) == 8 ? (TC)1e-15 : (TC)4e-7;
   __syncthreads();
   for (; sweep < max_sweeps && n > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
@@ -306,38 +338,42 @@ __global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
         if (a > b) { const int t = a; a = b; b = t; }
         double* ga = G + (long)a * ldg;
         double* gb = G + (long)b * ldg;
-        double al = 0.0, be = 0.0, ga_b = 0.0;
+        TC al = 0, be = 0, ga_b = 0;
         for (int i = lane; i < m; i += 32) {
-          const double u = ga[i], v = gb[i];
+          const TC u = (TC)ga[i], v = (TC)gb[i];
           al += u * u;
           be += v * v;
           ga_b += u * v;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga_b = warp_sum(ga_b);
-        if (al < 1e-300 || be < 1e-300) continue;
+        al = warp_sum_t<TC>(al);
+        be = warp_sum_t<TC>(be);
+        ga_b = warp_sum_t<TC>(ga_b);
+        const TC tiny = sizeof(TC) == 8 ? (TC)1e-300 : (TC)1e-36;
+        if (al < tiny || be < tiny) continue;
         if (fabs(ga_b) <= tol * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * ga_b);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const TC zeta = (be - al) / ((TC)2 * ga_b);
+        const TC t = (zeta >= (TC)0 ? (TC)1 : (TC)-1) / (fabs(zeta) + hypot((TC)1, zeta));
+        const TC c = (TC)1 / sqrt((TC)1 + t * t), s = c * t;
         for (int i = lane; i < m; i += 32) {
-          const double u = ga[i], v = gb[i];
-          ga[i] = c * u - s * v;
-          gb[i] = s * u + c * v;
+          const TC u = (TC)ga[i], v = (TC)gb[i];
+          ga[i] = (double)(c * u - s * v);
+          gb[i] = (double)(s * u + c * v);
         }
         double* wa = W + (long)a * n;
         double* wb = W + (long)b * n;
         for (int i = lane; i < n; i += 32) {
-          const double u = wa[i], v = wb[i];
-          wa[i] = c * u - s * v;
-          wb[i] = s * u + c * v;
+          const TC u = (TC)wa[i], v = (TC)wb[i];
+          wa[i] = (double)(c * u - s * v);
+          wb[i] = (double)(s * u + c * v);
         }
         if (lane == 0) s_rot = 1;
       }
       __syncthreads();
     }
-    if (!s_rot) break;
+    // every thread reads the flag before thread 0 may clear it for the next sweep
+    const int rotated = s_rot;
+    __syncthreads();
+    if (!rotated) break;
   }
   // column norms = singular values; order descending (ties: lower index first)
   for (int j = w; j < n; j += nw) {
@@ -348,14 +384,19 @@ __global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
     if (lane == 0) nrm[j] = sqrt(s);
   }
   __syncthreads();
+  // descending order, ties by index; a NaN norm sorts last (key -1), so the
+  // ranks are a permutation of 0..n-1 whatever the data
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     int rank = 0;
-    const double v = nrm[j];
-    for (int k = 0; k < n; ++k) rank += (nrm[k] > v) || (nrm[k] == v && k < j);
+    const double v = (nrm[j] == nrm[j]) ? nrm[j] : -1.0;
+    for (int k = 0; k < n; ++k) {
+      const double u = (nrm[k] == nrm[k]) ? nrm[k] : -1.0;
+      rank += (u > v) || (u == v && k < j);
+    }
     ord[rank] = j;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = nrm[ord[j]];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = nrm[ord[j]] / gscale;
   for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
     D.V[i + (long)j * D.ldv] = W[i + (long)ord[j] * n];

@@ -104,6 +104,7 @@ struct Factorizer {
   DeviceArena scratch;
   DeviceArena levelmem;
   int p, rc, maxrank;
+  int prec = P64;  // arithmetic of Schur GEMMs and recompression (pivots stay FP64)
   double* m2m_tab = nullptr;
   double* m2l_tab = nullptr;
   std::unordered_map<int64_t, int> replay;
@@ -113,12 +114,19 @@ struct Factorizer {
   int info_cap = 0;
   std::vector<double*> pinned_sig;
   double rank_capped = 0;
+  double t_wait = 0;
+  void wait() {
+    auto a = std::chrono::steady_clock::now();
+    CK(cudaStreamSynchronize(s));
+    t_wait += std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+  }
 
   Factorizer(ifmm_fact& f, cudaStream_t stream) : F(f), T(*f.t), s(stream) {
     st.stream = s;
     p = F.p;
     rc = F.rc;
     maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256;
+    prec = F.o.precision == IFMM_PREC_FP64 ? P64 : P32;
     if (F.o.rank_mode == IFMM_RANK_REPLAY) {
       IFMM_REQUIRE(F.o.replay != nullptr || F.o.replay_len == 0, IFMM_EINVAL, "replay table is NULL");
       for (int64_t e = 0; e < F.o.replay_len; ++e) {
@@ -224,12 +232,12 @@ struct Factorizer {
       }
     }
     launch_copy(st, cz);
-    launch_qr(st, qz);
+    launch_qr(st, qz, prec);
     cnt.add_gemm(gw);
-    launch_gemm(st, gw, P64);
+    launch_gemm(st, gw, prec);
     launch_copy(st, cf);
-    launch_qr(st, qy);
-    launch_svd(st, sv);
+    launch_qr(st, qy, prec);
+    launch_svd(st, sv, prec);
     // read back singular values (and pivot status)
     size_t total = 0;
     for (auto& ev : evs)
@@ -253,7 +261,7 @@ struct Factorizer {
       hi = (int*)st.host_alloc(sizeof(int) * n_inv);
       CK(cudaMemcpyAsync(hi, d_info, sizeof(int) * n_inv, cudaMemcpyDeviceToHost, s));
     }
-    CK(cudaStreamSynchronize(s));
+    wait();
     if (total) memcpy(hsig.data(), hp, total * sizeof(double));
     if (n_inv) memcpy(hinfo.data(), hi, sizeof(int) * n_inv);
     st.reset();
@@ -304,7 +312,7 @@ struct Factorizer {
       cb.push_back(cpy(ev.V[1], n, L2P_out[e], L2P_ld[e], n, k, 1.0, 0.0, 0));
     }
     cnt.add_gemm(gt);
-    launch_gemm(st, gt, P64);
+    launch_gemm(st, gt, prec);
     launch_copy(st, cb);
   }
 
@@ -515,8 +523,8 @@ struct Factorizer {
       }
     cnt.add_gemm(g1);
     cnt.add_gemm(g2);
-    launch_gemm(st, g1, P64);
-    launch_gemm(st, g2, P64);
+    launch_gemm(st, g1, prec);
+    launch_gemm(st, g2, prec);
   }
 
   // ------------------------------------------------------------------ one color
@@ -525,9 +533,13 @@ struct Factorizer {
     scratch.reset();
     const int ng = (int)grp.size();
     if (info_cap < ng) {
-      if (d_info) cudaFree(d_info);
+      if (d_info) {
+        registry().remove_range(d_info, sizeof(int) * info_cap);
+        cudaFree(d_info);
+      }
       CK(cudaMalloc(&d_info, sizeof(int) * std::max(ng, 64)));
       info_cap = std::max(ng, 64);
+      registry().add(d_info, sizeof(int) * info_cap);
     }
     // ---- pivots
     std::vector<CopyDesc> cpi;
@@ -646,8 +658,8 @@ struct Factorizer {
     launch_copy(st, cg);
     cnt.add_gemm(gx);
     cnt.add_gemm(gf);
-    launch_gemm(st, gx, P64);
-    launch_gemm(st, gf, P64);
+    launch_gemm(st, gx, prec);
+    launch_gemm(st, gf, prec);
     launch_copy(st, sc);
     // ---- recompression events (snapshots: nothing below reads what phase A changes)
     std::vector<Event> evs;
@@ -731,9 +743,9 @@ struct Factorizer {
       }
     cnt.add_gemm(b1);
     cnt.add_gemm(b2);
-    launch_gemm(st, b1, P64);
+    launch_gemm(st, b1, prec);
     launch_copy(st, bc1);
-    launch_gemm(st, b2, P64);
+    launch_gemm(st, b2, prec);
     launch_copy(st, bc2);
     for (auto& ev : evs) W.r[ev.q] = ev.k;
     // ---- phase C: fill-in coefficients in the new bases
@@ -760,8 +772,8 @@ struct Factorizer {
     }
     cnt.add_gemm(c1);
     cnt.add_gemm(c2);
-    launch_gemm(st, c1, P64);
-    launch_gemm(st, c2, P64);
+    launch_gemm(st, c1, prec);
+    launch_gemm(st, c2, prec);
     launch_copy(st, cc);
   }
 
@@ -816,7 +828,7 @@ struct Factorizer {
       DeviceArena child_mem;
       child_mem.swap(levelmem);
       init_level(*W, kappa, prev.get());
-      CK(cudaStreamSynchronize(s));
+      wait();
       st.reset();
       child_mem.release();
       prev.reset();
@@ -833,7 +845,7 @@ struct Factorizer {
       }
       LF.r = W->r;
       if (kappa == 2) top(*W);
-      CK(cudaStreamSynchronize(s));
+      wait();
       st.reset();
       auto te = std::chrono::steady_clock::now();
       F.stat("time_level_" + std::to_string(kappa), std::chrono::duration<double>(te - tl).count());
@@ -852,11 +864,15 @@ struct Factorizer {
     F.stat("flops_lu", cnt.lu);
     F.stat("flops_total", cnt.total());
     F.stat("rank_capped", rank_capped);
+    F.stat("time_device_wait", t_wait);
     F.stat("bytes_factor", (double)F.persist.high);
   }
 
   ~Factorizer() {
-    if (d_info) cudaFree(d_info);
+    if (d_info) {
+      registry().remove_range(d_info, sizeof(int) * info_cap);
+      cudaFree(d_info);
+    }
   }
 };
 

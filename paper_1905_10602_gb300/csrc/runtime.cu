@@ -1,6 +1,7 @@
 // Every device kernel of the library lives in this translation unit: the
 // batched dense primitives (dense.cuh) and the IFMM-specific kernels below,
 // plus their launchers.
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 
@@ -14,6 +15,52 @@ static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error() { return g_last_error.c_str(); }
 
+Registry& registry() {
+  static Registry r;
+  static bool init = false;
+  if (!init) {
+    const char* e = getenv("IFMM_CHECK");
+    r.on = e && e[0] == '1';
+    init = true;
+  }
+  return r;
+}
+
+// bytes spanned by an m x n column-major block with leading dimension ld
+static size_t span(int m, int n, long ld) {
+  if (m <= 0 || n <= 0) return 0;
+  return sizeof(double) * ((size_t)(n - 1) * ld + m);
+}
+static void req(const void* p, size_t bytes, const char* what, size_t idx) {
+  if (!bytes || registry().contains(p, bytes)) return;
+  throw Error(IFMM_EINVAL, std::string("bounds check failed: ") + what + " descriptor " + std::to_string(idx) +
+                               " touches " + std::to_string(bytes) + " bytes outside any allocation");
+}
+static void check_copy(const std::vector<CopyDesc>& v) {
+  if (!registry().on) return;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const CopyDesc& d = v[i];
+    if (d.rows < 0 || d.cols < 0) throw Error(IFMM_EINVAL, "negative copy size");
+    if (d.src) req(d.src, d.trans ? span(d.cols, d.rows, d.lds) : span(d.rows, d.cols, d.lds), "copy.src", i);
+    req(d.dst, span(d.rows, d.cols, d.ldd), "copy.dst", i);
+    if (d.ldd < d.rows || (d.src && d.lds < (d.trans ? d.cols : d.rows))) throw Error(IFMM_EINVAL, "copy ld too small");
+  }
+}
+static void check_gemm(const std::vector<GemmDesc>& v) {
+  if (!registry().on) return;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const GemmDesc& d = v[i];
+    if (d.m <= 0 || d.n <= 0) continue;
+    if (d.k > 0) {
+      req(d.A, d.ta ? span(d.k, d.m, d.lda) : span(d.m, d.k, d.lda), "gemm.A", i);
+      req(d.B, d.tb ? span(d.n, d.k, d.ldb) : span(d.k, d.n, d.ldb), "gemm.B", i);
+      if (d.lda < (d.ta ? d.k : d.m) || d.ldb < (d.tb ? d.n : d.k)) throw Error(IFMM_EINVAL, "gemm ld too small");
+    }
+    req(d.C, span(d.m, d.n, d.ldc), "gemm.C", i);
+    if (d.ldc < d.m) throw Error(IFMM_EINVAL, "gemm ldc too small");
+  }
+}
+
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(IFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -22,6 +69,7 @@ void check_launch(const char* what) {
 // ------------------------------------------------------------------ launchers
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
+  check_copy(v);
   const CopyDesc* d = st.push(v);
   k_copy<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_copy");
@@ -29,6 +77,7 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
 
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
   if (v.empty()) return;
+  check_gemm(v);
   std::vector<int> tp(v.size() + 1, 0);
   for (size_t i = 0; i < v.size(); ++i) {
     long t = (long)((v[i].m + 63) / 64) * ((v[i].n + 63) / 64);
@@ -58,35 +107,64 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     attr = true;
   }
   IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivot block too large");
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    req(v[i].A, span(v[i].n, v[i].n, v[i].ld), "inv.A", i);
+    req(v[i].info, sizeof(int), "inv.info", i);
+  }
   const InvDesc* d = st.push(v);
   k_inv<<<(unsigned)v.size(), 256, smem, st.stream>>>(d, (int)v.size());
   check_launch("k_inv");
 }
 
-void launch_qr(DescStage& st, const std::vector<QrDesc>& v) {
+void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
   if (v.empty()) return;
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    req(v[i].A, span(v[i].m, v[i].n, v[i].ld), "qr.A", i);
+    if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qr ld too small");
+  }
   const QrDesc* d = st.push(v);
-  k_qr<<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
+  if (prec == P32)
+    k_qr<float><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
+  else
+    k_qr<double><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_qr");
 }
 
-void launch_svd(DescStage& st, const std::vector<SvdDesc>& v) {
+void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
   if (v.empty()) return;
   int nmax = 0;
   for (auto& x : v) nmax = std::max(nmax, x.n);
   size_t smem = sizeof(double) * nmax + sizeof(int) * nmax + 16;
   static bool attr = false;
   if (!attr) {
-    CK(cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CK(cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CK(cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    const SvdDesc& x = v[i];
+    req(x.G, span(x.m, x.n, x.ldg), "svd.G", i);
+    req(x.V, span(x.n, x.n, x.ldv), "svd.V", i);
+    req(x.Vw, span(x.n, x.n, x.n), "svd.Vw", i);
+    req(x.sig, span(x.n, 1, x.n), "svd.sig", i);
+    if (x.ldg < x.m || x.ldv < x.n) throw Error(IFMM_EINVAL, "svd ld too small");
+  }
   const SvdDesc* d = st.push(v);
-  k_svd<<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
+  if (prec == P32)
+    k_svd<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
+  else
+    k_svd<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
   check_launch("k_svd");
 }
 
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
   if (v.empty()) return;
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    const GemvDesc& x = v[i];
+    req(x.A, span(x.m, x.n, x.lda), "gemv.A", i);
+    req(x.x, sizeof(double) * (x.trans ? x.m : x.n), "gemv.x", i);
+    req(x.y, sizeof(double) * (x.trans ? x.n : x.m), "gemv.y", i);
+  }
   const GemvDesc* d = st.push(v);
   k_gemv<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_gemv");
@@ -333,6 +411,11 @@ void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, doub
 
 void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag) {
   if (v.empty()) return;
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    req(v[i].dst, span(v[i].ni, v[i].nj, v[i].ld), "p2p.dst", i);
+    if (v[i].i0 < 0 || v[i].j0 < 0 || v[i].i0 + v[i].ni > N || v[i].j0 + v[i].nj > N)
+      throw Error(IFMM_EINVAL, "p2p point range");
+  }
   const P2pDesc* d = st.push(v);
   k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
   check_launch("k_p2p");
@@ -340,6 +423,10 @@ void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts,
 
 void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p) {
   if (v.empty()) return;
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    req(v[i].dst, span(p * p * p, v[i].n, v[i].ld), "interp.dst", i);
+    if (v[i].p0 < 0 || v[i].p0 + v[i].n > N) throw Error(IFMM_EINVAL, "interp point range");
+  }
   const InterpDesc* d = st.push(v);
   k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
   check_launch("k_interp");

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -20,6 +22,32 @@ namespace ifmm {
       throw ::ifmm::Error(e_ == cudaErrorMemoryAllocation ? IFMM_ENOMEM : IFMM_ECUDA,        \
                           std::string(#x) + ": " + cudaGetErrorString(e_));                  \
   } while (0)
+
+// Optional host-side bounds check of every launch (IFMM_CHECK=1): allocations
+// are registered, and each descriptor's address range must fall inside one of
+// them before the kernel is launched.
+struct Registry {
+  bool on = false;
+  std::map<uintptr_t, uintptr_t> iv;  // start -> end
+  void add(const void* p, size_t bytes) {
+    if (on) iv[(uintptr_t)p] = (uintptr_t)p + bytes;
+  }
+  void remove_range(const void* lo, size_t bytes) {
+    if (!on) return;
+    auto a = iv.lower_bound((uintptr_t)lo);
+    auto b = iv.lower_bound((uintptr_t)lo + bytes);
+    iv.erase(a, b);
+  }
+  bool contains(const void* p, size_t bytes) const {
+    if (!on) return true;
+    uintptr_t lo = (uintptr_t)p, hi = lo + bytes;
+    auto it = iv.upper_bound(lo);
+    if (it == iv.begin()) return false;
+    --it;
+    return it->first <= lo && hi <= it->second;
+  }
+};
+Registry& registry();
 
 // Bump allocator over cudaMalloc'd chunks.  reset() makes the memory reusable;
 // callers only reset at points where all earlier work on the stream that uses
@@ -40,6 +68,7 @@ struct DeviceArena {
       if (off + bytes <= chunks[ci].size) {
         void* r = chunks[ci].p + off;
         off += bytes;
+        registry().add(r, bytes);
         return r;
       }
       ++ci;
@@ -52,11 +81,17 @@ struct DeviceArena {
     ci = chunks.size() - 1;
     off = bytes;
     high += sz;
+    registry().add(p, bytes);
     return p;
   }
   double* alloc(size_t n) { return (double*)alloc_bytes(n * sizeof(double)); }
-  void reset() { ci = 0; off = 0; }
+  void reset() {
+    for (auto& c : chunks) registry().remove_range(c.p, c.size);
+    ci = 0;
+    off = 0;
+  }
   void release() {
+    for (auto& c : chunks) registry().remove_range(c.p, c.size);
     for (auto& c : chunks) cudaFree(c.p);
     chunks.clear();
     ci = off = 0;
@@ -133,8 +168,8 @@ enum Prec { P64 = 0, P32 = 1 };
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec);
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v);
-void launch_qr(DescStage& st, const std::vector<QrDesc>& v);
-void launch_svd(DescStage& st, const std::vector<SvdDesc>& v);
+void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec);
+void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec);
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v);
 void check_launch(const char* what);
 

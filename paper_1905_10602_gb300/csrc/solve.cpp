@@ -254,23 +254,36 @@ void ifmm_tree::ensure_device() {
   CK(cudaMemcpy(d_pts, soa.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
   CK(cudaMalloc(&d_perm, sizeof(int32_t) * N));
   CK(cudaMemcpy(d_perm, perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  registry().add(d_pts, sizeof(double) * 3 * N);
+  registry().add(d_perm, sizeof(int32_t) * N);
 }
 
 ifmm_tree::~ifmm_tree() {
-  if (d_pts) cudaFree(d_pts);
-  if (d_perm) cudaFree(d_perm);
+  if (d_pts) {
+    registry().remove_range(d_pts, sizeof(double) * 3 * N);
+    cudaFree(d_pts);
+  }
+  if (d_perm) {
+    registry().remove_range(d_perm, sizeof(int32_t) * N);
+    cudaFree(d_perm);
+  }
 }
 
 // device buffers for the GMRES / solve wrappers
 struct Vecs {
-  std::vector<double*> p;
+  std::vector<std::pair<double*, size_t>> p;
   ~Vecs() {
-    for (auto x : p) cudaFree(x);
+    for (auto x : p) {
+      registry().remove_range(x.first, x.second);
+      cudaFree(x.first);
+    }
   }
   double* get(size_t n) {
     double* x = nullptr;
-    CK(cudaMalloc(&x, sizeof(double) * std::max<size_t>(n, 1)));
-    p.push_back(x);
+    const size_t bytes = sizeof(double) * std::max<size_t>(n, 1);
+    CK(cudaMalloc(&x, bytes));
+    registry().add(x, bytes);
+    p.push_back({x, bytes});
     return x;
   }
 };
@@ -284,9 +297,11 @@ struct Blas1 {
   explicit Blas1(cudaStream_t s_) : s(s_) {
     st.stream = s;
     CK(cudaMalloc(&d_out, sizeof(double) * 64));
+    registry().add(d_out, sizeof(double) * 64);
     CK(cudaMallocHost(&h_out, sizeof(double) * 64));
   }
   ~Blas1() {
+    registry().remove_range(d_out, sizeof(double) * 64);
     cudaFree(d_out);
     cudaFreeHost(h_out);
   }
