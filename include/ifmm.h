@@ -53,10 +53,17 @@ typedef struct ifmm_fact ifmm_fact; /* opaque, library-owned: the factor's block
 
 /* Matrix entries: A_ij = scale/|x_i - x_j| for i != j, A_ii = diag.
  * The collocation BEM system of the paper's electrostatic example (Sec. 2) with
- * area weight 4pi/N has scale = 1/N and diag = 0.5 + 1/sqrt(N). */
+ * area weight 4pi/N has scale = 1/N and diag = 0.5 + 1/sqrt(N).
+ * arith selects how bem_matvec / bem_gmres sum the direct interactions:
+ * IFMM_ARITH_FP64 (plain FP64) or IFMM_ARITH_DF (pairs of floats with
+ * error-free transformations: FP64-level accuracy, about 1e-13 relative per
+ * interaction on well-separated points, at FP32 throughput). */
+enum { IFMM_ARITH_FP64 = 0, IFMM_ARITH_DF = 1 };
 typedef struct {
   double scale;
   double diag;
+  int arith;
+  int reserved;
 } ifmm_kernel;
 
 enum { IFMM_PREC_FP64 = 0, IFMM_PREC_FP32 = 1, IFMM_PREC_BF16 = 2 };
@@ -131,6 +138,17 @@ ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64
  * gives the name of entry `index` (NULL when out of range). */
 ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count);
 const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
+
+/* Kernel profiling of this process (no counterpart in the paper): ifmm_profile
+ * resets the per-kernel counters and, if timing != 0, brackets every later kernel
+ * launch (or solve graph launch) with CUDA events on its stream.  Timing adds
+ * event records between launches; leave it off for production runs. */
+ifmm_status ifmm_profile(int timing);
+
+/* Counter `index` (0..): kernel name, kernels launched so far (a solve graph
+ * counts its kernels), and summed event time in ms (0 unless timing).
+ * IFMM_EINVAL past the last counter.  Synchronizes with the timed events. */
+ifmm_status ifmm_profile_query(int index, const char** name, int64_t* launches, double* ms);
 
 void ifmm_tree_free(ifmm_tree* t);
 void ifmm_fact_free(ifmm_fact* f);

@@ -52,6 +52,7 @@ struct ifmm_tree {
   // device copies
   double* d_pts = nullptr;    // SoA: x[N], y[N], z[N] in tree order
   int32_t* d_perm = nullptr;  // tree order -> caller index
+  float* d_pts_df = nullptr;  // points as float pairs: xh xl yh yl zh zl [N] each
   int device = -1;
   void ensure_device();
   ~ifmm_tree();

@@ -404,6 +404,258 @@ __global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
   if (threadIdx.x == 0 && D.sweeps) D.sweeps[0] = sweep;
 }
 
+// ---------------------------------------------------------------- pivoted QR (truncated)
+// One CTA per matrix.  Column norms live in shared memory and are downdated
+// after each step (recomputed when cancellation has eaten two digits).
+// Dynamic shared memory: 2n doubles + n ints.
+template <typename TC>
+__global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const QrcpDesc D = d[blockIdx.x];
+  const int m = D.m, n = D.n;
+  const long ld = D.ld;
+  double* A = D.A;
+  extern __shared__ double sm[];
+  double* nrm = sm;
+  double* ref = sm + n;
+  int* jp = (int*)(sm + 2 * n);
+  __shared__ double scratch[32];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double s_tau2, s_alpha, s_tau, s_scale;
+  __shared__ int s_p, s_stop;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int j = w; j < n; j += nw) {
+    const double* c = A + (long)j * ld;
+    double ss = 0.0;
+    for (int i = lane; i < m; i += 32) ss += c[i] * c[i];
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      nrm[j] = ss;
+      ref[j] = ss;
+      jp[j] = j;
+    }
+  }
+  __syncthreads();
+  const int kmax = m < n ? m : n;
+  int k = 0;
+  for (; k < kmax; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
+      const double v = nrm[j];
+      if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[w] = best; red_i[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bv = -1.0;
+      int b = n;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < b)) { bv = red_v[i]; b = red_i[i]; }
+      if (k == 0) s_tau2 = D.tau_rel * D.tau_rel * bv;
+      s_stop = !(bv > s_tau2) || !(bv > 0.0) || b >= n;
+      s_p = b;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != k) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double t = A[i + k * ld];
+        A[i + k * ld] = A[i + p * ld];
+        A[i + p * ld] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = nrm[k]; nrm[k] = nrm[p]; nrm[p] = t;
+        t = ref[k]; ref[k] = ref[p]; ref[p] = t;
+        const int q = jp[k]; jp[k] = jp[p]; jp[p] = q;
+      }
+    }
+    __syncthreads();
+    double* x = A + k + k * ld;
+    const int len = m - k;
+    double ss = 0.0;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) ss += x[i] * x[i];
+    ss = block_sum(ss, scratch);
+    if (threadIdx.x == 0) {
+      const double x0 = x[0];
+      const double nr = sqrt(x0 * x0 + ss);
+      if (nr == 0.0 || ss == 0.0) {
+        s_alpha = x0;
+        s_tau = 0.0;
+      } else {
+        const double alpha = (x0 >= 0.0) ? -nr : nr;
+        s_alpha = alpha;
+        s_tau = (alpha - x0) / alpha;
+        s_scale = 1.0 / (x0 - alpha);
+      }
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    if (tau != 0.0) {
+      const double sc = s_scale;
+      for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] *= sc;
+      __syncthreads();
+    }
+    const TC t = (TC)tau;
+    for (int j = k + 1 + w; j < n; j += nw) {
+      double* y = A + k + (long)j * ld;
+      if (tau != 0.0) {
+        TC dot = (lane == 0) ? (TC)y[0] : (TC)0;
+        for (int i = 1 + lane; i < len; i += 32) dot += (TC)x[i] * (TC)y[i];
+        dot = warp_sum_t<TC>(dot) * t;
+        for (int i = 1 + lane; i < len; i += 32) y[i] = (double)((TC)y[i] - dot * (TC)x[i]);
+        if (lane == 0) y[0] = (double)((TC)y[0] - dot);
+      }
+      __syncwarp();
+      const double rkj = y[0];
+      int recompute = 0;
+      if (lane == 0) {
+        const double v = nrm[j] - rkj * rkj;
+        recompute = !(v > 1e-2 * ref[j]);
+        nrm[j] = v;
+      }
+      recompute = __shfl_sync(0xffffffffu, recompute, 0);
+      if (recompute) {
+        double s2 = 0.0;
+        for (int i = 1 + lane; i < len; i += 32) s2 += y[i] * y[i];
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+          nrm[j] = s2;
+          ref[j] = s2;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) x[0] = s_alpha;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) D.jpvt[j] = jp[j];
+  if (threadIdx.x == 0) D.kout[0] = k;
+}
+
+// ---------------------------------------------------------------- Jacobi on P R_k^T
+// B (n x k, column-major, ld n) lives in dynamic shared memory when it fits in
+// smem_bytes, else in the descriptor's global work buffer.  Columns are rotated
+// in place (no rotation matrix is accumulated: the rotated columns themselves,
+// normalised, are the singular vectors sought).  n <= 1024.
+template <typename TC>
+__global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps, int smem_bytes) {
+  if ((int)blockIdx.x >= nd) return;
+  const SvdRtDesc D = d[blockIdx.x];
+  const int n = D.n;
+  int k = D.kin[0];
+  k = k < 0 ? 0 : (k > n ? n : k);
+  extern __shared__ double smraw[];
+  __shared__ double nrm[1024];
+  __shared__ int ord[1024];
+  __shared__ double s_gmax[32];
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const bool in_smem = (size_t)n * k * sizeof(TC) <= (size_t)smem_bytes;
+  TC* B = in_smem ? (TC*)smraw : (TC*)D.work;
+  const long ld = D.ld;
+  double gmax = 0.0;
+  for (long e = threadIdx.x; e < (long)n * k; e += blockDim.x) {
+    const int pos = (int)(e % n), i = (int)(e / n);
+    const double v = (i <= pos) ? D.A[i + pos * ld] : 0.0;
+    B[D.jpvt[pos] + (long)i * n] = (TC)v;
+    const double a = fabs(v);
+    gmax = (a > gmax || a != a) ? a : gmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, gmax, o);
+    gmax = (ov > gmax || ov != ov) ? ov : gmax;
+  }
+  if (lane == 0) s_gmax[w] = gmax;
+  __syncthreads();
+  gmax = 0.0;
+  for (int i = 0; i < nw; ++i) gmax = (s_gmax[i] > gmax || s_gmax[i] != s_gmax[i]) ? s_gmax[i] : gmax;
+  const double gscale = (gmax > 0.0 && gmax < 1e300) ? 1.0 / gmax : 1.0;
+  for (long e = threadIdx.x; e < (long)n * k; e += blockDim.x) B[e] = (TC)((double)B[e] * gscale);
+  __syncthreads();
+  const TC tol = sizeof(TC) == 8 ? (TC)1e-15 : (TC)4e-7;
+  const TC tiny = sizeof(TC) == 8 ? (TC)1e-300 : (TC)1e-36;
+  const int kp = k + (k & 1);
+  for (int sweep = 0; sweep < max_sweeps && k > 1; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < kp - 1; ++r) {
+      for (int pi = w; pi < kp / 2; pi += nw) {
+        const int pa = pi, pb = kp - 1 - pi;
+        int a = (pa == 0) ? 0 : 1 + ((pa - 1 - r) % (kp - 1) + (kp - 1)) % (kp - 1);
+        int b = (pb == 0) ? 0 : 1 + ((pb - 1 - r) % (kp - 1) + (kp - 1)) % (kp - 1);
+        if (a >= k || b >= k) continue;
+        if (a > b) { const int tt = a; a = b; b = tt; }
+        TC* ga = B + (long)a * n;
+        TC* gb = B + (long)b * n;
+        TC al = 0, be = 0, gab = 0;
+        for (int i = lane; i < n; i += 32) {
+          const TC u = ga[i], v = gb[i];
+          al += u * u;
+          be += v * v;
+          gab += u * v;
+        }
+        al = warp_sum_t<TC>(al);
+        be = warp_sum_t<TC>(be);
+        gab = warp_sum_t<TC>(gab);
+        if (al < tiny || be < tiny) continue;
+        if (fabs(gab) <= tol * sqrt(al) * sqrt(be)) continue;
+        const TC zeta = (be - al) / ((TC)2 * gab);
+        const TC t = (zeta >= (TC)0 ? (TC)1 : (TC)-1) / (fabs(zeta) + hypot((TC)1, zeta));
+        const TC c = (TC)1 / sqrt((TC)1 + t * t), s = c * t;
+        for (int i = lane; i < n; i += 32) {
+          const TC u = ga[i], v = gb[i];
+          ga[i] = c * u - s * v;
+          gb[i] = s * u + c * v;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int rotated = s_rot;
+    __syncthreads();
+    if (!rotated) break;
+  }
+  for (int j = w; j < k; j += nw) {
+    const TC* g = B + (long)j * n;
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += (double)g[i] * (double)g[i];
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[j] = sqrt(s2);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    int rank = 0;
+    const double v = (nrm[j] == nrm[j]) ? nrm[j] : -1.0;
+    for (int q = 0; q < k; ++q) {
+      const double u = (nrm[q] == nrm[q]) ? nrm[q] : -1.0;
+      rank += (u > v) || (u == v && q < j);
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = (j < k) ? nrm[ord[j]] / gscale : 0.0;
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    double v = 0.0;
+    if (j < k) {
+      const double s2 = nrm[ord[j]];
+      v = (s2 > 0.0) ? (double)B[i + (long)ord[j] * n] / s2 : 0.0;
+    }
+    D.V[i + (long)j * D.ldv] = v;
+  }
+}
+
 // ---------------------------------------------------------------- GEMV
 // y = alpha * op(A) x + beta * y.  Non-transposed: a thread per row walks the
 // columns (consecutive threads read consecutive rows of a column).  Transposed:

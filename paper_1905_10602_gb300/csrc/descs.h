@@ -75,4 +75,33 @@ struct GemvSumDesc {
   int m, first, count, pad;
   double alpha, beta;
 };
+// Householder QR with column pivoting of the m x n matrix A, stopped at the
+// first step whose largest remaining column norm is <= tau_rel times the
+// largest initial column norm.  On exit the leading kout rows of A hold R (in
+// pivoted column order, zero below the diagonal), jpvt[pos] is the original
+// index of pivoted column pos, and *kout the number of steps taken.
+struct QrcpDesc {
+  double* A;
+  int ld, m, n;
+  double tau_rel;
+  int* jpvt;
+  int* kout;
+};
+
+// Right singular vectors of Y from its truncated pivoted QR (Y P ~ Q R_k):
+// one-sided Jacobi on B = P R_k^T (n x k); the rotated, normalised columns of B
+// are the right singular vectors, their norms the singular values.  V (n x n,
+// ldv): first k columns valid, the rest zero; sig (n) likewise, descending.
+// work: n x n doubles used when B does not fit in shared memory.
+struct SvdRtDesc {
+  const double* A;
+  int ld, n;
+  const int* jpvt;
+  const int* kin;
+  double* V;
+  int ldv, pad;
+  double* sig;
+  double* work;
+};
+
 }  // namespace ifmm

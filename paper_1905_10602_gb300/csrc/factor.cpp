@@ -94,6 +94,8 @@ struct Event {
   double* Tp = nullptr;  // k x r_old
   int64_t key = 0;
   int event_no = 0;
+  size_t sig_off[2] = {0, 0};
+  int* kdev[2] = {nullptr, nullptr};
 };
 
 struct Factorizer {
@@ -141,6 +143,17 @@ struct Factorizer {
     st.reset();
   }
 
+  // Truncation threshold of the pivoted QR that precedes each SVD, relative to
+  // the largest column norm: far enough below eps (divided by sqrt(n), which
+  // bounds sigma_max of the discarded part) that the eps-rank subspace is kept
+  // to well within the FP64 parity tolerance; in FP32 about two units of
+  // roundoff.
+  double tau_rel(int n) const {
+    const double floor64 = 4.0 * std::max(n, 1) * std::ldexp(1.0, -52);
+    if (prec == P32) return std::max(0.1 * F.o.eps, 2.0 * std::ldexp(1.0, -24));
+    return std::max(F.o.eps > 0 ? 1e-4 * F.o.eps / std::sqrt((double)std::max(n, 1)) : 0.0, floor64);
+  }
+
   // ------------------------------------------------------------------ ranks
   static int kept(const std::vector<double>& sig, int avail, int rows, int cols, double eps) {
     if (avail <= 0 || sig.empty() || !(sig[0] > 0.0)) return 0;
@@ -160,10 +173,18 @@ struct Factorizer {
                   const std::vector<double*>& L2P_out, const std::vector<int>& P2M_ld, const std::vector<int>& L2P_ld,
                   std::vector<InvDesc>* inv_check, int n_inv) {
     std::vector<CopyDesc> cz, cf;
-    std::vector<QrDesc> qz, qy;
+    std::vector<QrDesc> qz;
+    std::vector<QrcpDesc> qp;
     std::vector<GemmDesc> gw;
-    std::vector<SvdDesc> sv;
-    for (auto& ev : evs) {
+    std::vector<SvdRtDesc> sr;
+    // contiguous readback buffers: singular values and truncation counts
+    size_t sig_total = 0;
+    for (auto& ev : evs) sig_total += 2 * (size_t)ev.n;
+    double* sig_all = scratch.alloc(std::max<size_t>(sig_total, 1));
+    int* kall = (int*)scratch.alloc(evs.size() + 1);
+    size_t sig_off = 0;
+    for (size_t e = 0; e < evs.size(); ++e) {
+      Event& ev = evs[e];
       const int n = ev.n, r0 = ev.r_old;
       for (int side = 0; side < 2; ++side) {
         int mz = 0;
@@ -173,13 +194,17 @@ struct Factorizer {
         ev.nominal_rows[side] = r0 + mf;
         ev.avail[side] = std::min(r0 + mf, n);
         ev.V[side] = nullptr;
-        ev.sig[side] = nullptr;
+        ev.sig[side] = sig_all + sig_off;
+        ev.sig_off[side] = sig_off;
+        sig_off += n;
+        ev.kdev[side] = kall + 2 * e + side;
         if (n == 0) continue;
         const bool pathA = (n <= r0);
         const int mw = (mz == 0 || r0 == 0) ? 0 : (pathA ? mz : std::min(mz, r0));
         const int my = mw + mf;
         if (my == 0) {
           ev.avail[side] = 0;
+          cf.push_back(cpy(nullptr, 0, ev.sig[side], n, n, 1));
           continue;
         }
         double* Z = nullptr;
@@ -206,54 +231,48 @@ struct Factorizer {
           cf.push_back(cpy(f.p, f.ld, Y + off, my, f.rows, f.cols, 1.0, 0.0, f.trans));
           off += f.rows;
         }
-        int msvd = my;
-        if (my > n) {
-          qy.push_back(QrDesc{Y, my, my, n});
-          cnt.qr += 2.0 * my * n * (double)n - 2.0 * std::pow((double)n, 3) / 3.0;
-          msvd = n;
-        }
         ev.V[side] = scratch.alloc((size_t)n * n);
-        ev.sig[side] = scratch.alloc(n);
-        double* Vw = scratch.alloc((size_t)n * n);
-        SvdDesc d;
-        d.G = Y;
-        d.V = ev.V[side];
-        d.Vw = Vw;
-        d.sig = ev.sig[side];
-        d.ldg = my;
-        d.ldv = n;
-        d.m = msvd;
-        d.n = n;
-        d.sweeps = nullptr;
-        d.pad = 0;
-        sv.push_back(d);
+        double* work = scratch.alloc((size_t)n * n);
+        int* jp = (int*)scratch.alloc((size_t)n / 2 + 1);
+        qp.push_back(QrcpDesc{Y, my, my, n, tau_rel(n), jp, ev.kdev[side]});
+        SvdRtDesc sd;
+        sd.A = Y;
+        sd.ld = my;
+        sd.n = n;
+        sd.jpvt = jp;
+        sd.kin = ev.kdev[side];
+        sd.V = ev.V[side];
+        sd.ldv = n;
+        sd.pad = 0;
+        sd.sig = ev.sig[side];
+        sd.work = work;
+        sr.push_back(sd);
+        const double mm = std::max(my, n), nn = std::min(my, n);
+        cnt.qr += 2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0;
         cnt.svd += 6.0 * std::max(ev.nominal_rows[side], n) * std::pow((double)std::min(ev.nominal_rows[side], n), 2) +
                    20.0 * std::pow((double)std::min(ev.nominal_rows[side], n), 3);
       }
     }
+    CK(cudaMemsetAsync(kall, 0, sizeof(int) * (evs.size() * 2 + 0), s));
     launch_copy(st, cz);
     launch_qr(st, qz, prec);
     cnt.add_gemm(gw);
     launch_gemm(st, gw, prec);
     launch_copy(st, cf);
-    launch_qr(st, qy, prec);
-    launch_svd(st, sv, prec);
-    // read back singular values (and pivot status)
-    size_t total = 0;
-    for (auto& ev : evs)
-      for (int side = 0; side < 2; ++side)
-        if (ev.sig[side]) total += ev.n;
-    std::vector<double> hsig(total);
+    launch_qrcp(st, qp, prec);
+    launch_svd_rt(st, sr, prec);
+    // read back singular values, truncation counts and pivot status
+    std::vector<double> hsig(sig_total);
+    std::vector<int> hk(2 * evs.size(), 0);
     double* hp = nullptr;
-    if (total) {
-      hp = (double*)st.host_alloc(total * sizeof(double));
-      size_t o = 0;
-      for (auto& ev : evs)
-        for (int side = 0; side < 2; ++side)
-          if (ev.sig[side]) {
-            CK(cudaMemcpyAsync(hp + o, ev.sig[side], sizeof(double) * ev.n, cudaMemcpyDeviceToHost, s));
-            o += ev.n;
-          }
+    int* hkp = nullptr;
+    if (sig_total) {
+      hp = (double*)st.host_alloc(sig_total * sizeof(double));
+      CK(cudaMemcpyAsync(hp, sig_all, sizeof(double) * sig_total, cudaMemcpyDeviceToHost, s));
+    }
+    if (!evs.empty()) {
+      hkp = (int*)st.host_alloc(sizeof(int) * 2 * evs.size());
+      CK(cudaMemcpyAsync(hkp, kall, sizeof(int) * 2 * evs.size(), cudaMemcpyDeviceToHost, s));
     }
     std::vector<int> hinfo(n_inv, 0);
     int* hi = nullptr;
@@ -262,21 +281,21 @@ struct Factorizer {
       CK(cudaMemcpyAsync(hi, d_info, sizeof(int) * n_inv, cudaMemcpyDeviceToHost, s));
     }
     wait();
-    if (total) memcpy(hsig.data(), hp, total * sizeof(double));
+    if (sig_total) memcpy(hsig.data(), hp, sig_total * sizeof(double));
+    if (!evs.empty()) memcpy(hk.data(), hkp, sizeof(int) * 2 * evs.size());
     if (n_inv) memcpy(hinfo.data(), hi, sizeof(int) * n_inv);
     st.reset();
     for (int i = 0; i < n_inv; ++i)
       IFMM_REQUIRE(hinfo[i] == 0, IFMM_ESINGULAR, "singular pivot block at level " + std::to_string(W.kappa));
     (void)inv_check;
+    for (size_t e = 0; e < evs.size(); ++e)
+      for (int side = 0; side < 2; ++side)
+        if (evs[e].V[side]) evs[e].avail[side] = std::min(evs[e].avail[side], hk[2 * e + side]);
     // choose ranks (max of the row and column counts, both sides share it)
-    size_t o = 0;
     for (auto& ev : evs) {
       std::vector<double> sg[2];
       for (int side = 0; side < 2; ++side)
-        if (ev.sig[side]) {
-          sg[side].assign(hsig.begin() + o, hsig.begin() + o + ev.n);
-          o += ev.n;
-        }
+        if (ev.V[side]) sg[side].assign(hsig.begin() + ev.sig_off[side], hsig.begin() + ev.sig_off[side] + ev.n);
       const int kr = kept(sg[0], ev.avail[0], ev.nominal_rows[0], ev.n, F.o.eps);
       const int kc = kept(sg[1], ev.avail[1], ev.nominal_rows[1], ev.n, F.o.eps);
       int k = std::min(std::max(kr, kc), std::min(ev.avail[0], ev.avail[1]));

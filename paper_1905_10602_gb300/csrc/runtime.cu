@@ -61,6 +61,51 @@ static void check_gemm(const std::vector<GemmDesc>& v) {
   }
 }
 
+static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "gauss_jordan", "qr_fp64", "qr_fp32",
+                                           "svd_fp64", "svd_fp32", "gemv", "gemv_sum", "p2p", "interp", "tables",
+                                           "matvec", "permute", "gauss_jordan_big", "solve_graph"};
+const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+cudaEvent_t Profiler::begin(int kind, cudaStream_t s, long count) {
+  launches[kind] += count;
+  if (!timing) return nullptr;
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(e, s));
+  return e;
+}
+void Profiler::end(int kind, cudaStream_t s, cudaEvent_t b) {
+  if (!timing || !b) return;
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(e, s));
+  pending.push_back({kind, {b, e}});
+  if (pending.size() > 4096) collect();
+}
+void Profiler::collect() {
+  for (auto& p : pending) {
+    CK(cudaEventSynchronize(p.second.second));
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, p.second.first, p.second.second));
+    ms[p.first] += t;
+    events_kernels[p.first] += 1;
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  pending.clear();
+}
+void Profiler::reset() {
+  collect();
+  for (int k = 0; k < KK_COUNT; ++k) {
+    launches[k] = 0;
+    events_kernels[k] = 0;
+    ms[k] = 0;
+  }
+}
+
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(IFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -71,8 +116,10 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
   check_copy(v);
   const CopyDesc* d = st.push(v);
+  cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
   k_copy<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_copy");
+  profiler().end(KK_COPY, st.stream, pe);
 }
 
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
@@ -89,11 +136,14 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
   // descriptor whose start <= tile, and empty ones share their start with the next
   const GemmDesc* d = st.push(v);
   const int* p = st.push(tp);
+  const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
     k_gemm<float><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
   else
     k_gemm<double><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
   check_launch("k_gemm");
+  profiler().end(kk, st.stream, pe);
 }
 
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
@@ -112,8 +162,10 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     req(v[i].info, sizeof(int), "inv.info", i);
   }
   const InvDesc* d = st.push(v);
+  cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
   k_inv<<<(unsigned)v.size(), 256, smem, st.stream>>>(d, (int)v.size());
   check_launch("k_inv");
+  profiler().end(KK_INV, st.stream, pe);
 }
 
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
@@ -123,11 +175,14 @@ void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qr ld too small");
   }
   const QrDesc* d = st.push(v);
+  const int kk = prec == P32 ? KK_QR32 : KK_QR64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
     k_qr<float><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
   else
     k_qr<double><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_qr");
+  profiler().end(kk, st.stream, pe);
 }
 
 void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
@@ -150,11 +205,73 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
     if (x.ldg < x.m || x.ldv < x.n) throw Error(IFMM_EINVAL, "svd ld too small");
   }
   const SvdDesc* d = st.push(v);
+  const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
     k_svd<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
   else
     k_svd<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
   check_launch("k_svd");
+  profiler().end(kk, st.stream, pe);
+}
+
+void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
+  if (v.empty()) return;
+  int nmax = 0;
+  for (auto& x : v) nmax = std::max(nmax, x.n);
+  const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
+  IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivoted QR too wide");
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_qrcp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CK(cudaFuncSetAttribute(k_qrcp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  for (size_t i = 0; i < v.size() && registry().on; ++i) {
+    req(v[i].A, span(v[i].m, v[i].n, v[i].ld), "qrcp.A", i);
+    req(v[i].jpvt, sizeof(int) * v[i].n, "qrcp.jpvt", i);
+    req(v[i].kout, sizeof(int), "qrcp.kout", i);
+    if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qrcp ld too small");
+  }
+  const QrcpDesc* d = st.push(v);
+  const int kk = prec == P32 ? KK_QR32 : KK_QR64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
+  if (prec == P32)
+    k_qrcp<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size());
+  else
+    k_qrcp<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size());
+  check_launch("k_qrcp");
+  profiler().end(kk, st.stream, pe);
+}
+
+void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
+  if (v.empty()) return;
+  const int smem = 160 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_svd_rt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_svd_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  for (size_t i = 0; i < v.size(); ++i) {
+    IFMM_REQUIRE(v[i].n <= 1024, IFMM_EINVAL, "SVD wider than 1024 columns");
+    if (!registry().on) continue;
+    const SvdRtDesc& x = v[i];
+    req(x.A, span(x.n, x.n, x.ld) > 0 ? sizeof(double) : 0, "svd_rt.A", i);
+    req(x.jpvt, sizeof(int) * x.n, "svd_rt.jpvt", i);
+    req(x.V, span(x.n, x.n, x.ldv), "svd_rt.V", i);
+    req(x.sig, sizeof(double) * x.n, "svd_rt.sig", i);
+    req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
+  }
+  const SvdRtDesc* d = st.push(v);
+  const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
+  if (prec == P32)
+    k_svd_rt<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60, smem);
+  else
+    k_svd_rt<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60, smem);
+  check_launch("k_svd_rt");
+  profiler().end(kk, st.stream, pe);
 }
 
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
@@ -166,8 +283,10 @@ void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
     req(x.y, sizeof(double) * (x.trans ? x.n : x.m), "gemv.y", i);
   }
   const GemvDesc* d = st.push(v);
+  cudaEvent_t pe = profiler().begin(KK_GEMV, st.stream);
   k_gemv<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_gemv");
+  profiler().end(KK_GEMV, st.stream, pe);
 }
 
 // ------------------------------------------------------------------ IFMM kernels
@@ -302,6 +421,113 @@ __global__ void __launch_bounds__(256) k_matvec(const double* __restrict__ px, c
   if (i < n) y[i] = diag * x[i] + scale * acc;
 }
 
+// ---------------------------------------------------------------- double-float matvec
+// The same sum with every quantity carried as an unevaluated pair of floats
+// (hi + lo, ~48-bit significand) and error-free transformations on FP32 FMAs
+// (Knuth's two-sum, FMA two-product, Dekker's renormalisation); 1/sqrt(r^2)
+// from rsqrtf refined by one Newton step in pair arithmetic.  FP64-level
+// accuracy at FP32 throughput.
+struct df {
+  float h, l;
+};
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_quick(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.h, b.h);
+  return df_quick(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ df df_sub(df a, df b) {
+  df s = df_two_sum(a.h, -b.h);
+  return df_quick(s.h, s.l + (a.l - b.l));
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p);
+  return df_quick(p, e + (a.h * b.l + a.l * b.h));
+}
+__device__ __forceinline__ df df_rsqrt(df x) {
+  const float y0 = rsqrtf(x.h);
+  const df yy = df_mul({y0, 0.f}, {y0, 0.f});
+  const df t = df_mul(x, yy);
+  const df e = df_sub({1.f, 0.f}, t);
+  return df_add({y0, 0.f}, df_mul({0.5f * y0, 0.f}, e));
+}
+
+__global__ void k_split_df(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = in[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
+
+// pts: 6 float arrays (xh, xl, yh, yl, zh, zl) of length n; q: (qh, ql)
+__global__ void __launch_bounds__(256) k_matvec_df(const float* __restrict__ pts, const float* __restrict__ qh,
+                                                   const float* __restrict__ ql, const double* __restrict__ x,
+                                                   double* __restrict__ y, int n, double scale, double diag) {
+  __shared__ float s[8][256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* xh = pts;
+  const float* xl = pts + n;
+  const float* yh = pts + 2 * (long)n;
+  const float* yl = pts + 3 * (long)n;
+  const float* zh = pts + 4 * (long)n;
+  const float* zl = pts + 5 * (long)n;
+  df px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
+  if (i < n) {
+    px = {xh[i], xl[i]};
+    py = {yh[i], yl[i]};
+    pz = {zh[i], zl[i]};
+  }
+  df acc = {0.f, 0.f};
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    if (j < n) {
+      s[0][threadIdx.x] = xh[j];
+      s[1][threadIdx.x] = xl[j];
+      s[2][threadIdx.x] = yh[j];
+      s[3][threadIdx.x] = yl[j];
+      s[4][threadIdx.x] = zh[j];
+      s[5][threadIdx.x] = zl[j];
+      s[6][threadIdx.x] = qh[j];
+      s[7][threadIdx.x] = ql[j];
+    }
+    __syncthreads();
+    const int cnt = min((int)blockDim.x, n - j0);
+    for (int t = 0; t < cnt; ++t) {
+      const df dx = df_sub(px, {s[0][t], s[1][t]});
+      const df dy = df_sub(py, {s[2][t], s[3][t]});
+      const df dz = df_sub(pz, {s[4][t], s[5][t]});
+      const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+      if (j0 + t != i) acc = df_add(acc, df_mul({s[6][t], s[7][t]}, df_rsqrt(r2)));
+    }
+    __syncthreads();
+  }
+  if (i < n) y[i] = diag * x[i] + scale * ((double)acc.h + (double)acc.l);
+}
+
+void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n) {
+  k_split_df<<<(n + 255) / 256, 256, 0, s>>>(in, hi, lo, n);
+  check_launch("k_split_df");
+}
+
+void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
+                      int N, double scale, double diag) {
+  cudaEvent_t pe = profiler().begin(KK_MATVEC, s);
+  k_matvec_df<<<(N + 255) / 256, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  check_launch("k_matvec_df");
+  profiler().end(KK_MATVEC, s, pe);
+}
+
 __global__ void k_gather_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
                               int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,12 +627,14 @@ void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, doub
   // d_work_int: n ints (pivots); d_work: 2n doubles; d_info: 1 int (zeroed here)
   CK(cudaMemsetAsync(d_info, 0, sizeof(int), s));
   const int upd_blocks = (int)std::min<long>(152L * 8, ((long)n * n + 255) / 256);
+  cudaEvent_t pe = profiler().begin(KK_GJ_BIG, s, 2L * n + 1);
   for (int k = 0; k < n; ++k) {
     k_gj_pivot<<<1, 1024, 0, s>>>(A, ld, n, k, d_work_int, d_work, d_work + n, d_info);
     k_gj_update<<<upd_blocks, 256, 0, s>>>(A, ld, n, k, d_work, d_work + n, d_info);
   }
   k_gj_colswap<<<1, 1024, 0, s>>>(A, ld, n, d_work_int, d_info);
   check_launch("big_inverse");
+  profiler().end(KK_GJ_BIG, s, pe);
 }
 
 void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag) {
@@ -417,6 +645,7 @@ void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts,
       throw Error(IFMM_EINVAL, "p2p point range");
   }
   const P2pDesc* d = st.push(v);
+  profiler().launches[KK_P2P] += 1;
   k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
   check_launch("k_p2p");
 }
@@ -428,30 +657,37 @@ void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double
     if (v[i].p0 < 0 || v[i].p0 + v[i].n > N) throw Error(IFMM_EINVAL, "interp point range");
   }
   const InterpDesc* d = st.push(v);
+  profiler().launches[KK_INTERP] += 1;
   k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
   check_launch("k_interp");
 }
 
 void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale) {
+  profiler().launches[KK_TABLES] += 1;
   k_m2l_table<<<343, 256, 0, s>>>(out, p, h, scale);
   check_launch("k_m2l_table");
 }
 
 void launch_m2m_table(cudaStream_t s, double* out, int p) {
+  profiler().launches[KK_TABLES] += 1;
   k_m2m_table<<<8, 256, 0, s>>>(out, p);
   check_launch("k_m2m_table");
 }
 
 void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag) {
+  cudaEvent_t pe = profiler().begin(KK_MATVEC, s);
   k_matvec<<<(N + 255) / 256, 256, 0, s>>>(pts, pts + N, pts + 2 * (long)N, x, y, N, scale, diag);
   check_launch("k_matvec");
+  profiler().end(KK_MATVEC, s, pe);
 }
 
 void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+  profiler().launches[KK_PERM] += 1;
   k_gather_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
   check_launch("k_gather_perm");
 }
 void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+  profiler().launches[KK_PERM] += 1;
   k_scatter_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
   check_launch("k_scatter_perm");
 }
@@ -469,4 +705,34 @@ void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t
 
 }  // namespace ifmm
 
-extern "C" const char* ifmm_last_error(void) { return ifmm::last_error(); }
+extern "C" {
+const char* ifmm_last_error(void) { return ifmm::last_error(); }
+
+ifmm_status ifmm_profile(int timing) {
+  try {
+    ifmm::profiler().reset();
+    ifmm::profiler().timing = timing != 0;
+    return IFMM_OK;
+  } catch (const ifmm::Error& e) {
+    ifmm::set_last_error(e.what());
+    return e.code;
+  }
+}
+
+ifmm_status ifmm_profile_query(int index, const char** name, int64_t* launches, double* ms) {
+  try {
+    if (index < 0 || index >= ifmm::KK_COUNT) {
+      ifmm::set_last_error("profile index out of range");
+      return IFMM_EINVAL;
+    }
+    ifmm::profiler().collect();
+    if (name) *name = ifmm::kernel_kind_name(index);
+    if (launches) *launches = ifmm::profiler().launches[index];
+    if (ms) *ms = ifmm::profiler().ms[index];
+    return IFMM_OK;
+  } catch (const ifmm::Error& e) {
+    ifmm::set_last_error(e.what());
+    return e.code;
+  }
+}
+}

@@ -165,12 +165,34 @@ struct DescStage {
 
 enum Prec { P64 = 0, P32 = 1 };
 
+// Per-kernel launch counts and (when enabled) CUDA-event durations measured on
+// the launching stream around every launch.
+enum KernelKind {
+  KK_COPY = 0, KK_GEMM64, KK_GEMM32, KK_INV, KK_QR64, KK_QR32, KK_SVD64, KK_SVD32, KK_GEMV, KK_GEMV_SUM, KK_P2P,
+  KK_INTERP, KK_TABLES, KK_MATVEC, KK_PERM, KK_GJ_BIG, KK_SOLVE_GRAPH, KK_COUNT
+};
+struct Profiler {
+  bool timing = false;
+  long launches[KK_COUNT] = {0};
+  long events_kernels[KK_COUNT] = {0};
+  double ms[KK_COUNT] = {0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  cudaEvent_t begin(int kind, cudaStream_t s, long count = 1);
+  void end(int kind, cudaStream_t s, cudaEvent_t b);
+  void collect();  // synchronizes pending events and accumulates
+  void reset();
+};
+Profiler& profiler();
+const char* kernel_kind_name(int k);
+
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec);
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v);
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec);
 void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec);
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v);
+void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec);
+void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec);
 void check_launch(const char* what);
 
 inline CopyDesc cpy(const double* src, int lds, double* dst, int ldd, int rows, int cols, double alpha = 1.0,

@@ -222,7 +222,9 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
   const SolvePlan& P = F.plan;
   const int64_t N = F.t->N;
   CK(cudaMemcpyAsync(P.stage_in, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t pe = profiler().begin(KK_SOLVE_GRAPH, s, (long)P.prog.size());
   CK(cudaGraphLaunch(P.graph, s));
+  profiler().end(KK_SOLVE_GRAPH, s, pe);
   CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
 
@@ -254,8 +256,19 @@ void ifmm_tree::ensure_device() {
   CK(cudaMemcpy(d_pts, soa.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
   CK(cudaMalloc(&d_perm, sizeof(int32_t) * N));
   CK(cudaMemcpy(d_perm, perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  std::vector<float> dfp(6 * (size_t)N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int d = 0; d < 3; ++d) {
+      const double v = pts[3 * i + d];
+      const float h = (float)v;
+      dfp[(size_t)(2 * d) * N + i] = h;
+      dfp[(size_t)(2 * d + 1) * N + i] = (float)(v - (double)h);
+    }
+  CK(cudaMalloc(&d_pts_df, sizeof(float) * 6 * N));
+  CK(cudaMemcpy(d_pts_df, dfp.data(), sizeof(float) * 6 * N, cudaMemcpyHostToDevice));
   registry().add(d_pts, sizeof(double) * 3 * N);
   registry().add(d_perm, sizeof(int32_t) * N);
+  registry().add(d_pts_df, sizeof(float) * 6 * N);
 }
 
 ifmm_tree::~ifmm_tree() {
@@ -266,6 +279,10 @@ ifmm_tree::~ifmm_tree() {
   if (d_perm) {
     registry().remove_range(d_perm, sizeof(int32_t) * N);
     cudaFree(d_perm);
+  }
+  if (d_pts_df) {
+    registry().remove_range(d_pts_df, sizeof(float) * 6 * N);
+    cudaFree(d_pts_df);
   }
 }
 
@@ -367,7 +384,13 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       src = c;
     }
     launch_gather_perm(s, src, t->d_perm, a, (int)N);
-    launch_matvec(s, t->d_pts, (int)N, a, b, k->scale, k->diag);
+    if (k->arith == IFMM_ARITH_DF) {
+      float* q = (float*)V.get(N);
+      launch_split_df(s, a, q, q + N, (int)N);
+      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag);
+    } else {
+      launch_matvec(s, t->d_pts, (int)N, a, b, k->scale, k->diag);
+    }
     if (dev) {
       launch_scatter_perm(s, b, t->d_perm, y, (int)N);
     } else {
@@ -429,7 +452,16 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
       if (pre) run_solve_tree(*pre, in, out, s);
       else CK(cudaMemcpyAsync(out, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     };
-    auto Amul = [&](const double* in, double* out) { launch_matvec(s, t->d_pts, (int)N, in, out, k->scale, k->diag); };
+    const bool df_mv = k->arith == IFMM_ARITH_DF;
+    float* qdf = df_mv ? (float*)Vm.get(N) : nullptr;
+    auto Amul = [&](const double* in, double* out) {
+      if (df_mv) {
+        launch_split_df(s, in, qdf, qdf + N, (int)N);
+        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag);
+      } else {
+        launch_matvec(s, t->d_pts, (int)N, in, out, k->scale, k->diag);
+      }
+    };
     CK(cudaMemsetAsync(xt, 0, sizeof(double) * N, s));
     CK(cudaMemcpyAsync(rt, bt, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     const double bnorm = std::sqrt(dot(bt, bt));

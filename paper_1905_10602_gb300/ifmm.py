@@ -32,7 +32,8 @@ class IFMMError(RuntimeError):
 
 
 class Kernel(ctypes.Structure):
-    _fields_ = [("scale", ctypes.c_double), ("diag", ctypes.c_double)]
+    _fields_ = [("scale", ctypes.c_double), ("diag", ctypes.c_double), ("arith", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -58,6 +59,11 @@ _sig = {
 for _name, _args in _sig.items():
     getattr(lib, _name).argtypes = _args
     getattr(lib, _name).restype = ctypes.c_int
+lib.ifmm_profile.argtypes = [ctypes.c_int]
+lib.ifmm_profile.restype = ctypes.c_int
+lib.ifmm_profile_query.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i64),
+                                   ctypes.POINTER(_dbl)]
+lib.ifmm_profile_query.restype = ctypes.c_int
 lib.ifmm_fact_stat_name.argtypes = [_vp, _i64]
 lib.ifmm_fact_stat_name.restype = ctypes.c_char_p
 lib.ifmm_last_error.argtypes = []
@@ -67,7 +73,8 @@ lib.ifmm_tree_free.restype = None
 lib.ifmm_fact_free.argtypes = [_vp]
 lib.ifmm_fact_free.restype = None
 
-EXPORTED = sorted(list(_sig) + ["ifmm_fact_stat_name", "ifmm_last_error", "ifmm_tree_free", "ifmm_fact_free"])
+EXPORTED = sorted(list(_sig) + ["ifmm_fact_stat_name", "ifmm_last_error", "ifmm_tree_free", "ifmm_fact_free",
+                                 "ifmm_profile", "ifmm_profile_query"])
 
 
 def _check(code):
@@ -96,9 +103,13 @@ def _stream(x=None):
     return ctypes.c_void_p(0)
 
 
-def default_kernel(n):
-    """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N)."""
-    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n))
+ARITH = {"fp64": 0, "df": 1}
+
+
+def default_kernel(n, arith: str = "fp64"):
+    """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N); arith: matvec sums in
+    plain FP64 or in FP64-accurate float pairs ("df")."""
+    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n), ARITH[arith], 0)
 
 
 class Tree:
@@ -225,3 +236,20 @@ def ifmm_fact_stats(fact: Fact) -> dict:
     buf = np.zeros(cnt.value, dtype=np.float64)
     _check(lib.ifmm_fact_stats(fact.h, buf.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt)))
     return {lib.ifmm_fact_stat_name(fact.h, i).decode(): float(buf[i]) for i in range(cnt.value)}
+
+
+def ifmm_profile(timing: bool = True) -> None:
+    _check(lib.ifmm_profile(1 if timing else 0))
+
+
+def ifmm_profile_query() -> dict:
+    """{kernel name: (launches, milliseconds)} since the last ifmm_profile()."""
+    out = {}
+    i = 0
+    while True:
+        name, n, ms = ctypes.c_char_p(), _i64(), _dbl()
+        if lib.ifmm_profile_query(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)) != 0:
+            break
+        out[name.value.decode()] = (int(n.value), float(ms.value))
+        i += 1
+    return out

@@ -141,3 +141,21 @@ def test_empty_interaction_lists_small_tree():
     t, f = _gpu(pts, 2, 2, 0.0, 3)
     b = point_source_rhs(pts)
     assert _rel(ifmm.ifmm_solve(f, b), o.solve(b)) < 1e-11
+
+
+def test_matvec_double_float_accuracy():
+    """The float-pair matvec keeps FP64-level accuracy against the dense FP64 product."""
+    for pts in (fibonacci_sphere(3000, 2), bumpy_sphere(2500, 5)):
+        t = ifmm.ifmm_build_tree(pts, 3)
+        x = np.random.default_rng(1).standard_normal(len(pts))
+        y = ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(len(pts), "df"))
+        assert _rel(y, dense_matrix(pts) @ x) < 1e-12
+
+
+def test_matvec_double_float_sampled_large():
+    pts = bumpy_sphere(131072, 3)
+    t = ifmm.ifmm_build_tree(pts, 6)
+    x = np.random.default_rng(2).standard_normal(len(pts))
+    y = ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(len(pts), "df"))
+    rows = np.random.default_rng(3).choice(len(pts), 64, replace=False)
+    assert _rel(y[rows], direct_matvec(pts, x, rows)) < 1e-12
