@@ -40,6 +40,42 @@ __global__ void k_copy(const CopyDesc* __restrict__ d, int nd) {
   }
 }
 
+// ---------------------------------------------------------------- small problems
+// A warp per descriptor (8 per CTA) for blocks of at most 1024 elements.
+__global__ void k_copy_small(const CopyDesc* __restrict__ d, int nd) {
+  const int di = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (di >= nd) return;
+  const CopyDesc D = d[di];
+  const int total = D.rows * D.cols;
+  for (int e = lane; e < total; e += 32) {
+    const int i = e % D.rows, j = e / D.rows;
+    double v = 0.0;
+    if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
+    double* o = D.dst + i + (long)j * D.ldd;
+    *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
+  }
+}
+
+template <typename TC>
+__global__ void k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
+  const int di = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (di >= nd) return;
+  const GemmDesc D = d[di];
+  const int total = D.m * D.n;
+  for (int e = lane; e < total; e += 32) {
+    const int i = e % D.m, j = e / D.m;
+    TC acc = 0;
+    for (int q = 0; q < D.k; ++q) {
+      const double a = D.ta ? D.A[q + (long)i * D.lda] : D.A[i + (long)q * D.lda];
+      const double b = D.tb ? D.B[j + (long)q * D.ldb] : D.B[q + (long)j * D.ldb];
+      acc += (TC)a * (TC)b;
+    }
+    double* o = D.C + i + (long)j * D.ldc;
+    const double v = D.alpha * (double)acc;
+    *o = (D.beta == 0.0) ? v : v + D.beta * (*o);
+  }
+}
+
 // ---------------------------------------------------------------- GEMM
 // 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, K in
 // slices of 16 staged through shared memory.  TC is the arithmetic type
@@ -127,26 +163,31 @@ __device__ double block_sum(double v, double* scratch) {
 }
 
 // ---------------------------------------------------------------- Gauss-Jordan inverse
-// One CTA per matrix, in place in global memory.  Step k: pick the row of
-// largest |A(i,k)|, i >= k (ties: smallest i), swap it into row k, scale row k,
-// eliminate column k from every other row; finally undo the row interchanges
-// as column interchanges in reverse order.  Dynamic shared memory: 2n doubles
-// + n ints.
-__global__ void k_inv(const InvDesc* __restrict__ d, int nd) {
+// One CTA per matrix.  Step k: pick the row of largest |A(i,k)|, i >= k (ties:
+// smallest i), swap it into row k, scale row k, eliminate column k from every
+// other row; finally undo the row interchanges as column interchanges in
+// reverse order.  The matrix is worked on in shared memory when n*n doubles fit
+// in smem_mat bytes, else in place in global memory.  Dynamic shared memory:
+// smem_mat bytes + 2n doubles + n ints.
+__global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
   if ((int)blockIdx.x >= nd) return;
   const InvDesc D = d[blockIdx.x];
   const int n = D.n;
-  double* A = D.A;
-  const long ld = D.ld;
   extern __shared__ double sm[];
-  double* rowk = sm;
-  double* colk = sm + n;
-  int* piv = (int*)(sm + 2 * n);
+  const bool in_smem = (size_t)n * n * sizeof(double) <= (size_t)smem_mat;
+  double* A = in_smem ? sm : D.A;
+  const long ld = in_smem ? n : D.ld;
+  double* rowk = sm + smem_mat / sizeof(double);
+  double* colk = rowk + n;
+  int* piv = (int*)(colk + n);
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_p;
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
+  if (in_smem)
+    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) A[e] = D.A[(e % n) + (e / n) * (long)D.ld];
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
@@ -213,7 +254,116 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd) {
       }
     __syncthreads();
   }
+  if (in_smem)
+    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) D.A[(e % n) + (e / n) * (long)D.ld] = A[e];
   if (threadIdx.x == 0) D.info[0] = 0;
+}
+
+// Batched Gauss-Jordan for matrices too large for shared memory: one launch
+// pair per pivot step k over all matrices of the batch (k_gjb_pivot: a CTA per
+// matrix picks, swaps and scales the pivot row; k_gjb_update: a 2-D grid, one
+// row of CTAs per matrix, eliminates column k), then k_gjb_colswap.  work holds
+// 2n doubles and n ints per matrix at work_off[b].
+__global__ void k_gjb_pivot(const InvDesc* __restrict__ d, int nd, int k, double* __restrict__ work,
+                            const long* __restrict__ work_off) {
+  const int b = blockIdx.x;
+  if (b >= nd) return;
+  const InvDesc D = d[b];
+  const int n = D.n;
+  if (k >= n || D.info[0] != 0) return;
+  double* A = D.A;
+  const long ld = D.ld;
+  double* rowk = work + work_off[b];
+  double* colk = rowk + n;
+  int* piv = (int*)(colk + n);
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double best = -1.0;
+  int bi = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(A[i + k * ld]);
+    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { red_v[w] = best; red_i[w] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = -1.0;
+    int bb = n;
+    for (int i = 0; i < nw; ++i)
+      if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < bb)) { bv = red_v[i]; bb = red_i[i]; }
+    if (!(bv > 0.0) || bb >= n) {
+      D.info[0] = k + 1;
+      bb = k;
+    }
+    s_p = bb;
+    piv[k] = bb;
+  }
+  __syncthreads();
+  if (D.info[0] != 0) return;
+  const int p = s_p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double t = A[k + j * ld];
+      A[k + j * ld] = A[p + j * ld];
+      A[p + j * ld] = t;
+    }
+  __syncthreads();
+  const double inv = 1.0 / A[k + k * ld];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rowk[j] = (j == k) ? inv : A[k + j * ld] * inv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i + k * ld];
+}
+
+__global__ void k_gjb_update(const InvDesc* __restrict__ d, int nd, int k, const double* __restrict__ work,
+                             const long* __restrict__ work_off) {
+  const int b = blockIdx.y;
+  if (b >= nd) return;
+  const InvDesc D = d[b];
+  const int n = D.n;
+  if (k >= n || D.info[0] != 0) return;
+  double* A = D.A;
+  const long ld = D.ld;
+  const double* rowk = work + work_off[b];
+  const double* colk = rowk + n;
+  const long total = (long)n * n;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i == k) {
+      A[i + j * ld] = rowk[j];
+    } else {
+      const double a = (j == k) ? 0.0 : A[i + j * ld];
+      A[i + j * ld] = a - colk[i] * rowk[j];
+    }
+  }
+}
+
+__global__ void k_gjb_colswap(const InvDesc* __restrict__ d, int nd, const double* __restrict__ work,
+                              const long* __restrict__ work_off) {
+  const int b = blockIdx.x;
+  if (b >= nd) return;
+  const InvDesc D = d[b];
+  const int n = D.n;
+  if (D.info[0] != 0) return;
+  double* A = D.A;
+  const long ld = D.ld;
+  const int* piv = (const int*)(work + work_off[b] + 2 * n);
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = A[i + k * ld];
+        A[i + k * ld] = A[i + p * ld];
+        A[i + p * ld] = t;
+      }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- Householder QR
@@ -227,6 +377,44 @@ __device__ __forceinline__ TC warp_sum_t(TC v) {
   return v;
 }
 
+// Apply H = I - t v v^T (v_0 = 1, v_i = x_i for i >= 1) to the trailing
+// columns k+1..n-1 of A (rows k..k+len-1).  Each column's dot product and
+// update is split into S row segments when there are fewer trailing columns
+// than warps; the S partial sums are added in a fixed order (deterministic).
+// partial: shared memory of >= max(n, warps) doubles.  Ends with __syncthreads.
+template <typename TC>
+__device__ void apply_reflector(double* A, long ld, int k, int n, int len, const double* x, TC t, double* partial) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int nt = n - k - 1;
+  if (nt <= 0) return;
+  int S = nw / nt;
+  const int smax = (len + 63) / 64;
+  if (S > smax) S = smax;
+  if (S < 1) S = 1;
+  const int seg = (len + S - 1) / S;
+  const int items = nt * S;
+  for (int it = w; it < items; it += nw) {
+    const int jj = it / S, sg = it % S;
+    const double* y = A + k + (long)(k + 1 + jj) * ld;
+    const int r0 = sg * seg, r1 = min(len, r0 + seg);
+    TC dot = 0;
+    for (int i = r0 + lane; i < r1; i += 32) dot += (i == 0 ? (TC)1 : (TC)x[i]) * (TC)y[i];
+    dot = warp_sum_t<TC>(dot);
+    if (lane == 0) partial[it] = (double)dot;
+  }
+  __syncthreads();
+  for (int it = w; it < items; it += nw) {
+    const int jj = it / S, sg = it % S;
+    double* y = A + k + (long)(k + 1 + jj) * ld;
+    TC dot = 0;
+    for (int q = 0; q < S; ++q) dot += (TC)partial[jj * S + q];
+    dot *= t;
+    const int r0 = sg * seg, r1 = min(len, r0 + seg);
+    for (int i = r0 + lane; i < r1; i += 32) y[i] = (double)((TC)y[i] - dot * (i == 0 ? (TC)1 : (TC)x[i]));
+  }
+  __syncthreads();
+}
+
 template <typename TC>
 __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
   if ((int)blockIdx.x >= nd) return;
@@ -235,8 +423,8 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
   const long ld = D.ld;
   double* A = D.A;
   __shared__ double scratch[32];
+  __shared__ double partial[1024];
   __shared__ double s_alpha, s_beta, s_scale;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   const int kmax = m < n ? m : n;
   for (int k = 0; k < kmax; ++k) {
     double* x = A + k + k * ld;
@@ -265,15 +453,7 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
       const double sc = s_scale;
       for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] *= sc;
       __syncthreads();
-      const TC t = (TC)tau;
-      for (int j = k + 1 + w; j < n; j += nw) {
-        double* y = A + k + (long)j * ld;
-        TC dot = (lane == 0) ? (TC)y[0] : (TC)0;  // v_0 = 1
-        for (int i = 1 + lane; i < len; i += 32) dot += (TC)x[i] * (TC)y[i];
-        dot = warp_sum_t<TC>(dot) * t;
-        if (lane == 0) y[0] = (double)((TC)y[0] - dot);
-        for (int i = 1 + lane; i < len; i += 32) y[i] = (double)((TC)y[i] - dot * (TC)x[i]);
-      }
+      apply_reflector<TC>(A, ld, k, n, len, x, (TC)tau, partial);
     }
     __syncthreads();
     if (threadIdx.x == 0) x[0] = s_alpha;
@@ -420,6 +600,8 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
   double* ref = sm + n;
   int* jp = (int*)(sm + 2 * n);
   __shared__ double scratch[32];
+  __shared__ double partial[1024];
+  __shared__ char flag[1024];
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ double s_tau2, s_alpha, s_tau, s_scale;
@@ -504,33 +686,25 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
       for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] *= sc;
       __syncthreads();
     }
-    const TC t = (TC)tau;
+    if (tau != 0.0) apply_reflector<TC>(A, ld, k, n, len, x, (TC)tau, partial);
+    // downdate the column norms with the new row k of R; recompute a norm when
+    // cancellation has removed two digits
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double rkj = A[k + (long)j * ld];
+      const double v = nrm[j] - rkj * rkj;
+      flag[j] = !(v > 1e-2 * ref[j]);
+      nrm[j] = v;
+    }
+    __syncthreads();
     for (int j = k + 1 + w; j < n; j += nw) {
-      double* y = A + k + (long)j * ld;
-      if (tau != 0.0) {
-        TC dot = (lane == 0) ? (TC)y[0] : (TC)0;
-        for (int i = 1 + lane; i < len; i += 32) dot += (TC)x[i] * (TC)y[i];
-        dot = warp_sum_t<TC>(dot) * t;
-        for (int i = 1 + lane; i < len; i += 32) y[i] = (double)((TC)y[i] - dot * (TC)x[i]);
-        if (lane == 0) y[0] = (double)((TC)y[0] - dot);
-      }
-      __syncwarp();
-      const double rkj = y[0];
-      int recompute = 0;
+      if (!flag[j]) continue;
+      const double* y = A + k + (long)j * ld;
+      double s2 = 0.0;
+      for (int i = 1 + lane; i < len; i += 32) s2 += y[i] * y[i];
+      s2 = warp_sum(s2);
       if (lane == 0) {
-        const double v = nrm[j] - rkj * rkj;
-        recompute = !(v > 1e-2 * ref[j]);
-        nrm[j] = v;
-      }
-      recompute = __shfl_sync(0xffffffffu, recompute, 0);
-      if (recompute) {
-        double s2 = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) s2 += y[i] * y[i];
-        s2 = warp_sum(s2);
-        if (lane == 0) {
-          nrm[j] = s2;
-          ref[j] = s2;
-        }
+        nrm[j] = s2;
+        ref[j] = s2;
       }
     }
     __syncthreads();
@@ -657,6 +831,21 @@ __global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps
 }
 
 // ---------------------------------------------------------------- GEMV
+// 4 independent accumulators over the columns of a column-major block: row i,
+// columns [0, n) of A (leading dimension lda) against x.
+__device__ __forceinline__ double dot_row(const double* __restrict__ a, long lda, const double* __restrict__ x, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = 0;
+  for (; j + 3 < n; j += 4) {
+    s0 += a[(long)j * lda] * x[j];
+    s1 += a[(long)(j + 1) * lda] * x[j + 1];
+    s2 += a[(long)(j + 2) * lda] * x[j + 2];
+    s3 += a[(long)(j + 3) * lda] * x[j + 3];
+  }
+  for (; j < n; ++j) s0 += a[(long)j * lda] * x[j];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // y = alpha * op(A) x + beta * y.  Non-transposed: a thread per row walks the
 // columns (consecutive threads read consecutive rows of a column).  Transposed:
 // a warp per output reduces one contiguous column of A.
@@ -674,23 +863,36 @@ __global__ void k_gemv(const GemvDesc* __restrict__ d, int nd) {
     }
   } else {
     for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
-      double s = 0.0;
-      for (int j = 0; j < D.n; ++j) s += D.A[i + (long)j * D.lda] * D.x[j];
+      const double s = dot_row(D.A + i, D.lda, D.x, D.n);
       D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
     }
   }
 }
 
+// y = alpha * sum_t A_t x_t + beta * y, one CTA per output vector.  For each
+// block of 32 rows, warp w sums the terms t = w, w + warps, ... (a lane per
+// row); the per-warp sums are then added in warp order (deterministic).
 __global__ void k_gemv_sum(const GemvSumDesc* __restrict__ d, const GemvTerm* __restrict__ terms, int nd) {
   if ((int)blockIdx.x >= nd) return;
   const GemvSumDesc D = d[blockIdx.x];
-  for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __shared__ double part[32][33];
+  for (int rb = 0; rb < D.m; rb += 32) {
+    const int i = rb + lane;
     double s = 0.0;
-    for (int t = D.first; t < D.first + D.count; ++t) {
-      const GemvTerm T = terms[t];
-      for (int j = 0; j < T.n; ++j) s += T.A[i + (long)j * T.lda] * T.x[j];
+    if (i < D.m)
+      for (int t = D.first + w; t < D.first + D.count; t += nw) {
+        const GemvTerm T = terms[t];
+        s += dot_row(T.A + D.row0 + i, T.lda, T.x, T.n);
+      }
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < D.m) {
+      double tot = 0.0;
+      for (int q = 0; q < nw; ++q) tot += part[q][lane];
+      D.y[i] = (D.beta == 0.0) ? D.alpha * tot : D.alpha * tot + D.beta * D.y[i];
     }
-    D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
+    __syncthreads();
   }
 }
 

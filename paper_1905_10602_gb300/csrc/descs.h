@@ -71,8 +71,8 @@ struct GemvTerm {
   int lda, n;
 };
 struct GemvSumDesc {
-  double* y;
-  int m, first, count, pad;
+  double* y;  // rows [row0, row0 + m) of the output vector start here
+  int m, first, count, row0;
   double alpha, beta;
 };
 // Householder QR with column pivoting of the m x n matrix A, stopped at the

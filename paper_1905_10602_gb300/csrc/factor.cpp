@@ -498,18 +498,67 @@ struct Factorizer {
       return (LL.cells[3 * q] & 1) | ((LL.cells[3 * q + 1] & 1) << 1) | ((LL.cells[3 * q + 2] & 1) << 2);
     };
     const long rc2 = (long)rc * rc;
+    // Reduced-precision mode: the weights R (R^T R = Z^T Z) come from sums of
+    // per-offset Gram matrices of the translation table and an FP64 Cholesky,
+    // instead of a QR of the tall stacked table blocks.  Squaring the
+    // condition number resolves directions down to ~1e-7 of the largest,
+    // below what FP32 recompression distinguishes.
+    std::vector<double*> rz_row, rz_col;
+    if (prec == P32 && rc <= 128) {
+      double* gk = levelmem.alloc((size_t)2 * 343 * rc2);  // K^T K, then K K^T, per offset
+      double* gm = levelmem.alloc((size_t)8 * rc2);        // M2M^T M2M per octant
+      std::vector<GemmDesc> gg;
+      for (int o = 0; o < 343; ++o) {
+        const int ox = o % 7 - 3, oy = (o / 7) % 7 - 3, oz = o / 49 - 3;
+        if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+        gg.push_back(gmm(m2l_tab + o * rc2, rc, 1, m2l_tab + o * rc2, rc, 0, gk + o * rc2, rc, rc, rc, rc, 1.0, 0.0));
+        gg.push_back(gmm(m2l_tab + o * rc2, rc, 0, m2l_tab + o * rc2, rc, 1, gk + (343 + o) * rc2, rc, rc, rc, rc, 1.0,
+                         0.0));
+      }
+      for (int o = 0; o < 8; ++o)
+        gg.push_back(gmm(m2m_tab + o * rc2, rc, 1, m2m_tab + o * rc2, rc, 0, gm + o * rc2, rc, rc, rc, rc, 1.0, 0.0));
+      cnt.add_gemm(gg);
+      launch_gemm(st, gg, P64);
+      std::vector<double*> dst;
+      std::vector<const double*> terms;
+      std::vector<int> first{0};
+      rz_row.resize(nn);
+      rz_col.resize(nn);
+      for (int q = 0; q < nn; ++q)
+        for (int side = 0; side < 2; ++side) {
+          double* R = scratch.alloc((size_t)rc2);
+          (side == 0 ? rz_row : rz_col)[q] = R;
+          dst.push_back(R);
+          for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+            const int l = LL.il[e];
+            terms.push_back(side == 0 ? gk + off_index(l, q) * rc2 : gk + (343 + off_index(q, l)) * rc2);
+          }
+          if (kappa > 2) terms.push_back(gm + octant(q) * rc2);
+          first.push_back((int)terms.size());
+        }
+      launch_gram_sum(st, dst, terms, first, rc);
+      launch_chol(st, dst, rc, 1e-13);
+    }
     for (int q = 0; q < nn; ++q) {
       Event ev = make_event(W, q);
       ev.r_old = rc;
       ev.n = W.n[q];
-      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
-        const int l = LL.il[e];
-        ev.z[0].push_back(Blk{m2l_tab + off_index(l, q) * rc2, rc, rc, rc, 0});  // K(l,q)
-        ev.z[1].push_back(Blk{m2l_tab + off_index(q, l) * rc2, rc, rc, rc, 1});  // K(q,l)^T
-      }
-      if (kappa > 2) {
-        ev.z[0].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // M2M
-        ev.z[1].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // L2L^T = M2M
+      if (!rz_row.empty()) {
+        const bool any = (LL.il_ptr[q + 1] > LL.il_ptr[q]) || kappa > 2;
+        if (any) {
+          ev.z[0].push_back(Blk{rz_row[q], rc, rc, rc, 0});
+          ev.z[1].push_back(Blk{rz_col[q], rc, rc, rc, 0});
+        }
+      } else {
+        for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+          const int l = LL.il[e];
+          ev.z[0].push_back(Blk{m2l_tab + off_index(l, q) * rc2, rc, rc, rc, 0});  // K(l,q)
+          ev.z[1].push_back(Blk{m2l_tab + off_index(q, l) * rc2, rc, rc, rc, 1});  // K(q,l)^T
+        }
+        if (kappa > 2) {
+          ev.z[0].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // M2M
+          ev.z[1].push_back(Blk{m2m_tab + octant(q) * rc2, rc, rc, rc, 0});  // L2L^T = M2M
+        }
       }
       ev.b[0] = Blk{P2M0[q], rc, rc, W.n[q], 0};
       ev.b[1] = Blk{L2P0[q], W.n[q], rc, W.n[q], 1};
@@ -590,8 +639,20 @@ struct Factorizer {
       int ld, rows, cols;
     };
     std::vector<FarFill> fills;
-    std::map<int, std::vector<Blk>> rowfill, colfill;
+    // per-node fill lists, indexed through the order in which nodes first
+    // receive a far fill (the re-base order)
+    std::vector<int> slot_of(W.nn, -1);
     std::vector<int> rebase_order;
+    std::vector<std::vector<Blk>> rowfill_v, colfill_v;
+    auto rebase_slot = [&](int q) {
+      if (slot_of[q] < 0) {
+        slot_of[q] = (int)rebase_order.size();
+        rebase_order.push_back(q);
+        rowfill_v.emplace_back();
+        colfill_v.emplace_back();
+      }
+      return slot_of[q];
+    };
     for (int g = 0; g < ng; ++g) {
       const int i = grp[g];
       const int ni = W.n[i], ri = W.r[i], m = ni + ri;
@@ -660,15 +721,8 @@ struct Factorizer {
           } else {
             IFMM_REQUIRE(W.farix(q, q2) >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
             fills.push_back(FarFill{q, q2, src, M, mq, mq2});
-            if (!W.elim[q]) {
-              colfill[q].push_back(Blk{src, M, mq2, W.n[q], 1});
-              if (std::find(rebase_order.begin(), rebase_order.end(), q) == rebase_order.end()) rebase_order.push_back(q);
-            }
-            if (!W.elim[q2]) {
-              rowfill[q2].push_back(Blk{src, M, mq, W.n[q2], 0});
-              if (std::find(rebase_order.begin(), rebase_order.end(), q2) == rebase_order.end())
-                rebase_order.push_back(q2);
-            }
+            if (!W.elim[q]) colfill_v[rebase_slot(q)].push_back(Blk{src, M, mq2, W.n[q], 1});
+            if (!W.elim[q2]) rowfill_v[rebase_slot(q2)].push_back(Blk{src, M, mq, W.n[q2], 0});
           }
         }
       }
@@ -704,8 +758,8 @@ struct Factorizer {
       }
       ev.b[0] = Blk{W.P2M[q], W.capr[q], rq, W.n[q], 0};
       ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
-      ev.f[0] = rowfill[q];
-      ev.f[1] = colfill[q];
+      ev.f[0] = std::move(rowfill_v[slot_of[q]]);
+      ev.f[1] = std::move(colfill_v[slot_of[q]]);
       evs.push_back(ev);
       po.push_back(W.P2M[q]);
       lo.push_back(W.L2P[q]);
@@ -846,6 +900,7 @@ struct Factorizer {
       // the child level's blocks stay alive until this level's initial copies ran
       DeviceArena child_mem;
       child_mem.swap(levelmem);
+      profiler().level_tag = kappa;
       init_level(*W, kappa, prev.get());
       wait();
       st.reset();
@@ -870,6 +925,7 @@ struct Factorizer {
       F.stat("time_level_" + std::to_string(kappa), std::chrono::duration<double>(te - tl).count());
       prev = std::move(W);
     }
+    profiler().level_tag = -1;
     build_solve_plan(F, s);
     CK(cudaStreamSynchronize(s));
     levelmem.release();

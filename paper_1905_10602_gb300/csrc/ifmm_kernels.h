@@ -31,6 +31,9 @@ void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, do
 void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n);
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
                       int N, double scale, double diag);
+void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::vector<const double*>& terms,
+                     const std::vector<int>& first, int r);
+void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta);
 void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
 void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
 void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info);

@@ -83,19 +83,31 @@ void Profiler::end(int kind, cudaStream_t s, cudaEvent_t b) {
   CK(cudaEventCreate(&e));
   CK(cudaEventRecord(e, s));
   pending.push_back({kind, {b, e}});
+  pending_tags.push_back({level_tag, batch_tag});
   if (pending.size() > 4096) collect();
 }
 void Profiler::collect() {
-  for (auto& p : pending) {
+  static FILE* log = nullptr;
+  static bool log_init = false;
+  if (!log_init) {
+    const char* path = getenv("IFMM_PROFILE_LOG");
+    if (path && path[0]) log = fopen(path, "a");
+    log_init = true;
+  }
+  for (size_t i = 0; i < pending.size(); ++i) {
+    auto& p = pending[i];
     CK(cudaEventSynchronize(p.second.second));
     float t = 0;
     CK(cudaEventElapsedTime(&t, p.second.first, p.second.second));
     ms[p.first] += t;
     events_kernels[p.first] += 1;
+    if (log) fprintf(log, "%s %d %ld %.4f\n", kKindNames[p.first], pending_tags[i].first, pending_tags[i].second, t);
     cudaEventDestroy(p.second.first);
     cudaEventDestroy(p.second.second);
   }
+  if (log) fflush(log);
   pending.clear();
+  pending_tags.clear();
 }
 void Profiler::reset() {
   collect();
@@ -115,16 +127,43 @@ void check_launch(const char* what) {
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
   check_copy(v);
-  const CopyDesc* d = st.push(v);
+  std::vector<CopyDesc> small, big;
+  for (auto& x : v) ((long)x.rows * x.cols <= 1024 ? small : big).push_back(x);
+  profiler().batch_tag = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
-  k_copy<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
+  if (!small.empty()) {
+    const CopyDesc* d = st.push(small);
+    k_copy_small<<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+  }
+  if (!big.empty()) {
+    const CopyDesc* d = st.push(big);
+    k_copy<<<(unsigned)big.size(), 256, 0, st.stream>>>(d, (int)big.size());
+  }
   check_launch("k_copy");
   profiler().end(KK_COPY, st.stream, pe);
 }
 
-void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
+void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
+  if (v0.empty()) return;
+  check_gemm(v0);
+  std::vector<GemmDesc> small, v;
+  for (auto& x : v0) {
+    if (x.m <= 0 || x.n <= 0) continue;
+    (x.m <= 32 && x.n <= 32 && x.k <= 128 ? small : v).push_back(x);
+  }
+  if (!small.empty()) {
+    const GemmDesc* d = st.push(small);
+    const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
+    profiler().batch_tag = (long)small.size();
+    cudaEvent_t pe = profiler().begin(kk, st.stream);
+    if (prec == P32)
+      k_gemm_small<float><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+    else
+      k_gemm_small<double><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+    check_launch("k_gemm_small");
+    profiler().end(kk, st.stream, pe);
+  }
   if (v.empty()) return;
-  check_gemm(v);
   std::vector<int> tp(v.size() + 1, 0);
   for (size_t i = 0; i < v.size(); ++i) {
     long t = (long)((v[i].m + 63) / 64) * ((v[i].n + 63) / 64);
@@ -135,6 +174,7 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
   // descriptors with zero tiles are never selected: find_desc returns the last
   // descriptor whose start <= tile, and empty ones share their start with the next
   const GemmDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   const int* p = st.push(tp);
   const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
@@ -148,33 +188,68 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
 
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   if (v.empty()) return;
-  int nmax = 0;
-  for (auto& x : v) nmax = std::max(nmax, x.n);
-  size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
-  static bool attr = false;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
-  IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivot block too large");
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
     req(v[i].A, span(v[i].n, v[i].n, v[i].ld), "inv.A", i);
     req(v[i].info, sizeof(int), "inv.info", i);
   }
-  const InvDesc* d = st.push(v);
-  cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
-  k_inv<<<(unsigned)v.size(), 256, smem, st.stream>>>(d, (int)v.size());
-  check_launch("k_inv");
-  profiler().end(KK_INV, st.stream, pe);
+  // size classes: shared-memory Gauss-Jordan for n <= 64 and n <= 160, the
+  // batched multi-CTA variant above
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+    attr = true;
+  }
+  std::vector<InvDesc> cls[3];
+  for (auto& x : v) cls[x.n <= 64 ? 0 : (x.n <= 160 ? 1 : 2)].push_back(x);
+  for (int c = 0; c < 2; ++c) {
+    if (cls[c].empty()) continue;
+    int nmax = 0;
+    for (auto& x : cls[c]) nmax = std::max(nmax, x.n);
+    const int smem_mat = nmax * nmax * (int)sizeof(double);
+    const size_t smem = (size_t)smem_mat + sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
+    const InvDesc* d = st.push(cls[c]);
+    profiler().batch_tag = (long)cls[c].size();
+    cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
+    k_inv<<<(unsigned)cls[c].size(), c == 0 ? 128 : 256, smem, st.stream>>>(d, (int)cls[c].size(), smem_mat);
+    check_launch("k_inv");
+    profiler().end(KK_INV, st.stream, pe);
+  }
+  if (!cls[2].empty()) {
+    const std::vector<InvDesc>& L = cls[2];
+    int nmax = 0;
+    std::vector<long> off(L.size());
+    long tot = 0;
+    for (size_t i = 0; i < L.size(); ++i) {
+      nmax = std::max(nmax, L[i].n);
+      off[i] = tot;
+      tot += 3 * (long)L[i].n + 2;
+    }
+    double* work = (double*)st.dev.alloc_bytes(sizeof(double) * tot);
+    const InvDesc* d = st.push(L);
+    const long* o = st.push(off);
+    const int nb = (int)L.size();
+    const int gx = (int)std::max<long>(1, std::min<long>((long)nmax * nmax / 1024 + 1, 64));
+    profiler().batch_tag = (long)nb;
+    cudaEvent_t pe = profiler().begin(KK_GJ_BIG, st.stream, 2L * nmax + 1);
+    for (int k = 0; k < nmax; ++k) {
+      k_gjb_pivot<<<nb, 256, 0, st.stream>>>(d, nb, k, work, o);
+      k_gjb_update<<<dim3(gx, nb), 256, 0, st.stream>>>(d, nb, k, work, o);
+    }
+    k_gjb_colswap<<<nb, 256, 0, st.stream>>>(d, nb, work, o);
+    check_launch("k_gjb");
+    profiler().end(KK_GJ_BIG, st.stream, pe);
+  }
 }
 
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
   if (v.empty()) return;
+  for (auto& x : v) IFMM_REQUIRE(x.n <= 1024, IFMM_EINVAL, "QR wider than 1024 columns");
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
     req(v[i].A, span(v[i].m, v[i].n, v[i].ld), "qr.A", i);
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qr ld too small");
   }
   const QrDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -205,6 +280,7 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
     if (x.ldg < x.m || x.ldv < x.n) throw Error(IFMM_EINVAL, "svd ld too small");
   }
   const SvdDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -217,6 +293,7 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
 
 void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   if (v.empty()) return;
+  for (auto& x : v) IFMM_REQUIRE(x.n <= 1024, IFMM_EINVAL, "pivoted QR wider than 1024 columns");
   int nmax = 0;
   for (auto& x : v) nmax = std::max(nmax, x.n);
   const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
@@ -234,6 +311,7 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qrcp ld too small");
   }
   const QrcpDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -264,6 +342,7 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
   }
   const SvdRtDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -283,6 +362,7 @@ void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
     req(x.y, sizeof(double) * (x.trans ? x.n : x.m), "gemv.y", i);
   }
   const GemvDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_GEMV, st.stream);
   k_gemv<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_gemv");
@@ -528,6 +608,88 @@ void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, cons
   profiler().end(KK_MATVEC, s, pe);
 }
 
+// ---------------------------------------------------------------- Gram sums, Cholesky
+// dst (r x r) = sum of the listed r x r matrices (one CTA per output).
+__global__ void k_gram_sum(double* const* __restrict__ dst, const double* const* __restrict__ terms,
+                           const int* __restrict__ first, int nd, int r) {
+  const int b = blockIdx.x;
+  if (b >= nd) return;
+  const int t0 = first[b], t1 = first[b + 1];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += terms[t][e];
+    dst[b][e] = s;
+  }
+}
+
+// Upper Cholesky factor R (R^T R = G + delta * max_i G_ii * I) of each r x r
+// matrix, r <= 128, in shared memory; a pivot that is still not positive is
+// replaced by delta * max_i G_ii (the direction then carries almost no weight).
+__global__ void k_chol(double* const* __restrict__ mats, int nd, int r, double delta) {
+  const int b = blockIdx.x;
+  if (b >= nd) return;
+  extern __shared__ double G[];
+  double* M = mats[b];
+  __shared__ double s_diag, s_piv;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) G[e] = M[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < r; ++i) mx = fmax(mx, G[i + i * r]);
+    s_diag = mx > 0.0 ? delta * mx : 1e-300;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) G[i + i * r] += s_diag;
+  __syncthreads();
+  // right-looking: column-major G, upper factor stored in the upper triangle
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      double d = G[k + k * r];
+      if (!(d > s_diag * 1e-3)) d = s_diag;
+      s_piv = sqrt(d);
+      G[k + k * r] = s_piv;
+    }
+    __syncthreads();
+    const double pv = s_piv;
+    for (int j = k + 1 + threadIdx.x; j < r; j += blockDim.x) G[k + j * r] /= pv;  // row k of R
+    __syncthreads();
+    for (int e = threadIdx.x; e < (r - k - 1) * (r - k - 1); e += blockDim.x) {
+      const int i = k + 1 + e % (r - k - 1), j = k + 1 + e / (r - k - 1);
+      if (i <= j) G[i + j * r] -= G[k + i * r] * G[k + j * r];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    M[e] = (i <= j) ? G[e] : 0.0;
+  }
+}
+
+void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::vector<const double*>& terms,
+                     const std::vector<int>& first, int r) {
+  if (dst.empty()) return;
+  double* const* d = st.push(dst);
+  const double* const* t = st.push(terms);
+  const int* f = st.push(first);
+  profiler().launches[KK_TABLES] += 1;
+  k_gram_sum<<<(unsigned)dst.size(), 256, 0, st.stream>>>(d, t, f, (int)dst.size(), r);
+  check_launch("k_gram_sum");
+}
+
+void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta) {
+  if (mats.empty()) return;
+  IFMM_REQUIRE(r <= 128, IFMM_EINVAL, "Cholesky block too large");
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr = true;
+  }
+  double* const* d = st.push(mats);
+  profiler().launches[KK_TABLES] += 1;
+  k_chol<<<(unsigned)mats.size(), 256, sizeof(double) * r * r, st.stream>>>(d, (int)mats.size(), r, delta);
+  check_launch("k_chol");
+}
+
 __global__ void k_gather_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
                               int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -645,6 +807,7 @@ void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts,
       throw Error(IFMM_EINVAL, "p2p point range");
   }
   const P2pDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   profiler().launches[KK_P2P] += 1;
   k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
   check_launch("k_p2p");
@@ -657,6 +820,7 @@ void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double
     if (v[i].p0 < 0 || v[i].p0 + v[i].n > N) throw Error(IFMM_EINVAL, "interp point range");
   }
   const InterpDesc* d = st.push(v);
+  profiler().batch_tag = (long)v.size();
   profiler().launches[KK_INTERP] += 1;
   k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
   check_launch("k_interp");

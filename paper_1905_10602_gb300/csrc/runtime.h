@@ -173,6 +173,9 @@ enum KernelKind {
 };
 struct Profiler {
   bool timing = false;
+  int level_tag = -1;  // level being factored (for the per-launch log)
+  long batch_tag = 0;  // descriptors in the launch being timed
+  std::vector<std::pair<int, long>> pending_tags;
   long launches[KK_COUNT] = {0};
   long events_kernels[KK_COUNT] = {0};
   double ms[KK_COUNT] = {0};

@@ -9,12 +9,30 @@
 // "aggregate x of the children") and splitting cost nothing.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fact.h"
 #include "ifmm_kernels.h"
 
 namespace ifmm {
+
+// A GEMV over many rows becomes several descriptors of at most 64 rows (one
+// CTA each), so a large pivot block is spread over several SMs.
+static void push_gemv_rows(std::vector<GemvDesc>& out, const GemvDesc& g) {
+  const int chunk = 64;
+  if (g.trans || g.m <= chunk) {
+    out.push_back(g);
+    return;
+  }
+  for (int r = 0; r < g.m; r += chunk) {
+    GemvDesc c = g;
+    c.A = g.A + r;
+    c.y = g.y + r;
+    c.m = std::min(chunk, g.m - r);
+    out.push_back(c);
+  }
+}
 
 void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
   const ifmm_tree& T = *F.t;
@@ -111,14 +129,14 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
         const int n = nf.n, r = nf.r, m = n + r;
         double* t = P.tvec + toff[kappa][i];
         if (m == 0) continue;
-        if (n) g1.push_back(gmv(nf.piinv, m, m, n, 0, Xk + xoff[kappa][i], t, 1.0, 0.0));
+        if (n) push_gemv_rows(g1, gmv(nf.piinv, m, m, n, 0, Xk + xoff[kappa][i], t, 1.0, 0.0));
         else c2.push_back(cpy(nullptr, 0, t, m, m, 1));
         for (size_t a = 0; a < nf.nb.size(); ++a) {
           const int q = nf.nb[a];
           const int mq = nf.lcol_rows[a];
           if (!mq || !n) continue;
           double* y = nf.was_elim[a] ? X + rloc(kappa, q) : Xk + xoff[kappa][q];
-          g2.push_back(gmv(nf.lcol[a], nf.lcol_ld[a], mq, n, 0, t, y, -1.0, 1.0));
+          push_gemv_rows(g2, gmv(nf.lcol[a], nf.lcol_ld[a], mq, n, 0, t, y, -1.0, 1.0));
         }
         if (r) c2.push_back(cpy(t + n, m, X + rloc(kappa, i), r, r, 1));
       }
@@ -131,7 +149,7 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
   if (F.ntop) {
     std::vector<GemvDesc> g;
     std::vector<CopyDesc> c;
-    g.push_back(gmv(F.top_inv, F.ntop, F.ntop, F.ntop, 0, X + base[1], P.tvec, 1.0, 0.0));
+    push_gemv_rows(g, gmv(F.top_inv, F.ntop, F.ntop, F.ntop, 0, X + base[1], P.tvec, 1.0, 0.0));
     c.push_back(cpy(P.tvec, F.ntop, X + base[1], F.ntop, F.ntop, 1));
     emit_gemv(g);
     emit_copy(c);
@@ -154,9 +172,9 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
         GemvSumDesc sd;
         sd.y = sv;
         sd.m = n;
+        sd.row0 = 0;
         sd.first = (int)all_terms.size();
         sd.count = 0;
-        sd.pad = 0;
         sd.alpha = -1.0;
         sd.beta = 1.0;
         for (size_t a = 0; a < nf.nb.size(); ++a) {
@@ -167,8 +185,15 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
           all_terms.push_back(GemvTerm{nf.urow[a], val, n, mq});
           sd.count++;
         }
-        if (sd.count) s1.push_back(sd);
-        g2.push_back(gmv(nf.piinv, m, n, m, 0, sv, Xk + xoff[kappa][i], 1.0, 0.0));
+        if (sd.count)
+          for (int r0 = 0; r0 < n; r0 += 32) {
+            GemvSumDesc c = sd;
+            c.m = std::min(32, n - r0);
+            c.y = sd.y + r0;
+            c.row0 = r0;
+            s1.push_back(c);
+          }
+        push_gemv_rows(g2, gmv(nf.piinv, m, n, m, 0, sv, Xk + xoff[kappa][i], 1.0, 0.0));
       }
       emit_copy(c1);
       emit_sum(s1);
@@ -222,9 +247,25 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
   const SolvePlan& P = F.plan;
   const int64_t N = F.t->N;
   CK(cudaMemcpyAsync(P.stage_in, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-  cudaEvent_t pe = profiler().begin(KK_SOLVE_GRAPH, s, (long)P.prog.size());
-  CK(cudaGraphLaunch(P.graph, s));
-  profiler().end(KK_SOLVE_GRAPH, s, pe);
+  static const bool direct = [] {
+    const char* e = getenv("IFMM_SOLVE_NOGRAPH");
+    return e && e[0] == '1';
+  }();
+  if (direct) {  // the same program as individual launches, each timed when profiling
+    for (auto& l : P.prog) {
+      const int kind = l.kind == 0 ? KK_COPY : (l.kind == 1 ? KK_GEMV : KK_GEMV_SUM);
+      profiler().batch_tag = l.count;
+      cudaEvent_t pe = profiler().begin(kind, s);
+      if (l.kind == 0) launch_copy_dev(s, (const CopyDesc*)l.desc, l.count);
+      else if (l.kind == 1) launch_gemv_dev(s, (const GemvDesc*)l.desc, l.count);
+      else launch_gemv_sum_dev(s, (const GemvSumDesc*)l.desc, (const GemvTerm*)l.terms, l.count);
+      profiler().end(kind, s, pe);
+    }
+  } else {
+    cudaEvent_t pe = profiler().begin(KK_SOLVE_GRAPH, s, (long)P.prog.size());
+    CK(cudaGraphLaunch(P.graph, s));
+    profiler().end(KK_SOLVE_GRAPH, s, pe);
+  }
   CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
 

@@ -159,3 +159,24 @@ def test_matvec_double_float_sampled_large():
     y = ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(len(pts), "df"))
     rows = np.random.default_rng(3).choice(len(pts), 64, replace=False)
     assert _rel(y[rows], direct_matvec(pts, x, rows)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_precision_error_and_gmres(prec):
+    """Reduced-precision Schur updates and recompression: the applied inverse stays
+    within 1e-4 of the FP64 oracle's (eps = 1e-6) and GMRES with FP64-accurate
+    residuals still reaches 1e-8 in at most two more iterations than FP64."""
+    pts = bumpy_sphere(4096, 3)
+    b = point_source_rhs(pts)
+    o = IFMMOracle(pts, 4, 3, 1e-6, 3).factor()
+    t = ifmm.ifmm_build_tree(pts, 4)
+    ifmm.ifmm_color(t, 3)
+    f = ifmm.ifmm_factor(t, 3, 1e-6, precision=prec)
+    err = _rel(ifmm.ifmm_solve(f, b), o.solve(b))
+    assert err < 1e-4, err
+    k = ifmm.default_kernel(len(pts), "df")
+    x, its, rel = ifmm.bem_gmres(t, b, precond=f, tol=1e-8, kernel=k)
+    f64 = ifmm.ifmm_factor(t, 3, 1e-6, precision="fp64")
+    _, its64, _ = ifmm.bem_gmres(t, b, precond=f64, tol=1e-8)
+    assert rel <= 1e-8 and its <= its64 + 2
+    assert _rel(x, np.linalg.solve(dense_matrix(pts), b)) < 1e-7
