@@ -128,6 +128,29 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
  * x, y: n doubles, host or device (same side); they must not alias. */
 ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
 
+/* y = A x like bem_matvec, but without allocating any device memory, for callers
+ * that cannot call cudaMalloc/cudaFree (code running inside a host framework
+ * that owns and sizes the device memory pool, or code that must not trigger the
+ * synchronisation an allocation can imply).  The paper has no counterpart: it
+ * is a deployment variant of the direct-summation matvec.
+ *   - x, y: N doubles in device memory of the current device, caller order,
+ *     caller-allocated; they must not alias.  The call only enqueues work on
+ *     `stream` and returns; y is ready when the stream reaches that point.
+ *   - Scratch is a fixed array in the library's device image (4 MiB, trees of at
+ *     most 262,144 points), kept by every GPU that loads the library until the
+ *     process exits.  Larger trees are rejected with IFMM_EINVAL.
+ *   - The tree must already be resident on the current device: any earlier
+ *     ifmm_factor, bem_matvec or bem_gmres on it uploads it (this call never
+ *     does, since that would allocate).  Otherwise IFMM_EINVAL.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one scratch array: calls that overlap on the GPU (on
+ *     different streams, or from different threads) race and give wrong results.
+ *     No part of the scratch needs clearing between calls.
+ *   - k->arith selects FP64 or float-pair sums, as for bem_matvec. */
+ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
+
 /* Ranks chosen by ifmm_factor, as (level, node, event, rank) quadruples; node is the
  * tree-order node index at that level and event counts that node's recompressions
  * at that level (0 = level start).  Same buffer protocol as ifmm_tree_query. */

@@ -1,7 +1,8 @@
 """Builds libifmm.so in-tree for sm_103a (GB300).
 
-One CUDA translation unit (runtime.cu, every kernel) compiled by nvcc and the
-host translation units compiled by g++, in parallel, then linked against the
+Two CUDA translation units compiled by nvcc (runtime.cu: every kernel of the
+main path; noalloc.cu: the allocation-free matvec) and the host translation
+units compiled by g++, in parallel, then linked against the
 CUDA runtime.  `python -m paper_1905_10602_gb300.build` or build() from Python.
 """
 
@@ -19,7 +20,7 @@ LIB = os.path.join(HERE, "libifmm.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["runtime.cu"]
+CU_SOURCES = ["runtime.cu", "noalloc.cu"]
 CPP_SOURCES = ["tree.cpp", "factor.cpp", "solve.cpp"]
 
 

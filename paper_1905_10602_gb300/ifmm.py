@@ -53,6 +53,7 @@ _sig = {
     "bem_gmres": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp, ctypes.c_int, _dbl, ctypes.c_int,
                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_dbl), _vp],
     "bem_matvec": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
+    "bem_matvec_noalloc": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
     "ifmm_fact_ranks": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
     "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
 }
@@ -253,3 +254,12 @@ def ifmm_profile_query() -> dict:
         out[name.value.decode()] = (int(n.value), float(ms.value))
         i += 1
     return out
+
+
+def bem_matvec_noalloc(tree: Tree, x, y, kernel: Kernel | None = None, stream=None) -> None:
+    """y = A x into the caller's device tensor y, with no device allocation (for
+    callers that cannot allocate device memory; see include/ifmm.h).  x and y
+    are float64 CUDA tensors of N elements; the call returns once the work is
+    enqueued on the stream."""
+    k = kernel if kernel is not None else default_kernel(tree.n)
+    _check(lib.bem_matvec_noalloc(tree.h, ctypes.byref(k), _ptr(x), _ptr(y), stream or _stream(x)))
