@@ -77,7 +77,7 @@ typedef struct {
   const int32_t* replay; /* rank_mode REPLAY: host array of (level,node,event,rank)     */
   int64_t replay_len;    /*   quadruples, replay_len quadruples                         */
   int max_rank;          /* cap on any node rank (0 = library default, 256)             */
-  const float* mlp;      /* rank_mode LEARNED: host weights, layout of ifmm_mlp_layout  */
+  const float* mlp;      /* rank_mode LEARNED: host weights, IFMM_MLP_NWEIGHTS floats   */
   uint64_t seed;         /* seed of the randomized range finder (LEARNED mode)          */
 } ifmm_opts;
 
@@ -150,6 +150,44 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
  *     No part of the scratch needs clearing between calls.
  *   - k->arith selects FP64 or float-pair sums, as for bem_matvec. */
 ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
+
+/* Rank predictor (BASELINE's learned part; Sec. 4.2 uses randomized SVD at a
+ * prescribed accuracy, here a learned rank caps the pivoted-QR range finder).
+ * A multilayer perceptron 9 -> 64 -> 64 -> 64 -> 1 with ReLU hidden layers, FP32.
+ * Inputs per recompression event: cell centre in [-1,1]^3 (3), block size
+ * n_q / 256 (1), level / 10 (1), current rank / 64 (1), fill-in rows / 1024 (1),
+ * L1 cell offset to the eliminated neighbour whose fill-ins caused the event / 3
+ * (1; 0 at a level start), log10(eps) / 10 (1).  Output: rank / 64.  Weights, row-major W[in][out]:
+ *   W1[9][64] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64][1] b4[1].
+ * In IFMM_RANK_LEARNED mode ifmm_factor recompresses an event whose predicted
+ * rank k is well below its block width with a randomized range finder of width
+ * s = ceil(k) + 8 (Y^T Omega with a +-1 SplitMix64 sketch, orthonormalised;
+ * B = Y Q; SVD of B).  The result is accepted when ||Y - B Q^T||_F <=
+ * max(eps * sigma_1, 16 u ||Y||_F) (u: unit roundoff of the arithmetic), else the
+ * exact pivoted-QR + Jacobi path runs on the same Y.  Counts: ifmm_fact_stats
+ * learned_events / learned_sketched / learned_fallbacks. */
+#define IFMM_MLP_INPUTS 9
+#define IFMM_MLP_NWEIGHTS 9025
+
+/* y[i] = MLP(x[i]) for n feature rows x (n x 9 row-major, host), y (n, host). */
+ifmm_status ifmm_mlp_forward(const float* weights, const float* x, int64_t n, float* y, void* stream);
+
+/* Loss L = mean_i (y_i - t_i)^2 / 2 over n rows and its gradient with respect to
+ * every weight (IFMM_MLP_NWEIGHTS floats, host), by the library's backward kernels. */
+ifmm_status ifmm_mlp_grad(const float* weights, const float* x, const float* t, int64_t n, float* grad, float* loss,
+                          void* stream);
+
+/* Trains the MLP on the device: He-uniform initialisation from `seed`
+ * (SplitMix64 counter stream), Adam (beta 0.9 / 0.999) with step `lr`, minibatches
+ * of `batch` rows in order, `epochs` passes.  weights: out, host; final_loss (may
+ * be NULL): L over all rows with the final weights. */
+ifmm_status ifmm_mlp_train(const float* x, const float* t, int64_t n, int epochs, int batch, float lr, uint64_t seed,
+                           float* weights, float* final_loss, void* stream);
+
+/* Training data from a factorization: the 9 predictor inputs (row-major) and the
+ * chosen rank of every recompression event, in the order of ifmm_fact_ranks.
+ * features/ranks may be NULL; min(count, cap) rows are written, *count = total. */
+ifmm_status ifmm_fact_events(const ifmm_fact* f, float* features, int32_t* ranks, int64_t cap, int64_t* count);
 
 /* Ranks chosen by ifmm_factor, as (level, node, event, rank) quadruples; node is the
  * tree-order node index at that level and event counts that node's recompressions

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libifmm.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["runtime.cu", "noalloc.cu"]
+CU_SOURCES = ["runtime.cu", "noalloc.cu", "mlp.cu"]
 CPP_SOURCES = ["tree.cpp", "factor.cpp", "solve.cpp"]
 
 

@@ -604,8 +604,8 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
   __shared__ char flag[1024];
   __shared__ double red_v[32];
   __shared__ int red_i[32];
-  __shared__ double s_tau2, s_alpha, s_tau, s_scale;
-  __shared__ int s_p, s_stop;
+  __shared__ double s_tau2, s_alpha, s_tau, s_scale, s_first, s_tailv;
+  __shared__ int s_p, s_stop, s_capped;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   for (int j = w; j < n; j += nw) {
     const double* c = A + (long)j * ld;
@@ -642,7 +642,14 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
       for (int i = 0; i < nw; ++i)
         if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < b)) { bv = red_v[i]; b = red_i[i]; }
       if (k == 0) s_tau2 = D.tau_rel * D.tau_rel * bv;
+      if (k == 0) s_first = bv;
       s_stop = !(bv > s_tau2) || !(bv > 0.0) || b >= n;
+      s_capped = 0;
+      if (!s_stop && D.kcap > 0 && k >= D.kcap) {
+        s_stop = 1;
+        s_capped = 1;
+        s_tailv = (s_first > 0.0) ? sqrt(bv / s_first) : 0.0;
+      }
       s_p = b;
     }
     __syncthreads();
@@ -713,7 +720,10 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
     __syncthreads();
   }
   for (int j = threadIdx.x; j < n; j += blockDim.x) D.jpvt[j] = jp[j];
-  if (threadIdx.x == 0) D.kout[0] = k;
+  if (threadIdx.x == 0) {
+    D.kout[0] = k;
+    if (D.tail) D.tail[0] = (k < kmax && s_capped) ? s_tailv : 0.0;
+  }
 }
 
 // ---------------------------------------------------------------- Jacobi on P R_k^T
@@ -740,8 +750,14 @@ __global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps
   double gmax = 0.0;
   for (long e = threadIdx.x; e < (long)n * k; e += blockDim.x) {
     const int pos = (int)(e % n), i = (int)(e / n);
-    const double v = (i <= pos) ? D.A[i + pos * ld] : 0.0;
-    B[D.jpvt[pos] + (long)i * n] = (TC)v;
+    double v;
+    if (D.jpvt) {
+      v = (i <= pos) ? D.A[i + pos * ld] : 0.0;
+      B[D.jpvt[pos] + (long)i * n] = (TC)v;
+    } else {  // explicit n x k matrix: orthonormal basis of its range
+      v = D.A[pos + (long)i * ld];
+      B[pos + (long)i * n] = (TC)v;
+    }
     const double a = fabs(v);
     gmax = (a > gmax || a != a) ? a : gmax;
   }
@@ -828,6 +844,35 @@ __global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps
     }
     D.V[i + (long)j * D.ldv] = v;
   }
+}
+
+// ---------------------------------------------------------------- randomized range finder helpers
+// Omega (m x s, ld m) of +-1 entries: bit 63 of SplitMix64(seed + 0x9E37..*(index+1)).
+__global__ void k_sketch(const SketchDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const SketchDesc D = d[blockIdx.x];
+  const long total = (long)D.m * D.s;
+  for (long e = threadIdx.x; e < total; e += blockDim.x) {
+    unsigned long long z = D.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(e + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    D.omega[e] = (z >> 63) ? 1.0 : -1.0;
+  }
+}
+// out[0] = Frobenius norm of the m x n block (ld)
+__global__ void k_frob(const FrobDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const FrobDesc D = d[blockIdx.x];
+  __shared__ double scratch[32];
+  double s = 0.0;
+  const long total = (long)D.m * D.n;
+  for (long e = threadIdx.x; e < total; e += blockDim.x) {
+    const double v = D.A[(e % D.m) + (e / D.m) * (long)D.ld];
+    s += v * v;
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) D.out[0] = sqrt(s);
 }
 
 // ---------------------------------------------------------------- GEMV

@@ -86,6 +86,10 @@ struct QrcpDesc {
   double tau_rel;
   int* jpvt;
   int* kout;
+  int kcap;      // > 0: also stop after kcap steps (predicted rank + margin)
+  int pad;
+  double* tail;  // out (may be NULL): largest remaining column norm / largest
+                 // initial column norm when stopped by kcap, else 0
 };
 
 // Right singular vectors of Y from its truncated pivoted QR (Y P ~ Q R_k):
@@ -102,6 +106,20 @@ struct SvdRtDesc {
   int ldv, pad;
   double* sig;
   double* work;
+};
+
+// Random sketch matrix (m x s, ld m) of +-1 entries from a counter stream.
+struct SketchDesc {
+  double* omega;
+  int m, s;
+  unsigned long long seed;
+};
+
+// out[0] = Frobenius norm of an m x n block.
+struct FrobDesc {
+  const double* A;
+  int ld, m, n;
+  double* out;
 };
 
 }  // namespace ifmm

@@ -61,6 +61,7 @@ struct ifmm_fact {
   std::vector<int> top_off;
   ifmm::SolvePlan plan;
   std::vector<std::array<int, 4>> rank_log;
+  std::vector<float> event_feat;  // rank-predictor inputs of every event, in rank_log order
   std::vector<std::pair<std::string, double>> stats;
   void stat(const std::string& name, double v) {
     for (auto& s : stats)

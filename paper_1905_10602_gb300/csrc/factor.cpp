@@ -28,6 +28,7 @@
 
 #include "fact.h"
 #include "ifmm_kernels.h"
+#include "mlp.h"
 
 namespace ifmm {
 
@@ -96,6 +97,18 @@ struct Event {
   int event_no = 0;
   size_t sig_off[2] = {0, 0};
   int* kdev[2] = {nullptr, nullptr};
+  int trigger = -1;  // eliminated neighbour whose fill-ins caused the event (-1: level start)
+  float feat[IFMM_MLP_IN];
+  int kcap = 0;      // learned cap of the pivoted QR (0: none)
+  // what is needed to redo one side without the cap
+  int gw_idx[2] = {-1, -1};
+  int cf_first[2] = {0, 0}, cf_count[2] = {0, 0};
+  QrcpDesc qd[2];
+  SvdRtDesc sd[2];
+  bool has_qd[2] = {false, false};
+  bool rnd[2] = {false, false};  // randomized range finder (learned mode)
+  double* Y[2] = {nullptr, nullptr};
+  int my[2] = {0, 0};
 };
 
 struct Factorizer {
@@ -117,6 +130,8 @@ struct Factorizer {
   std::vector<double*> pinned_sig;
   double rank_capped = 0;
   double t_wait = 0;
+  float* d_mlp = nullptr;  // rank-predictor weights on the device (learned mode)
+  double n_learned = 0, n_capped = 0, n_fallback = 0, qrcp_steps = 0;
   void wait() {
     auto a = std::chrono::steady_clock::now();
     CK(cudaStreamSynchronize(s));
@@ -129,6 +144,11 @@ struct Factorizer {
     rc = F.rc;
     maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256;
     prec = F.o.precision == IFMM_PREC_FP64 ? P64 : P32;
+    if (F.o.rank_mode == IFMM_RANK_LEARNED) {
+      IFMM_REQUIRE(F.o.mlp != nullptr, IFMM_EINVAL, "learned rank mode needs the MLP weights");
+      CK(cudaMalloc(&d_mlp, sizeof(float) * IFMM_MLP_NWEIGHTS));
+      CK(cudaMemcpy(d_mlp, F.o.mlp, sizeof(float) * IFMM_MLP_NWEIGHTS, cudaMemcpyHostToDevice));
+    }
     if (F.o.rank_mode == IFMM_RANK_REPLAY) {
       IFMM_REQUIRE(F.o.replay != nullptr || F.o.replay_len == 0, IFMM_EINVAL, "replay table is NULL");
       for (int64_t e = 0; e < F.o.replay_len; ++e) {
@@ -177,11 +197,37 @@ struct Factorizer {
     std::vector<QrcpDesc> qp;
     std::vector<GemmDesc> gw;
     std::vector<SvdRtDesc> sr;
-    // contiguous readback buffers: singular values and truncation counts
+    for (auto& ev : evs) {
+      int mf = 0;
+      for (auto& f : ev.f[0]) mf += f.rows;
+      ev.feat[5] = (float)(ev.r_old / 64.0);
+      ev.feat[6] = (float)(mf / 1024.0);
+    }
+    // learned mode: predicted rank of every event -> width of its sketch
+    const bool learned = d_mlp && F.o.eps > 0.0;
+    if (learned && !evs.empty()) {
+      std::vector<float> feat(evs.size() * IFMM_MLP_IN);
+      for (size_t e = 0; e < evs.size(); ++e)
+        memcpy(&feat[e * IFMM_MLP_IN], evs[e].feat, sizeof(float) * IFMM_MLP_IN);
+      float* dx = (float*)scratch.alloc(feat.size() / 2 + 1);
+      float* dy = (float*)scratch.alloc(evs.size() / 2 + 1);
+      CK(cudaMemcpyAsync(dx, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, s));
+      mlp_predict_device(d_mlp, dx, dy, (int)evs.size(), s);
+      std::vector<float> pred(evs.size());
+      CK(cudaMemcpy(pred.data(), dy, sizeof(float) * evs.size(), cudaMemcpyDeviceToHost));
+      for (size_t e = 0; e < evs.size(); ++e) {
+        // sketch width: predicted rank plus oversampling
+        const double k = std::max(0.0, (double)pred[e]) * 64.0;
+        evs[e].kcap = std::max(1, (int)std::ceil(k) + 8);
+        n_learned += 1;
+      }
+    }
+    // contiguous readback buffers: singular values, truncation counts, tails
     size_t sig_total = 0;
     for (auto& ev : evs) sig_total += 2 * (size_t)ev.n;
     double* sig_all = scratch.alloc(std::max<size_t>(sig_total, 1));
     int* kall = (int*)scratch.alloc(evs.size() + 1);
+    double* tail_all = scratch.alloc(2 * evs.size() + 1);
     size_t sig_off = 0;
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
@@ -224,17 +270,38 @@ struct Factorizer {
         if (mw > 0) {
           const Blk& B = ev.b[side];
           // W = Z * B (path A) or R_Z * B (path B); B logical r0 x n
+          ev.gw_idx[side] = (int)gw.size();
           gw.push_back(gmm(Z, mz, 0, B.p, B.ld, B.trans, Y, my, mw, n, r0, 1.0, 0.0));
         }
         int off = mw;
+        ev.cf_first[side] = (int)cf.size();
         for (auto& f : ev.f[side]) {
           cf.push_back(cpy(f.p, f.ld, Y + off, my, f.rows, f.cols, 1.0, 0.0, f.trans));
           off += f.rows;
         }
+        ev.cf_count[side] = (int)cf.size() - ev.cf_first[side];
         ev.V[side] = scratch.alloc((size_t)n * n);
         double* work = scratch.alloc((size_t)n * n);
         int* jp = (int*)scratch.alloc((size_t)n / 2 + 1);
-        qp.push_back(QrcpDesc{Y, my, my, n, tau_rel(n), jp, ev.kdev[side]});
+        QrcpDesc qd;
+        qd.A = Y;
+        qd.ld = my;
+        qd.m = my;
+        qd.n = n;
+        qd.tau_rel = tau_rel(n);
+        qd.jpvt = jp;
+        qd.kout = ev.kdev[side];
+        qd.kcap = 0;
+        qd.pad = 0;
+        qd.tail = tail_all + 2 * e + side;
+        ev.qd[side] = qd;
+        ev.has_qd[side] = true;
+        ev.Y[side] = Y;
+        ev.my[side] = my;
+        // learned mode: a randomized range finder at the predicted rank when it
+        // is clearly narrower than the block; otherwise the exact path
+        ev.rnd[side] = learned && ev.kcap < (3 * n) / 4 && ev.kcap < my;
+        if (!ev.rnd[side]) qp.push_back(qd);
         SvdRtDesc sd;
         sd.A = Y;
         sd.ld = my;
@@ -246,7 +313,8 @@ struct Factorizer {
         sd.pad = 0;
         sd.sig = ev.sig[side];
         sd.work = work;
-        sr.push_back(sd);
+        if (!ev.rnd[side]) sr.push_back(sd);
+        ev.sd[side] = sd;
         const double mm = std::max(my, n), nn = std::min(my, n);
         cnt.qr += 2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0;
         cnt.svd += 6.0 * std::max(ev.nominal_rows[side], n) * std::pow((double)std::min(ev.nominal_rows[side], n), 2) +
@@ -254,6 +322,7 @@ struct Factorizer {
       }
     }
     CK(cudaMemsetAsync(kall, 0, sizeof(int) * (evs.size() * 2 + 0), s));
+    CK(cudaMemsetAsync(tail_all, 0, sizeof(double) * (evs.size() * 2 + 1), s));
     launch_copy(st, cz);
     launch_qr(st, qz, prec);
     cnt.add_gemm(gw);
@@ -261,6 +330,98 @@ struct Factorizer {
     launch_copy(st, cf);
     launch_qrcp(st, qp, prec);
     launch_svd_rt(st, sr, prec);
+    // randomized range finder (Halko, Martinsson, Tropp) at the predicted rank s:
+    // Z = Y^T Omega, Q = orth(Z), B = Y Q, SVD of B -> V = Q V_B; residual
+    // E = Y - B Q^T, whose Frobenius norm bounds what the sketch missed
+    double* enorm_all = scratch.alloc(2 * evs.size() + 1);
+    double* ynorm_all = scratch.alloc(2 * evs.size() + 1);
+    {
+      std::vector<SketchDesc> sk;
+      std::vector<GemmDesc> g1, g2, g3, g4;
+      std::vector<SvdRtDesc> so, sb;
+      std::vector<QrcpDesc> qb;
+      std::vector<CopyDesc> ce, cz0;
+      std::vector<FrobDesc> fr;
+      std::vector<int> widths;
+      std::vector<int*> wdev;
+      int* sarr = (int*)scratch.alloc(evs.size() + 1);
+      for (size_t e = 0; e < evs.size(); ++e)
+        for (int side = 0; side < 2; ++side) {
+          Event& ev = evs[e];
+          if (!ev.rnd[side]) continue;
+          const int n = ev.n, my = ev.my[side], sw = std::min(ev.kcap, n);
+          double* Om = scratch.alloc((size_t)my * sw);
+          double* Zs = scratch.alloc((size_t)n * sw);
+          double* Q = scratch.alloc((size_t)n * n);
+          double* qs = scratch.alloc(n);
+          double* qw = scratch.alloc((size_t)n * n);
+          double* Bm = scratch.alloc((size_t)my * sw);
+          double* VB = scratch.alloc((size_t)sw * sw);
+          double* bw = scratch.alloc((size_t)sw * sw);
+          double* E = scratch.alloc((size_t)my * n);
+          int* jpb = (int*)scratch.alloc((size_t)sw / 2 + 1);
+          int* sdev = sarr + widths.size();
+          widths.push_back(sw);
+          sk.push_back(SketchDesc{Om, my, sw, (unsigned long long)(F.o.seed * 0x100000001B3ull + (uint64_t)ev.key * 2 + side)});
+          g1.push_back(gmm(ev.Y[side], my, 1, Om, my, 0, Zs, n, n, sw, my, 1.0, 0.0));  // Z = Y^T Omega
+          SvdRtDesc o;
+          o.A = Zs;
+          o.ld = n;
+          o.n = n;
+          o.jpvt = nullptr;
+          o.kin = sdev;
+          o.V = Q;
+          o.ldv = n;
+          o.pad = 0;
+          o.sig = qs;
+          o.work = qw;
+          so.push_back(o);                                                                  // Q = orth(Z)
+          g2.push_back(gmm(ev.Y[side], my, 0, Q, n, 0, Bm, my, my, sw, n, 1.0, 0.0));       // B = Y Q
+          QrcpDesc qd = ev.qd[side];
+          qd.A = Bm;
+          qd.ld = my;
+          qd.m = my;
+          qd.n = sw;
+          qd.jpvt = jpb;
+          qb.push_back(qd);
+          SvdRtDesc b = ev.sd[side];
+          b.A = Bm;
+          b.ld = my;
+          b.n = sw;
+          b.jpvt = jpb;
+          b.kin = ev.kdev[side];
+          b.V = VB;
+          b.ldv = sw;
+          b.sig = ev.sig[side];
+          b.work = bw;
+          cz0.push_back(cpy(nullptr, 0, ev.sig[side], n, n, 1));
+          sb.push_back(b);
+          g3.push_back(gmm(Q, n, 0, VB, sw, 0, ev.V[side], n, n, sw, sw, 1.0, 0.0));      // V = Q V_B
+          ce.push_back(cpy(ev.Y[side], my, E, my, my, n));
+          g4.push_back(gmm(Bm, my, 0, Q, n, 1, E, my, my, n, sw, -1.0, 1.0));              // E = Y - B Q^T
+          fr.push_back(FrobDesc{E, my, my, n, enorm_all + 2 * e + side});
+          fr.push_back(FrobDesc{ev.Y[side], my, my, n, ynorm_all + 2 * e + side});
+        }
+      if (!widths.empty()) {
+        CK(cudaMemcpyAsync(sarr, widths.data(), sizeof(int) * widths.size(), cudaMemcpyHostToDevice, s));
+        // B = Y Q is needed twice (pivoted QR destroys it): keep the SVD on a copy
+        launch_sketch(st, sk);
+        cnt.add_gemm(g1);
+        launch_gemm(st, g1, prec);
+        launch_svd_rt(st, so, prec);
+        cnt.add_gemm(g2);
+        launch_gemm(st, g2, prec);
+        launch_copy(st, ce);
+        cnt.add_gemm(g4);
+        launch_gemm(st, g4, prec);
+        launch_frob(st, fr);
+        launch_copy(st, cz0);
+        launch_qrcp(st, qb, prec);
+        launch_svd_rt(st, sb, prec);
+        cnt.add_gemm(g3);
+        launch_gemm(st, g3, prec);
+      }
+    }
     // read back singular values, truncation counts and pivot status
     std::vector<double> hsig(sig_total);
     std::vector<int> hk(2 * evs.size(), 0);
@@ -288,9 +449,50 @@ struct Factorizer {
     for (int i = 0; i < n_inv; ++i)
       IFMM_REQUIRE(hinfo[i] == 0, IFMM_ESINGULAR, "singular pivot block at level " + std::to_string(W.kappa));
     (void)inv_check;
+    if (learned && !evs.empty()) {
+      // a-posteriori check of every sketch: ||Y - B Q^T||_F (>= the 2-norm of
+      // what the range finder missed) must be <= eps * sigma_1; sides that fail
+      // run the exact path on Y, which the randomized path left untouched
+      std::vector<double> en(2 * evs.size()), yn(2 * evs.size());
+      CK(cudaMemcpy(en.data(), enorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(yn.data(), ynorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost));
+      // below 16 units of roundoff of the arithmetic (times ||Y||_F) no
+      // recompression in that arithmetic can certify anything
+      const double unit = prec == P32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+      std::vector<QrcpDesc> rqp;
+      std::vector<SvdRtDesc> rsr;
+      std::vector<std::pair<size_t, int>> redo;
+      for (size_t e = 0; e < evs.size(); ++e)
+        for (int side = 0; side < 2; ++side) {
+          Event& ev = evs[e];
+          if (!ev.rnd[side]) continue;
+          n_capped += 0.5;
+          const double s1 = hsig[ev.sig_off[side]];
+          if (en[2 * e + side] <= std::max(F.o.eps * s1, 16.0 * unit * yn[2 * e + side])) continue;
+          redo.push_back({e, side});
+          rqp.push_back(ev.qd[side]);
+          rsr.push_back(ev.sd[side]);
+        }
+      if (!redo.empty()) {
+        n_fallback += (double)redo.size() * 0.5;
+        launch_qrcp(st, rqp, prec);
+        launch_svd_rt(st, rsr, prec);
+        wait();
+        st.reset();
+        for (auto& rd : redo) {
+          Event& ev = evs[rd.first];
+          CK(cudaMemcpy(hsig.data() + ev.sig_off[rd.second], ev.sig[rd.second], sizeof(double) * ev.n,
+                        cudaMemcpyDeviceToHost));
+          CK(cudaMemcpy(&hk[2 * rd.first + rd.second], ev.kdev[rd.second], sizeof(int), cudaMemcpyDeviceToHost));
+        }
+      }
+    }
     for (size_t e = 0; e < evs.size(); ++e)
       for (int side = 0; side < 2; ++side)
-        if (evs[e].V[side]) evs[e].avail[side] = std::min(evs[e].avail[side], hk[2 * e + side]);
+        if (evs[e].V[side]) {
+          evs[e].avail[side] = std::min(evs[e].avail[side], hk[2 * e + side]);
+          qrcp_steps += hk[2 * e + side];
+        }
     // choose ranks (max of the row and column counts, both sides share it)
     for (auto& ev : evs) {
       std::vector<double> sg[2];
@@ -311,6 +513,7 @@ struct Factorizer {
       }
       ev.k = k;
       F.rank_log.push_back({W.kappa, ev.q, ev.event_no, k});
+      F.event_feat.insert(F.event_feat.end(), ev.feat, ev.feat + IFMM_MLP_IN);
     }
     // T = P2M_old V_row[:, :k], T' = V_col[:, :k]^T L2P_old, then the new bases
     std::vector<GemmDesc> gt;
@@ -335,11 +538,27 @@ struct Factorizer {
     launch_copy(st, cb);
   }
 
-  Event make_event(Work& W, int q) {
+  Event make_event(Work& W, int q, int trigger = -1) {
     Event ev;
     ev.q = q;
     ev.event_no = event_count[q]++;
     ev.key = key3(W.kappa, q, ev.event_no);
+    ev.trigger = trigger;
+    // rank-predictor inputs: cell centre in [-1,1]^3, cell size and level, offset
+    // to the eliminated neighbour, log10(eps)
+    const LevelLists& LL = *W.LL;
+    const double m = (double)((int64_t)1 << W.kappa);
+    int l1 = 0;
+    for (int d = 0; d < 3; ++d) {
+      ev.feat[d] = (float)((LL.cells[3 * q + d] + 0.5) / m * 2.0 - 1.0);
+      if (trigger >= 0) l1 += std::abs(LL.cells[3 * q + d] - LL.cells[3 * trigger + d]);
+    }
+    ev.feat[3] = (float)(W.n[q] / 256.0);          // block size n_q
+    ev.feat[4] = (float)(W.kappa / 10.0);
+    ev.feat[5] = (float)(W.r[q] / 64.0);           // current rank (set by set_event_sizes)
+    ev.feat[6] = 0.f;                              // fill rows (set by set_event_sizes)
+    ev.feat[7] = (float)(l1 / 3.0);                // offset to the eliminated neighbour, L1
+    ev.feat[8] = (float)((F.o.eps > 0 ? std::log10(F.o.eps) : -16.0) / 10.0);
     return ev;
   }
 
@@ -644,17 +863,21 @@ struct Factorizer {
     std::vector<int> slot_of(W.nn, -1);
     std::vector<int> rebase_order;
     std::vector<std::vector<Blk>> rowfill_v, colfill_v;
+    std::vector<int> trigger_of;
+    int cur_i = -1;
     auto rebase_slot = [&](int q) {
       if (slot_of[q] < 0) {
         slot_of[q] = (int)rebase_order.size();
         rebase_order.push_back(q);
         rowfill_v.emplace_back();
         colfill_v.emplace_back();
+        trigger_of.push_back(cur_i);
       }
       return slot_of[q];
     };
     for (int g = 0; g < ng; ++g) {
       const int i = grp[g];
+      cur_i = i;
       const int ni = W.n[i], ri = W.r[i], m = ni + ri;
       const int q0 = LL.nbr_ptr[i], q1 = LL.nbr_ptr[i + 1];
       NodeFactor& nf = LF.nf[i];
@@ -740,7 +963,7 @@ struct Factorizer {
     std::vector<int> pld, lld;
     std::vector<int> r_before(W.r);
     for (int q : rebase_order) {
-      Event ev = make_event(W, q);
+      Event ev = make_event(W, q, trigger_of[slot_of[q]]);
       ev.r_old = W.r[q];
       ev.n = W.n[q];
       const int rq = W.r[q];
@@ -940,10 +1163,15 @@ struct Factorizer {
     F.stat("flops_total", cnt.total());
     F.stat("rank_capped", rank_capped);
     F.stat("time_device_wait", t_wait);
+    F.stat("learned_events", n_learned);
+    F.stat("learned_sketched", n_capped);
+    F.stat("learned_fallbacks", n_fallback);
+    F.stat("qrcp_steps", qrcp_steps);
     F.stat("bytes_factor", (double)F.persist.high);
   }
 
   ~Factorizer() {
+    if (d_mlp) cudaFree(d_mlp);
     if (d_info) {
       registry().remove_range(d_info, sizeof(int) * info_cap);
       cudaFree(d_info);
@@ -1012,6 +1240,19 @@ ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64
   }
   *count = (int64_t)f->rank_log.size() * 4;
   for (int64_t e = 0; e < *count && e < cap && buf; ++e) buf[e] = f->rank_log[e / 4][e % 4];
+  return IFMM_OK;
+}
+
+ifmm_status ifmm_fact_events(const ifmm_fact* f, float* features, int32_t* ranks, int64_t cap, int64_t* count) {
+  if (!f || !count) {
+    set_last_error("NULL argument");
+    return IFMM_EINVAL;
+  }
+  *count = (int64_t)f->rank_log.size();
+  for (int64_t e = 0; e < *count && e < cap; ++e) {
+    if (features) memcpy(features + e * IFMM_MLP_IN, &f->event_feat[e * IFMM_MLP_IN], sizeof(float) * IFMM_MLP_IN);
+    if (ranks) ranks[e] = f->rank_log[e][3];
+  }
   return IFMM_OK;
 }
 

@@ -336,7 +336,7 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     if (!registry().on) continue;
     const SvdRtDesc& x = v[i];
     req(x.A, span(x.n, x.n, x.ld) > 0 ? sizeof(double) : 0, "svd_rt.A", i);
-    req(x.jpvt, sizeof(int) * x.n, "svd_rt.jpvt", i);
+    if (x.jpvt) req(x.jpvt, sizeof(int) * x.n, "svd_rt.jpvt", i);
     req(x.V, span(x.n, x.n, x.ldv), "svd_rt.V", i);
     req(x.sig, sizeof(double) * x.n, "svd_rt.sig", i);
     req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
@@ -351,6 +351,21 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     k_svd_rt<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60, smem);
   check_launch("k_svd_rt");
   profiler().end(kk, st.stream, pe);
+}
+
+void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v) {
+  if (v.empty()) return;
+  const SketchDesc* d = st.push(v);
+  profiler().launches[KK_TABLES] += 1;
+  k_sketch<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
+  check_launch("k_sketch");
+}
+void launch_frob(DescStage& st, const std::vector<FrobDesc>& v) {
+  if (v.empty()) return;
+  const FrobDesc* d = st.push(v);
+  profiler().launches[KK_TABLES] += 1;
+  k_frob<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
+  check_launch("k_frob");
 }
 
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {

@@ -196,6 +196,8 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec);
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v);
 void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec);
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec);
+void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v);
+void launch_frob(DescStage& st, const std::vector<FrobDesc>& v);
 void check_launch(const char* what);
 
 inline CopyDesc cpy(const double* src, int lds, double* dst, int ldd, int rows, int cols, double alpha = 1.0,

@@ -55,6 +55,10 @@ _sig = {
     "bem_matvec": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
     "bem_matvec_noalloc": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
     "ifmm_fact_ranks": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_fact_events": [_vp, _vp, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_mlp_forward": [_vp, _vp, _i64, _vp, _vp],
+    "ifmm_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "ifmm_mlp_train": [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp],
     "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
 }
 for _name, _args in _sig.items():
@@ -263,3 +267,48 @@ def bem_matvec_noalloc(tree: Tree, x, y, kernel: Kernel | None = None, stream=No
     enqueued on the stream."""
     k = kernel if kernel is not None else default_kernel(tree.n)
     _check(lib.bem_matvec_noalloc(tree.h, ctypes.byref(k), _ptr(x), _ptr(y), stream or _stream(x)))
+
+
+MLP_INPUTS = 9
+MLP_NWEIGHTS = 9025
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ifmm_fact_events(fact: Fact):
+    """(features (n, 9) float32, ranks (n,) int32) of every recompression event."""
+    cnt = _i64()
+    _check(lib.ifmm_fact_events(fact.h, None, None, 0, ctypes.byref(cnt)))
+    X = np.zeros((cnt.value, MLP_INPUTS), dtype=np.float32)
+    r = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.ifmm_fact_events(fact.h, _fp(X), _fp(r), cnt.value, ctypes.byref(cnt)))
+    return X, r
+
+
+def ifmm_mlp_forward(weights, X):
+    w, X = _f32(weights), _f32(X)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _check(lib.ifmm_mlp_forward(_fp(w), _fp(X), X.shape[0], _fp(y), None))
+    return y
+
+
+def ifmm_mlp_grad(weights, X, t):
+    w, X, t = _f32(weights), _f32(X), _f32(t)
+    g = np.zeros(MLP_NWEIGHTS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib.ifmm_mlp_grad(_fp(w), _fp(X), _fp(t), X.shape[0], _fp(g), ctypes.byref(loss), None))
+    return float(loss.value), g
+
+
+def ifmm_mlp_train(X, t, epochs=200, batch=4096, lr=1e-3, seed=1):
+    X, t = _f32(X), _f32(t)
+    w = np.zeros(MLP_NWEIGHTS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib.ifmm_mlp_train(_fp(X), _fp(t), X.shape[0], epochs, batch, lr, seed, _fp(w), ctypes.byref(loss), None))
+    return w, float(loss.value)
