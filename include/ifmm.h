@@ -98,6 +98,8 @@ ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors_per_level);
  *   "color"           color per node      "group_ptr" "group"  colors as CSR lists
  *   "perm"            tree order -> caller index (level ignored)
  *   "leaf_ptr"        point CSR of the leaves (level ignored)
+ *   "matvec_block"    source tile of the float-pair matvec chosen by its
+ *                     autotuner on the first such product with this tree (0 before)
  * Writes min(count, cap) int32 values to buf (may be NULL) and the full count to
  * *count. */
 ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int32_t* buf, int64_t cap,
@@ -123,6 +125,25 @@ ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs,
  * b, x: n doubles, host or device (same side).  iters and relres may be NULL. */
 ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact* precond, const double* b,
                       double* x, int restart, double tol, int maxit, int* iters, double* relres, void* stream);
+
+/* Independent problems together (BASELINE's batched workload; the paper factors
+ * one problem at a time).  Problem i uses trees[i], kernels[i], opts[i]; out[i]
+ * receives its factor.  nworkers host threads (<= 0: 8), each with its own CUDA
+ * stream, take problems in index order, so kernels of different problems
+ * overlap on the GPU.  Each factor equals what ifmm_factor gives for the same
+ * problem.  On error every out[i] is NULL and the message names the problem.
+ * Trees are uploaded to the device first, in the calling thread. */
+ifmm_status ifmm_factor_batched(const ifmm_tree* const* trees, const ifmm_kernel* kernels, const ifmm_opts* opts,
+                                int nprob, int nworkers, ifmm_fact** out);
+
+/* bem_gmres for nprob independent problems on worker threads and streams as
+ * above.  b[i], x[i]: N_i doubles (host or device); precond may be NULL (no
+ * preconditioner for any problem) or hold NULL entries; iters/relres may be NULL.
+ * Returns the first failing problem's status (IFMM_ENOCONV if one did not
+ * converge); every x[i] is written. */
+ifmm_status bem_gmres_batched(const ifmm_tree* const* trees, const ifmm_kernel* kernels, const ifmm_fact* const* precond,
+                              const double* const* b, double* const* x, int nprob, int restart, double tol, int maxit,
+                              int* iters, double* relres, int nworkers);
 
 /* y = A x by direct summation on the device (the matrix of bem_gmres).
  * x, y: n doubles, host or device (same side); they must not alias. */

@@ -1123,7 +1123,7 @@ struct Factorizer {
       // the child level's blocks stay alive until this level's initial copies ran
       DeviceArena child_mem;
       child_mem.swap(levelmem);
-      profiler().level_tag = kappa;
+      prof_level_tag() = kappa;
       init_level(*W, kappa, prev.get());
       wait();
       st.reset();
@@ -1148,7 +1148,7 @@ struct Factorizer {
       F.stat("time_level_" + std::to_string(kappa), std::chrono::duration<double>(te - tl).count());
       prev = std::move(W);
     }
-    profiler().level_tag = -1;
+    prof_level_tag() = -1;
     build_solve_plan(F, s);
     CK(cudaStreamSynchronize(s));
     levelmem.release();

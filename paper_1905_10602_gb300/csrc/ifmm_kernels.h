@@ -30,7 +30,9 @@ void launch_m2m_table(cudaStream_t s, double* out, int p);
 void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag);
 void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n);
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
-                      int N, double scale, double diag);
+                      int N, double scale, double diag, int bs);
+int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x,
+                       double* y, int N, double scale, double diag);
 void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::vector<const double*>& terms,
                      const std::vector<int>& first, int r);
 void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta);

@@ -3,6 +3,7 @@
 // plus their launchers.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <thread>
 
 #include "dense.cuh"
@@ -65,11 +66,21 @@ static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "ga
                                            "svd_fp64", "svd_fp32", "gemv", "gemv_sum", "p2p", "interp", "tables",
                                            "matvec", "permute", "gauss_jordan_big", "solve_graph"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
+int& prof_level_tag() {
+  static thread_local int t = -1;
+  return t;
+}
+long& prof_batch_tag() {
+  static thread_local long t = 0;
+  return t;
+}
 Profiler& profiler() {
   static Profiler p;
   return p;
 }
+static std::mutex g_prof_mutex;
 cudaEvent_t Profiler::begin(int kind, cudaStream_t s, long count) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
   launches[kind] += count;
   if (!timing) return nullptr;
   cudaEvent_t e;
@@ -79,14 +90,19 @@ cudaEvent_t Profiler::begin(int kind, cudaStream_t s, long count) {
 }
 void Profiler::end(int kind, cudaStream_t s, cudaEvent_t b) {
   if (!timing || !b) return;
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
   cudaEvent_t e;
   CK(cudaEventCreate(&e));
   CK(cudaEventRecord(e, s));
   pending.push_back({kind, {b, e}});
-  pending_tags.push_back({level_tag, batch_tag});
-  if (pending.size() > 4096) collect();
+  pending_tags.push_back({prof_level_tag(), prof_batch_tag()});
+  if (pending.size() > 4096) collect_locked();
 }
 void Profiler::collect() {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  collect_locked();
+}
+void Profiler::collect_locked() {
   static FILE* log = nullptr;
   static bool log_init = false;
   if (!log_init) {
@@ -109,8 +125,13 @@ void Profiler::collect() {
   pending.clear();
   pending_tags.clear();
 }
+void Profiler::count(int kind, long n) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  launches[kind] += n;
+}
 void Profiler::reset() {
-  collect();
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  collect_locked();
   for (int k = 0; k < KK_COUNT; ++k) {
     launches[k] = 0;
     events_kernels[k] = 0;
@@ -129,7 +150,7 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   check_copy(v);
   std::vector<CopyDesc> small, big;
   for (auto& x : v) ((long)x.rows * x.cols <= 1024 ? small : big).push_back(x);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
   if (!small.empty()) {
     const CopyDesc* d = st.push(small);
@@ -154,7 +175,7 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   if (!small.empty()) {
     const GemmDesc* d = st.push(small);
     const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
-    profiler().batch_tag = (long)small.size();
+    prof_batch_tag() = (long)small.size();
     cudaEvent_t pe = profiler().begin(kk, st.stream);
     if (prec == P32)
       k_gemm_small<float><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
@@ -174,7 +195,7 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   // descriptors with zero tiles are never selected: find_desc returns the last
   // descriptor whose start <= tile, and empty ones share their start with the next
   const GemmDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   const int* p = st.push(tp);
   const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
@@ -194,11 +215,10 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   }
   // size classes: shared-memory Gauss-Jordan for n <= 64 and n <= 160, the
   // batched multi-CTA variant above
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-    attr = true;
-  }
+  });
   std::vector<InvDesc> cls[3];
   for (auto& x : v) cls[x.n <= 64 ? 0 : (x.n <= 160 ? 1 : 2)].push_back(x);
   for (int c = 0; c < 2; ++c) {
@@ -208,7 +228,7 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     const int smem_mat = nmax * nmax * (int)sizeof(double);
     const size_t smem = (size_t)smem_mat + sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
     const InvDesc* d = st.push(cls[c]);
-    profiler().batch_tag = (long)cls[c].size();
+    prof_batch_tag() = (long)cls[c].size();
     cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
     k_inv<<<(unsigned)cls[c].size(), c == 0 ? 128 : 256, smem, st.stream>>>(d, (int)cls[c].size(), smem_mat);
     check_launch("k_inv");
@@ -229,7 +249,7 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     const long* o = st.push(off);
     const int nb = (int)L.size();
     const int gx = (int)std::max<long>(1, std::min<long>((long)nmax * nmax / 1024 + 1, 64));
-    profiler().batch_tag = (long)nb;
+    prof_batch_tag() = (long)nb;
     cudaEvent_t pe = profiler().begin(KK_GJ_BIG, st.stream, 2L * nmax + 1);
     for (int k = 0; k < nmax; ++k) {
       k_gjb_pivot<<<nb, 256, 0, st.stream>>>(d, nb, k, work, o);
@@ -249,7 +269,7 @@ void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qr ld too small");
   }
   const QrDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -265,12 +285,11 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
   int nmax = 0;
   for (auto& x : v) nmax = std::max(nmax, x.n);
   size_t smem = sizeof(double) * nmax + sizeof(int) * nmax + 16;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CK(cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  });
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
     const SvdDesc& x = v[i];
     req(x.G, span(x.m, x.n, x.ldg), "svd.G", i);
@@ -280,7 +299,7 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
     if (x.ldg < x.m || x.ldv < x.n) throw Error(IFMM_EINVAL, "svd ld too small");
   }
   const SvdDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -298,12 +317,11 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   for (auto& x : v) nmax = std::max(nmax, x.n);
   const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
   IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivoted QR too wide");
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_qrcp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CK(cudaFuncSetAttribute(k_qrcp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  });
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
     req(v[i].A, span(v[i].m, v[i].n, v[i].ld), "qrcp.A", i);
     req(v[i].jpvt, sizeof(int) * v[i].n, "qrcp.jpvt", i);
@@ -311,7 +329,7 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qrcp ld too small");
   }
   const QrcpDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -325,12 +343,11 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
   if (v.empty()) return;
   const int smem = 160 * 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_svd_rt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CK(cudaFuncSetAttribute(k_svd_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
-  }
+  });
   for (size_t i = 0; i < v.size(); ++i) {
     IFMM_REQUIRE(v[i].n <= 1024, IFMM_EINVAL, "SVD wider than 1024 columns");
     if (!registry().on) continue;
@@ -342,7 +359,7 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
   }
   const SvdRtDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
@@ -356,14 +373,14 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
 void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v) {
   if (v.empty()) return;
   const SketchDesc* d = st.push(v);
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_sketch<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_sketch");
 }
 void launch_frob(DescStage& st, const std::vector<FrobDesc>& v) {
   if (v.empty()) return;
   const FrobDesc* d = st.push(v);
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_frob<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_frob");
 }
@@ -377,7 +394,7 @@ void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v) {
     req(x.y, sizeof(double) * (x.trans ? x.n : x.m), "gemv.y", i);
   }
   const GemvDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
+  prof_batch_tag() = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_GEMV, st.stream);
   k_gemv<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size());
   check_launch("k_gemv");
@@ -565,11 +582,13 @@ __global__ void k_split_df(const double* __restrict__ in, float* __restrict__ hi
   }
 }
 
-// pts: 6 float arrays (xh, xl, yh, yl, zh, zl) of length n; q: (qh, ql)
-__global__ void __launch_bounds__(256) k_matvec_df(const float* __restrict__ pts, const float* __restrict__ qh,
-                                                   const float* __restrict__ ql, const double* __restrict__ x,
-                                                   double* __restrict__ y, int n, double scale, double diag) {
-  __shared__ float s[8][256];
+// pts: 6 float arrays (xh, xl, yh, yl, zh, zl) of length n; q: (qh, ql).
+// BS threads per CTA = sources per shared-memory tile (autotuned per tree).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_matvec_df(const float* __restrict__ pts, const float* __restrict__ qh,
+                                                  const float* __restrict__ ql, const double* __restrict__ x,
+                                                  double* __restrict__ y, int n, double scale, double diag) {
+  __shared__ float s[8][BS];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const float* xh = pts;
   const float* xl = pts + n;
@@ -615,10 +634,49 @@ void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int
   check_launch("k_split_df");
 }
 
+static void matvec_df_bs(int bs, cudaStream_t s, const float* pts_df, const float* qh, const float* ql,
+                         const double* x, double* y, int N, double scale, double diag) {
+  if (bs == 128)
+    k_matvec_df<128><<<(N + 127) / 128, 128, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  else if (bs == 512)
+    k_matvec_df<512><<<(N + 511) / 512, 512, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  else
+    k_matvec_df<256><<<(N + 255) / 256, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+}
+
+// Autotuner: times each source-tile width twice on the caller's data (after one
+// untimed launch of each) and returns the fastest; y is overwritten.
+int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x,
+                       double* y, int N, double scale, double diag) {
+  const int cand[3] = {128, 256, 512};
+  float best = 1e30f;
+  int pick = 256;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (int c : cand) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag);
+  for (int c : cand) {
+    CK(cudaEventRecord(a, s));
+    for (int r = 0; r < 2; ++r) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag);
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  check_launch("autotune_matvec_df");
+  return pick;
+}
+
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
-                      int N, double scale, double diag) {
+                      int N, double scale, double diag, int bs) {
   cudaEvent_t pe = profiler().begin(KK_MATVEC, s);
-  k_matvec_df<<<(N + 255) / 256, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  matvec_df_bs(bs, s, pts_df, qh, ql, x, y, N, scale, diag);
   check_launch("k_matvec_df");
   profiler().end(KK_MATVEC, s, pe);
 }
@@ -686,7 +744,7 @@ void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::
   double* const* d = st.push(dst);
   const double* const* t = st.push(terms);
   const int* f = st.push(first);
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_gram_sum<<<(unsigned)dst.size(), 256, 0, st.stream>>>(d, t, f, (int)dst.size(), r);
   check_launch("k_gram_sum");
 }
@@ -694,13 +752,12 @@ void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::
 void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta) {
   if (mats.empty()) return;
   IFMM_REQUIRE(r <= 128, IFMM_EINVAL, "Cholesky block too large");
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
-    attr = true;
-  }
+  });
   double* const* d = st.push(mats);
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_chol<<<(unsigned)mats.size(), 256, sizeof(double) * r * r, st.stream>>>(d, (int)mats.size(), r, delta);
   check_launch("k_chol");
 }
@@ -822,8 +879,8 @@ void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts,
       throw Error(IFMM_EINVAL, "p2p point range");
   }
   const P2pDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
-  profiler().launches[KK_P2P] += 1;
+  prof_batch_tag() = (long)v.size();
+  profiler().count(KK_P2P, 1);
   k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
   check_launch("k_p2p");
 }
@@ -835,20 +892,20 @@ void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double
     if (v[i].p0 < 0 || v[i].p0 + v[i].n > N) throw Error(IFMM_EINVAL, "interp point range");
   }
   const InterpDesc* d = st.push(v);
-  profiler().batch_tag = (long)v.size();
-  profiler().launches[KK_INTERP] += 1;
+  prof_batch_tag() = (long)v.size();
+  profiler().count(KK_INTERP, 1);
   k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
   check_launch("k_interp");
 }
 
 void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale) {
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_m2l_table<<<343, 256, 0, s>>>(out, p, h, scale);
   check_launch("k_m2l_table");
 }
 
 void launch_m2m_table(cudaStream_t s, double* out, int p) {
-  profiler().launches[KK_TABLES] += 1;
+  profiler().count(KK_TABLES, 1);
   k_m2m_table<<<8, 256, 0, s>>>(out, p);
   check_launch("k_m2m_table");
 }
@@ -861,12 +918,12 @@ void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, do
 }
 
 void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
-  profiler().launches[KK_PERM] += 1;
+  profiler().count(KK_PERM, 1);
   k_gather_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
   check_launch("k_gather_perm");
 }
 void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
-  profiler().launches[KK_PERM] += 1;
+  profiler().count(KK_PERM, 1);
   k_scatter_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
   check_launch("k_scatter_perm");
 }

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -29,17 +30,22 @@ namespace ifmm {
 struct Registry {
   bool on = false;
   std::map<uintptr_t, uintptr_t> iv;  // start -> end
+  std::mutex mu;
   void add(const void* p, size_t bytes) {
-    if (on) iv[(uintptr_t)p] = (uintptr_t)p + bytes;
+    if (!on) return;
+    std::lock_guard<std::mutex> lock(mu);
+    iv[(uintptr_t)p] = (uintptr_t)p + bytes;
   }
   void remove_range(const void* lo, size_t bytes) {
     if (!on) return;
+    std::lock_guard<std::mutex> lock(mu);
     auto a = iv.lower_bound((uintptr_t)lo);
     auto b = iv.lower_bound((uintptr_t)lo + bytes);
     iv.erase(a, b);
   }
-  bool contains(const void* p, size_t bytes) const {
+  bool contains(const void* p, size_t bytes) {
     if (!on) return true;
+    std::lock_guard<std::mutex> lock(mu);
     uintptr_t lo = (uintptr_t)p, hi = lo + bytes;
     auto it = iv.upper_bound(lo);
     if (it == iv.begin()) return false;
@@ -173,8 +179,6 @@ enum KernelKind {
 };
 struct Profiler {
   bool timing = false;
-  int level_tag = -1;  // level being factored (for the per-launch log)
-  long batch_tag = 0;  // descriptors in the launch being timed
   std::vector<std::pair<int, long>> pending_tags;
   long launches[KK_COUNT] = {0};
   long events_kernels[KK_COUNT] = {0};
@@ -183,9 +187,14 @@ struct Profiler {
   cudaEvent_t begin(int kind, cudaStream_t s, long count = 1);
   void end(int kind, cudaStream_t s, cudaEvent_t b);
   void collect();  // synchronizes pending events and accumulates
+  void collect_locked();
+  void count(int kind, long n);
   void reset();
 };
 Profiler& profiler();
+// per-thread tags of the per-launch log: level being factored, batch size
+int& prof_level_tag();
+long& prof_batch_tag();
 const char* kernel_kind_name(int k);
 
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);

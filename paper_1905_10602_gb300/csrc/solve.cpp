@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "fact.h"
 #include "ifmm_kernels.h"
@@ -254,7 +255,7 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
   if (direct) {  // the same program as individual launches, each timed when profiling
     for (auto& l : P.prog) {
       const int kind = l.kind == 0 ? KK_COPY : (l.kind == 1 ? KK_GEMV : KK_GEMV_SUM);
-      profiler().batch_tag = l.count;
+      prof_batch_tag() = l.count;
       cudaEvent_t pe = profiler().begin(kind, s);
       if (l.kind == 0) launch_copy_dev(s, (const CopyDesc*)l.desc, l.count);
       else if (l.kind == 1) launch_gemv_dev(s, (const GemvDesc*)l.desc, l.count);
@@ -268,6 +269,8 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
   }
   CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
+
+static std::mutex g_tune_mutex;
 
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -428,7 +431,12 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
     if (k->arith == IFMM_ARITH_DF) {
       float* q = (float*)V.get(N);
       launch_split_df(s, a, q, q + N, (int)N);
-      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag);
+      ifmm_tree* tm = const_cast<ifmm_tree*>(t);
+      if (!tm->matvec_block) {
+        tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag);
+        tm->matvec_block_v[0] = tm->matvec_block;
+      }
+      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tm->matvec_block);
     } else {
       launch_matvec(s, t->d_pts, (int)N, a, b, k->scale, k->diag);
     }
@@ -498,7 +506,15 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
     auto Amul = [&](const double* in, double* out) {
       if (df_mv) {
         launch_split_df(s, in, qdf, qdf + N, (int)N);
-        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag);
+        ifmm_tree* tm = const_cast<ifmm_tree*>(t);
+        if (!tm->matvec_block) {
+          std::lock_guard<std::mutex> lock(g_tune_mutex);
+          if (!tm->matvec_block) {
+            tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag);
+            tm->matvec_block_v[0] = tm->matvec_block;
+          }
+        }
+        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tm->matvec_block);
       } else {
         launch_matvec(s, t->d_pts, (int)N, in, out, k->scale, k->diag);
       }

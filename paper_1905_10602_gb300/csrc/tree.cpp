@@ -299,6 +299,8 @@ ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int
     const std::vector<int32_t>* v = nullptr;
     if (w == "perm") {
       v = &t->perm;
+    } else if (w == "matvec_block") {
+      v = &t->matvec_block_v;
     } else if (w == "leaf_ptr") {
       v = &t->leaf_ptr;
     } else {

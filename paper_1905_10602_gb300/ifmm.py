@@ -55,6 +55,9 @@ _sig = {
     "bem_matvec": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
     "bem_matvec_noalloc": [_vp, ctypes.POINTER(Kernel), _vp, _vp, _vp],
     "ifmm_fact_ranks": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_factor_batched": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp],
+    "bem_gmres_batched": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _dbl, ctypes.c_int, _vp, _vp,
+                          ctypes.c_int],
     "ifmm_fact_events": [_vp, _vp, _vp, _i64, ctypes.POINTER(_i64)],
     "ifmm_mlp_forward": [_vp, _vp, _i64, _vp, _vp],
     "ifmm_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
@@ -312,3 +315,43 @@ def ifmm_mlp_train(X, t, epochs=200, batch=4096, lr=1e-3, seed=1):
     loss = ctypes.c_float()
     _check(lib.ifmm_mlp_train(_fp(X), _fp(t), X.shape[0], epochs, batch, lr, seed, _fp(w), ctypes.byref(loss), None))
     return w, float(loss.value)
+
+
+def ifmm_factor_batched(trees, cheb_order: int, eps: float, precision: str = "fp64", rank_mode: str = "svd",
+                        mlp=None, nworkers: int = 8, kernels=None):
+    """Factors independent problems concurrently (one stream per worker)."""
+    n = len(trees)
+    TA = ctypes.c_void_p * n
+    KA = Kernel * n
+    OA = Opts * n
+    ks = KA(*[kernels[i] if kernels else default_kernel(t.n) for i, t in enumerate(trees)])
+    os_ = OA()
+    keep = []
+    for i in range(n):
+        os_[i].cheb_order, os_[i].eps, os_[i].precision = cheb_order, eps, PREC[precision]
+        os_[i].rank_mode = RANK_MODE[rank_mode]
+        if mlp is not None:
+            w = np.ascontiguousarray(np.asarray(mlp, dtype=np.float32))
+            keep.append(w)
+            os_[i].mlp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    outs = TA()
+    _check(lib.ifmm_factor_batched(TA(*[t.h for t in trees]), ks, os_, n, nworkers, outs))
+    return [Fact(ctypes.c_void_p(outs[i]), trees[i]) for i in range(n)]
+
+
+def bem_gmres_batched(trees, bs, facts=None, restart: int = 30, tol: float = 1e-8, maxit: int = 500,
+                      kernels=None, nworkers: int = 8, raise_on_noconv: bool = True):
+    """GMRES for independent problems concurrently; returns (xs, iters, relres)."""
+    n = len(trees)
+    TA = ctypes.c_void_p * n
+    ks = (Kernel * n)(*[kernels[i] if kernels else default_kernel(t.n) for i, t in enumerate(trees)])
+    bs = [np.ascontiguousarray(np.asarray(b, dtype=np.float64)) for b in bs]
+    xs = [np.empty_like(b) for b in bs]
+    its = (ctypes.c_int * n)()
+    rel = (ctypes.c_double * n)()
+    pre = TA(*[f.h if f is not None else None for f in facts]) if facts else None
+    code = lib.bem_gmres_batched(TA(*[t.h for t in trees]), ks, pre, TA(*[_ptr(b).value for b in bs]),
+                                 TA(*[_ptr(x).value for x in xs]), n, restart, tol, maxit, its, rel, nworkers)
+    if code != 5 or raise_on_noconv:
+        _check(code)
+    return xs, list(its), list(rel)
