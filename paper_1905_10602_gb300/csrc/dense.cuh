@@ -726,6 +726,418 @@ __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
   }
 }
 
+// ---------------------------------------------------------------- Householder QR in shared memory
+// The factorisations of k_qr (PIV = false) and k_qrcp (PIV = true) for blocks
+// that fit in shared memory in the arithmetic type TC: the block is read from
+// global memory once, factorised in shared memory, and written back once.
+// On the way in it is multiplied by a power of two (exact) that brings its
+// largest magnitude into [0.5, 1): squared column norms of FP32 blocks whose
+// entries are ~1e-12 would otherwise fall out of the FP32 normal range.  R is
+// scaled back (exactly) on the way out.  The Householder vector of step k,
+// v_0 = 1, v_i = sc x_i, is formed on the fly from the untouched column and
+// never stored; the column is zeroed below the diagonal on write-back.  The
+// norm of every pivot candidate is downdated right after its column has been
+// updated, in the same pass.
+// Slot of one problem: A (m x n, ld m) | nrm (n) | ref (n), in TC | jp (n ints).
+__host__ __device__ __forceinline__ size_t qr_slot_bytes(int m, int n, int tc_bytes) {
+  return (((size_t)m * n + 2 * (size_t)n) * tc_bytes + sizeof(int) * (size_t)n + 15) & ~(size_t)15;
+}
+
+// power of two that maps gmax into [0.5, 1); 1 for zero or non-finite gmax
+__device__ __forceinline__ double pow2_scale(double gmax) {
+  if (!(gmax > 0.0) || !(gmax < 1e300)) return 1.0;
+  int e;
+  frexp(gmax, &e);
+  return ldexp(1.0, -e);
+}
+
+__device__ __forceinline__ double warp_max_nan(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (ov > v || ov != ov) ? ov : v;
+  }
+  return v;
+}
+
+// physical row of logical row i (QrcpDesc::rb, rs)
+__device__ __forceinline__ long qr_row(const QrcpDesc& D, int i) {
+  return D.rb > 0 ? (long)(i / D.rb) * D.rs + i % D.rb : (long)i;
+}
+
+// One warp per problem; blockDim.x / 32 problems per CTA; slot_bytes of
+// dynamic shared memory per warp.  Only __syncwarp is used.
+template <typename TC, bool PIV>
+__global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int di = blockIdx.x * (blockDim.x >> 5) + w;
+  if (di >= nd) return;
+  const QrcpDesc D = d[di];
+  const int m = D.m, n = D.n;
+  const long ld = D.ld;
+  const int mn = m * n;
+  TC* A = (TC*)(qsm + (size_t)w * slot_bytes);
+  TC* nrm = A + mn;
+  TC* ref = nrm + n;
+  int* jp = (int*)(ref + n);
+  double gmax = 0.0;
+  for (int e = lane; e < mn; e += 32) {
+    const double a = fabs(D.A[qr_row(D, e % m) + (long)(e / m) * ld]);
+    gmax = (a > gmax || a != a) ? a : gmax;
+  }
+  const double s_in = pow2_scale(warp_max_nan(gmax));
+  for (int e = lane; e < mn; e += 32) A[e] = (TC)(D.A[qr_row(D, e % m) + (long)(e / m) * ld] * s_in);
+  __syncwarp();
+  if (PIV) {
+    for (int j = 0; j < n; ++j) {
+      const TC* c = A + (size_t)j * m;
+      TC ss = 0;
+      for (int i = lane; i < m; i += 32) ss += c[i] * c[i];
+      ss = warp_sum_t<TC>(ss);
+      if (lane == 0) {
+        nrm[j] = ss;
+        ref[j] = ss;
+        jp[j] = j;
+      }
+    }
+    __syncwarp();
+  }
+  const int kmax = m < n ? m : n;
+  TC tau2 = 0, first = 0;
+  double tailv = 0.0;
+  bool capped = false;
+  int k = 0;
+  for (; k < kmax; ++k) {
+    if (PIV) {
+      TC best = -1;
+      int bi = n;
+      for (int j = k + lane; j < n; j += 32) {
+        const TC v = nrm[j];
+        if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const TC ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (k == 0) {
+        tau2 = (TC)(D.tau_rel * D.tau_rel) * best;
+        first = best;
+      }
+      bool stop = !(best > tau2) || !(best > (TC)0) || bi >= n;
+      if (!stop && D.kcap > 0 && k >= D.kcap) {
+        stop = true;
+        capped = true;
+        tailv = (first > (TC)0) ? sqrt((double)best / (double)first) : 0.0;
+      }
+      if (stop) break;
+      if (bi != k) {
+        TC* ck = A + (size_t)k * m;
+        TC* cp = A + (size_t)bi * m;
+        for (int i = lane; i < m; i += 32) {
+          const TC t = ck[i];
+          ck[i] = cp[i];
+          cp[i] = t;
+        }
+        if (lane == 0) {
+          TC t = nrm[k]; nrm[k] = nrm[bi]; nrm[bi] = t;
+          t = ref[k]; ref[k] = ref[bi]; ref[bi] = t;
+          const int q = jp[k]; jp[k] = jp[bi]; jp[bi] = q;
+        }
+        __syncwarp();
+      }
+    }
+    TC* x = A + k + (size_t)k * m;
+    const int len = m - k;
+    TC ss = 0;
+    for (int i = lane; i < len; i += 32)
+      if (i > 0) ss += x[i] * x[i];
+    ss = warp_sum_t<TC>(ss);
+    const TC x0 = x[0];
+    const TC nr = sqrt(x0 * x0 + ss);
+    TC alpha = x0, tau = 0, sc = 0;
+    if (!(nr == (TC)0 || ss == (TC)0)) {
+      alpha = (x0 >= (TC)0) ? -nr : nr;
+      tau = (alpha - x0) / alpha;
+      sc = (TC)1 / (x0 - alpha);
+    }
+    for (int j = k + 1; j < n; ++j) {
+      TC* y = A + k + (size_t)j * m;
+      TC nj = 0, rj = 0;
+      if (PIV) {
+        nj = nrm[j];
+        rj = ref[j];
+      }
+      if (tau != (TC)0) {
+        TC dot = 0;
+        for (int i = lane; i < len; i += 32) dot += (i == 0 ? (TC)1 : sc * x[i]) * y[i];
+        dot = warp_sum_t<TC>(dot) * tau;
+        for (int i = lane; i < len; i += 32) y[i] -= dot * (i == 0 ? (TC)1 : sc * x[i]);
+      }
+      if (PIV) {
+        const TC r = __shfl_sync(0xffffffffu, lane == 0 ? y[0] : (TC)0, 0);
+        TC nv = nj - r * r;
+        if (!(nv > (TC)1e-2 * rj)) {  // two digits lost: recompute from the column
+          TC s2 = 0;
+          for (int i = lane; i < len; i += 32)
+            if (i > 0) s2 += y[i] * y[i];
+          nv = warp_sum_t<TC>(s2);
+          if (lane == 0) ref[j] = nv;
+        }
+        if (lane == 0) nrm[j] = nv;
+      }
+    }
+    if (lane == 0) x[0] = alpha;
+    __syncwarp();
+  }
+  const double s_out = 1.0 / s_in;
+  for (int e = lane; e < mn; e += 32) {
+    const int i = e % m, j = e / m;
+    const TC v = (j < k && i > j) ? (TC)0 : A[e];
+    D.A[qr_row(D, i) + (long)j * ld] = (double)v * s_out;
+  }
+  if (PIV) {
+    for (int j = lane; j < n; j += 32) D.jpvt[j] = jp[j];
+    if (lane == 0) {
+      D.kout[0] = k;
+      if (D.tail) D.tail[0] = (k < kmax && capped) ? tailv : 0.0;
+    }
+  }
+}
+
+// One CTA (<= 256 threads) per problem, the block in dynamic shared memory.
+// Per column step: one barrier for the pivot search, one after a column swap,
+// one for the reflector norm, one between the segment dot products and the
+// update, and one closing the step (plus one more in the rare step where a
+// downdated norm has to be recomputed).
+template <typename TC, bool PIV>
+__global__ void __launch_bounds__(256) k_qr_cta(const QrcpDesc* __restrict__ d, int nd) {
+  if ((int)blockIdx.x >= nd) return;
+  const QrcpDesc D = d[blockIdx.x];
+  const int m = D.m, n = D.n;
+  const long ld = D.ld;
+  const int mn = m * n;
+  extern __shared__ __align__(16) unsigned char qsm[];
+  TC* A = (TC*)qsm;
+  TC* nrm = A + mn;
+  TC* ref = nrm + n;
+  int* jp = (int*)(ref + n);
+  __shared__ TC part[8];
+  __shared__ unsigned char flag[1024];
+  __shared__ TC red_s[8], red_v[8];
+  __shared__ int red_i[8];
+  __shared__ double red_g[8];
+  const int tid = threadIdx.x, nt_ = blockDim.x;
+  const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
+  double gmax = 0.0;
+  for (int e = tid; e < mn; e += nt_) {
+    const double a = fabs(D.A[qr_row(D, e % m) + (long)(e / m) * ld]);
+    gmax = (a > gmax || a != a) ? a : gmax;
+  }
+  gmax = warp_max_nan(gmax);
+  if (lane == 0) red_g[w] = gmax;
+  __syncthreads();
+  gmax = 0.0;
+  for (int i = 0; i < nw; ++i) gmax = (red_g[i] > gmax || red_g[i] != red_g[i]) ? red_g[i] : gmax;
+  const double s_in = pow2_scale(gmax);
+  for (int e = tid; e < mn; e += nt_) A[e] = (TC)(D.A[qr_row(D, e % m) + (long)(e / m) * ld] * s_in);
+  for (int j = tid; j < n; j += nt_) flag[j] = 0;
+  __syncthreads();
+  if (PIV) {
+    for (int j = w; j < n; j += nw) {
+      const TC* c = A + (size_t)j * m;
+      TC ss = 0;
+      for (int i = lane; i < m; i += 32) ss += c[i] * c[i];
+      ss = warp_sum_t<TC>(ss);
+      if (lane == 0) {
+        nrm[j] = ss;
+        ref[j] = ss;
+        jp[j] = j;
+      }
+    }
+    __syncthreads();
+  }
+  const int kmax = m < n ? m : n;
+  TC tau2 = 0, first = 0;
+  double tailv = 0.0;
+  bool capped = false;
+  int k = 0;
+  for (; k < kmax; ++k) {
+    if (PIV) {
+      TC best = -1;
+      int bi = n;
+      for (int j = k + tid; j < n; j += nt_) {
+        const TC v = nrm[j];
+        if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const TC ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        red_v[w] = best;
+        red_i[w] = bi;
+      }
+      __syncthreads();
+      best = -1;
+      bi = n;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > best || (red_v[i] == best && red_i[i] < bi)) { best = red_v[i]; bi = red_i[i]; }
+      if (k == 0) {
+        tau2 = (TC)(D.tau_rel * D.tau_rel) * best;
+        first = best;
+      }
+      bool stop = !(best > tau2) || !(best > (TC)0) || bi >= n;
+      if (!stop && D.kcap > 0 && k >= D.kcap) {
+        stop = true;
+        capped = true;
+        tailv = (first > (TC)0) ? sqrt((double)best / (double)first) : 0.0;
+      }
+      if (stop) break;
+      if (bi != k) {
+        TC* ck = A + (size_t)k * m;
+        TC* cp = A + (size_t)bi * m;
+        for (int i = tid; i < m; i += nt_) {
+          const TC t = ck[i];
+          ck[i] = cp[i];
+          cp[i] = t;
+        }
+        if (tid == 0) {
+          TC t = nrm[k]; nrm[k] = nrm[bi]; nrm[bi] = t;
+          t = ref[k]; ref[k] = ref[bi]; ref[bi] = t;
+          const int q = jp[k]; jp[k] = jp[bi]; jp[bi] = q;
+        }
+        __syncthreads();
+      }
+    }
+    TC* x = A + k + (size_t)k * m;
+    const int len = m - k;
+    TC ss = 0;
+    for (int i = tid; i < len; i += nt_)
+      if (i > 0) ss += x[i] * x[i];
+    ss = warp_sum_t<TC>(ss);
+    if (lane == 0) red_s[w] = ss;
+    __syncthreads();
+    ss = 0;
+    for (int i = 0; i < nw; ++i) ss += red_s[i];
+    const TC x0 = x[0];
+    const TC nr = sqrt(x0 * x0 + ss);
+    TC alpha = x0, tau = 0, sc = 0;
+    if (!(nr == (TC)0 || ss == (TC)0)) {
+      alpha = (x0 >= (TC)0) ? -nr : nr;
+      tau = (alpha - x0) / alpha;
+      sc = (TC)1 / (x0 - alpha);
+    }
+    const int ntr = n - k - 1;
+    int need = 0;
+    if (ntr > 0 && tau != (TC)0) {
+      // a trailing column is split into S row segments when there are fewer
+      // columns than warps (then ntr * S <= nw); segment sums are added in a
+      // fixed order
+      int S = nw / ntr;
+      const int smax = (len + 63) / 64;
+      if (S > smax) S = smax;
+      if (S < 1) S = 1;
+      if (S == 1) {
+        for (int j = k + 1 + w; j < n; j += nw) {
+          TC* y = A + k + (size_t)j * m;
+          TC dot = 0;
+          for (int i = lane; i < len; i += 32) dot += (i == 0 ? (TC)1 : sc * x[i]) * y[i];
+          dot = warp_sum_t<TC>(dot) * tau;
+          for (int i = lane; i < len; i += 32) y[i] -= dot * (i == 0 ? (TC)1 : sc * x[i]);
+          if (PIV && lane == 0) {
+            const TC r = y[0];
+            const TC nv = nrm[j] - r * r;
+            nrm[j] = nv;
+            if (!(nv > (TC)1e-2 * ref[j])) {
+              flag[j] = 1;
+              need = 1;
+            }
+          }
+        }
+      } else {
+        const int seg = (len + S - 1) / S;
+        const int items = ntr * S;
+        for (int it = w; it < items; it += nw) {
+          const int jj = it / S, sg = it % S;
+          const TC* y = A + k + (size_t)(k + 1 + jj) * m;
+          const int r0 = sg * seg, r1 = min(len, r0 + seg);
+          TC dot = 0;
+          for (int i = r0 + lane; i < r1; i += 32) dot += (i == 0 ? (TC)1 : sc * x[i]) * y[i];
+          dot = warp_sum_t<TC>(dot);
+          if (lane == 0) part[it] = dot;
+        }
+        __syncthreads();
+        for (int it = w; it < items; it += nw) {
+          const int jj = it / S, sg = it % S;
+          const int j = k + 1 + jj;
+          TC* y = A + k + (size_t)j * m;
+          TC dot = 0;
+          for (int q = 0; q < S; ++q) dot += part[jj * S + q];
+          dot *= tau;
+          const int r0 = sg * seg, r1 = min(len, r0 + seg);
+          for (int i = r0 + lane; i < r1; i += 32) y[i] -= dot * (i == 0 ? (TC)1 : sc * x[i]);
+          if (PIV && sg == 0 && lane == 0) {
+            const TC r = y[0];
+            const TC nv = nrm[j] - r * r;
+            nrm[j] = nv;
+            if (!(nv > (TC)1e-2 * ref[j])) {
+              flag[j] = 1;
+              need = 1;
+            }
+          }
+        }
+      }
+    } else if (PIV && ntr > 0) {
+      for (int j = k + 1 + tid; j < n; j += nt_) {
+        const TC r = A[k + (size_t)j * m];
+        const TC nv = nrm[j] - r * r;
+        nrm[j] = nv;
+        if (!(nv > (TC)1e-2 * ref[j])) {
+          flag[j] = 1;
+          need = 1;
+        }
+      }
+    }
+    const int any = __syncthreads_or(need);
+    if (PIV && any) {  // two digits lost: recompute those norms from the columns
+      for (int j = k + 1 + w; j < n; j += nw) {
+        if (!flag[j]) continue;
+        const TC* y = A + k + (size_t)j * m;
+        TC s2 = 0;
+        for (int i = lane; i < len; i += 32)
+          if (i > 0) s2 += y[i] * y[i];
+        s2 = warp_sum_t<TC>(s2);
+        if (lane == 0) {
+          nrm[j] = s2;
+          ref[j] = s2;
+          flag[j] = 0;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) x[0] = alpha;
+  }
+  __syncthreads();
+  const double s_out = 1.0 / s_in;
+  for (int e = tid; e < mn; e += nt_) {
+    const int i = e % m, j = e / m;
+    const TC v = (j < k && i > j) ? (TC)0 : A[e];
+    D.A[qr_row(D, i) + (long)j * ld] = (double)v * s_out;
+  }
+  if (PIV) {
+    for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
+    if (tid == 0) {
+      D.kout[0] = k;
+      if (D.tail) D.tail[0] = (k < kmax && capped) ? tailv : 0.0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- Jacobi on P R_k^T
 // B (n x k, column-major, ld n) lives in dynamic shared memory when it fits in
 // smem_bytes, else in the descriptor's global work buffer.  Columns are rotated

@@ -90,6 +90,8 @@ struct QrcpDesc {
   int pad;
   double* tail;  // out (may be NULL): largest remaining column norm / largest
                  // initial column norm when stopped by kcap, else 0
+  int rb, rs;    // rb > 0: row i of the logical matrix is row (i / rb) * rs + i % rb
+                 // of A (stacked rb-row blocks rs rows apart); rb = 0: row i
 };
 
 // Right singular vectors of Y from its truncated pivoted QR (Y P ~ Q R_k):

@@ -50,6 +50,10 @@ struct Work {
   std::vector<double*> far;  // indexed by position in the IL CSR
   std::vector<double*> P2M, L2P, M2M, L2L;
   std::vector<int> choff;  // offset of this node's y inside its parent's x
+  std::vector<int> il_T;   // il_T[e] = position of (b, a) for the IL entry e = (a, b)
+  std::vector<int> il_row; // il_row[e] = a for the IL entry e = (a, b)
+  std::vector<char> touched;  // per IL entry, cleared after every use
+  std::vector<int> mark;      // per node, -1 outside a lookup scope
   int slot(int p, int q) const {
     if (p == q) return slot_ptr[p];
     const int* b = LL->nbr.data() + LL->nbr_ptr[p];
@@ -125,6 +129,22 @@ struct Factorizer {
   std::unordered_map<int64_t, int> replay;
   std::vector<int> event_count;
   Counter cnt;
+  // descriptor lists rebuilt for every color; members so that their capacity
+  // survives from one color to the next (cleared before each use)
+  struct Lists {
+    std::vector<CopyDesc> cz, cf, cpi, cg, sc, bc1, bc2, cc, cb;
+    std::vector<QrDesc> qz;
+    std::vector<QrcpDesc> qp;
+    std::vector<GemmDesc> gw, gx, gf, b1, b2, c1, c2, gt;
+    std::vector<SvdRtDesc> sr;
+    std::vector<InvDesc> inv;
+    std::vector<int> tl;
+  } L;
+  template <class V>
+  static V& fresh(V& v) {
+    v.clear();
+    return v;
+  }
   int* d_info = nullptr;
   int info_cap = 0;
   std::vector<double*> pinned_sig;
@@ -132,6 +152,12 @@ struct Factorizer {
   double t_wait = 0;
   float* d_mlp = nullptr;  // rank-predictor weights on the device (learned mode)
   double n_learned = 0, n_capped = 0, n_fallback = 0, qrcp_steps = 0;
+  // host wall time of a factorization phase, accumulated into a stat
+  void phase(const char* name, std::chrono::steady_clock::time_point& t) {
+    const auto now = std::chrono::steady_clock::now();
+    F.stat_add(name, std::chrono::duration<double>(now - t).count());
+    t = now;
+  }
   void wait() {
     auto a = std::chrono::steady_clock::now();
     CK(cudaStreamSynchronize(s));
@@ -192,11 +218,12 @@ struct Factorizer {
   void run_events(std::vector<Event>& evs, Work& W, const std::vector<double*>& P2M_out,
                   const std::vector<double*>& L2P_out, const std::vector<int>& P2M_ld, const std::vector<int>& L2P_ld,
                   std::vector<InvDesc>* inv_check, int n_inv) {
-    std::vector<CopyDesc> cz, cf;
-    std::vector<QrDesc> qz;
-    std::vector<QrcpDesc> qp;
-    std::vector<GemmDesc> gw;
-    std::vector<SvdRtDesc> sr;
+    auto& cz = fresh(L.cz);
+    auto& cf = fresh(L.cf);
+    auto& qz = fresh(L.qz);
+    auto& qp = fresh(L.qp);
+    auto& gw = fresh(L.gw);
+    auto& sr = fresh(L.sr);
     for (auto& ev : evs) {
       int mf = 0;
       for (auto& f : ev.f[0]) mf += f.rows;
@@ -293,6 +320,8 @@ struct Factorizer {
         qd.kout = ev.kdev[side];
         qd.kcap = 0;
         qd.pad = 0;
+        qd.rb = 0;
+        qd.rs = 0;
         qd.tail = tail_all + 2 * e + side;
         ev.qd[side] = qd;
         ev.has_qd[side] = true;
@@ -516,8 +545,8 @@ struct Factorizer {
       F.event_feat.insert(F.event_feat.end(), ev.feat, ev.feat + IFMM_MLP_IN);
     }
     // T = P2M_old V_row[:, :k], T' = V_col[:, :k]^T L2P_old, then the new bases
-    std::vector<GemmDesc> gt;
-    std::vector<CopyDesc> cb;
+    auto& gt = fresh(L.gt);
+    auto& cb = fresh(L.cb);
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
       const int k = ev.k, n = ev.n, r0 = ev.r_old;
@@ -589,6 +618,16 @@ struct Factorizer {
     W.r.assign(nn, 0);
     W.elim.assign(nn, 0);
     event_count.assign(nn, 0);
+    W.il_row.assign(LL.il.size(), 0);
+    W.il_T.assign(LL.il.size(), -1);
+    W.touched.assign(LL.il.size(), 0);
+    W.mark.assign(nn, -1);
+    for (int a = 0; a < nn; ++a)
+      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+        W.il_row[e] = a;
+        W.il_T[e] = W.farix(LL.il[e], a);
+        IFMM_REQUIRE(W.il_T[e] >= 0, IFMM_EINVAL, "internal: interaction list not symmetric");
+      }
     // near slots
     W.slot_ptr.assign(nn + 1, 0);
     for (int i = 0; i < nn; ++i) W.slot_ptr[i + 1] = W.slot_ptr[i] + 1 + (LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]);
@@ -781,7 +820,7 @@ struct Factorizer {
       }
       ev.b[0] = Blk{P2M0[q], rc, rc, W.n[q], 0};
       ev.b[1] = Blk{L2P0[q], W.n[q], rc, W.n[q], 1};
-      evs.push_back(ev);
+      evs.push_back(std::move(ev));
       po.push_back(W.P2M[q]);
       lo.push_back(W.L2P[q]);
       pld.push_back(W.capr[q]);
@@ -817,6 +856,7 @@ struct Factorizer {
   // ------------------------------------------------------------------ one color
   void eliminate_color(Work& W, const std::vector<int>& grp, LevelFactor& LF) {
     const LevelLists& LL = *W.LL;
+    auto tp = std::chrono::steady_clock::now();
     scratch.reset();
     const int ng = (int)grp.size();
     if (info_cap < ng) {
@@ -829,8 +869,8 @@ struct Factorizer {
       registry().add(d_info, sizeof(int) * info_cap);
     }
     // ---- pivots
-    std::vector<CopyDesc> cpi;
-    std::vector<InvDesc> inv;
+    auto& cpi = fresh(L.cpi);
+    auto& inv = fresh(L.inv);
     std::vector<double*> Pi(ng);
     for (int g = 0; g < ng; ++g) {
       const int i = grp[g];
@@ -849,13 +889,17 @@ struct Factorizer {
     CK(cudaMemsetAsync(d_info, 0, sizeof(int) * ng, s));
     launch_copy(st, cpi);
     launch_inv(st, inv);
+    phase("host_pivots", tp);
     // ---- Schur complements of the cliques
-    std::vector<CopyDesc> cg, sc;
-    std::vector<GemmDesc> gx, gf;
+    auto& cg = fresh(L.cg);
+    auto& sc = fresh(L.sc);
+    auto& gx = fresh(L.gx);
+    auto& gf = fresh(L.gf);
     struct FarFill {
       int a, b;
       const double* Fp;
       int ld, rows, cols;
+      int fx;  // position of (a, b) in the IL CSR
     };
     std::vector<FarFill> fills;
     // per-node fill lists, indexed through the order in which nodes first
@@ -923,6 +967,9 @@ struct Factorizer {
       for (size_t a = 0; a < nf.nb.size(); ++a) {
         const int q = nf.nb[a];
         const int mq = dims[a];
+        // O(1) slot lookups of q's near blocks in the pair loop below
+        W.mark[q] = W.slot_ptr[q];
+        for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) W.mark[LL.nbr[e]] = W.slot_ptr[q] + 1 + (e - LL.nbr_ptr[q]);
         // row-var(q) x y_i  <- L A12
         if (mq && ri && ni)
           sc.push_back(cpy(X + roff[a] + (long)ni * M, M, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
@@ -938,16 +985,20 @@ struct Factorizer {
           const int mq2 = dims[b2];
           if (!mq || !mq2 || !ni) continue;
           const double* src = Fm + roff[a] + (long)roff[b2] * M;
-          if (q == q2 || W.slot(q, q2) >= 0) {
+          const int sl = W.mark[q2];
+          if (sl >= 0) {
             const int stg = W.elim[q] + W.elim[q2];
-            sc.push_back(cpy(src, M, W.nb[stg][W.slot(q, q2)], W.n[q], mq, mq2, 1.0, 1.0));
+            sc.push_back(cpy(src, M, W.nb[stg][sl], W.n[q], mq, mq2, 1.0, 1.0));
           } else {
-            IFMM_REQUIRE(W.farix(q, q2) >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
-            fills.push_back(FarFill{q, q2, src, M, mq, mq2});
+            const int fx = W.farix(q, q2);
+            IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
+            fills.push_back(FarFill{q, q2, src, M, mq, mq2, fx});
             if (!W.elim[q]) colfill_v[rebase_slot(q)].push_back(Blk{src, M, mq2, W.n[q], 1});
             if (!W.elim[q2]) rowfill_v[rebase_slot(q2)].push_back(Blk{src, M, mq, W.n[q2], 0});
           }
         }
+        W.mark[q] = -1;
+        for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) W.mark[LL.nbr[e]] = -1;
       }
     }
     for (int g = 0; g < ng; ++g) W.elim[grp[g]] = 1;
@@ -957,6 +1008,7 @@ struct Factorizer {
     launch_gemm(st, gx, prec);
     launch_gemm(st, gf, prec);
     launch_copy(st, sc);
+    phase("host_schur", tp);
     // ---- recompression events (snapshots: nothing below reads what phase A changes)
     std::vector<Event> evs;
     std::vector<double*> po, lo;
@@ -967,11 +1019,13 @@ struct Factorizer {
       ev.r_old = W.r[q];
       ev.n = W.n[q];
       const int rq = W.r[q];
+      ev.z[0].reserve(LL.il_ptr[q + 1] - LL.il_ptr[q] + 1);
+      ev.z[1].reserve(LL.il_ptr[q + 1] - LL.il_ptr[q] + 1);
       for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
         const int l = LL.il[e];
         const int rl = W.r[l];
         if (!rl || !rq) continue;
-        const int fl = W.farix(l, q);
+        const int fl = W.il_T[e];
         ev.z[0].push_back(Blk{W.far[fl], W.capr[l], rl, rq, 0});      // M2L_lq
         ev.z[1].push_back(Blk{W.far[e], W.capr[q], rl, rq, 1});       // M2L_ql^T
       }
@@ -983,13 +1037,17 @@ struct Factorizer {
       ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
       ev.f[0] = std::move(rowfill_v[slot_of[q]]);
       ev.f[1] = std::move(colfill_v[slot_of[q]]);
-      evs.push_back(ev);
+      evs.push_back(std::move(ev));
       po.push_back(W.P2M[q]);
       lo.push_back(W.L2P[q]);
       pld.push_back(W.capr[q]);
       lld.push_back(W.n[q]);
     }
+    phase("host_events", tp);
+    const double w0 = t_wait;
     run_events(evs, W, po, lo, pld, lld, nullptr, ng);
+    F.stat_add("host_run_events_wait", t_wait - w0);
+    phase("host_run_events", tp);
     // ---- phase B: re-express blocks that touch a re-based node
     std::vector<int> newk(W.nn, -1);
     std::vector<const Event*> evof(W.nn, nullptr);
@@ -997,15 +1055,19 @@ struct Factorizer {
       newk[ev.q] = ev.k;
       evof[ev.q] = &ev;
     }
-    std::vector<GemmDesc> b1, b2;
-    std::vector<CopyDesc> bc1, bc2;
-    std::vector<char> touched(LL.il.size(), 0);
+    auto& b1 = fresh(L.b1);
+    auto& b2 = fresh(L.b2);
+    auto& bc1 = fresh(L.bc1);
+    auto& bc2 = fresh(L.bc2);
+    auto& tl = fresh(L.tl);  // IL entries with an endpoint re-based in this color
     for (auto& ev : evs) {
       const int q = ev.q;
       for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
-        touched[e] = 1;
-        const int fl = W.farix(LL.il[e], q);
-        touched[fl] = 1;
+        for (const int x : {e, W.il_T[e]})
+          if (!W.touched[x]) {
+            W.touched[x] = 1;
+            tl.push_back(x);
+          }
       }
       if (W.kappa > 2 && ev.k && ev.r_old) {
         double* t1 = scratch.alloc((size_t)rc * ev.k);
@@ -1016,42 +1078,44 @@ struct Factorizer {
         bc1.push_back(cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc));
       }
     }
-    for (int a = 0; a < W.nn; ++a)
-      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
-        if (!touched[e]) continue;
-        const int b = LL.il[e];
-        const int ra = r_before[a], rb = r_before[b];
-        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
-        if (!ka || !kb) continue;
-        double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
-        if (!ra || !rb) {
-          bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
-          continue;
-        }
-        if (newk[a] >= 0)
-          b1.push_back(gmm(evof[a]->Tp, ka, 0, W.far[e], W.capr[a], 0, t1, ka, ka, rb, ra, 1.0, 0.0));
-        else
-          bc1.push_back(cpy(W.far[e], W.capr[a], t1, ka, ka, rb));
-        if (newk[b] >= 0)
-          b2.push_back(gmm(t1, ka, 0, evof[b]->T, rb, 0, W.far[e], W.capr[a], ka, kb, rb, 1.0, 0.0));
-        else
-          bc2.push_back(cpy(t1, ka, W.far[e], W.capr[a], ka, kb));
+    for (const int e : tl) {
+      W.touched[e] = 0;
+      const int a = W.il_row[e];
+      const int b = LL.il[e];
+      const int ra = r_before[a], rb = r_before[b];
+      const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
+      if (!ka || !kb) continue;
+      double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
+      if (!ra || !rb) {
+        bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
+        continue;
       }
+      if (newk[a] >= 0)
+        b1.push_back(gmm(evof[a]->Tp, ka, 0, W.far[e], W.capr[a], 0, t1, ka, ka, rb, ra, 1.0, 0.0));
+      else
+        bc1.push_back(cpy(W.far[e], W.capr[a], t1, ka, ka, rb));
+      if (newk[b] >= 0)
+        b2.push_back(gmm(t1, ka, 0, evof[b]->T, rb, 0, W.far[e], W.capr[a], ka, kb, rb, 1.0, 0.0));
+      else
+        bc2.push_back(cpy(t1, ka, W.far[e], W.capr[a], ka, kb));
+    }
     cnt.add_gemm(b1);
     cnt.add_gemm(b2);
     launch_gemm(st, b1, prec);
     launch_copy(st, bc1);
     launch_gemm(st, b2, prec);
     launch_copy(st, bc2);
+    phase("host_phase_b", tp);
     for (auto& ev : evs) W.r[ev.q] = ev.k;
     // ---- phase C: fill-in coefficients in the new bases
-    std::vector<GemmDesc> c1, c2;
-    std::vector<CopyDesc> cc;
+    auto& c1 = fresh(L.c1);
+    auto& c2 = fresh(L.c2);
+    auto& cc = fresh(L.cc);
     for (auto& f : fills) {
       const int a = f.a, b = f.b;
       const bool la = newk[a] >= 0, lb = newk[b] >= 0;  // live (re-based this color)
       const int ka = W.r[a], kb = W.r[b];
-      double* dst = W.far[W.farix(a, b)];
+      double* dst = W.far[f.fx];
       const int ldd = W.capr[a];
       if (!ka || !kb) continue;
       if (la && lb) {
@@ -1071,6 +1135,7 @@ struct Factorizer {
     launch_gemm(st, c1, prec);
     launch_gemm(st, c2, prec);
     launch_copy(st, cc);
+    phase("host_phase_c", tp);
   }
 
   // ------------------------------------------------------------------ top level
@@ -1124,8 +1189,11 @@ struct Factorizer {
       DeviceArena child_mem;
       child_mem.swap(levelmem);
       prof_level_tag() = kappa;
+      auto ti = std::chrono::steady_clock::now();
       init_level(*W, kappa, prev.get());
+      phase("host_init", ti);
       wait();
+      phase("host_init_wait", ti);
       st.reset();
       child_mem.release();
       prev.reset();

@@ -148,7 +148,10 @@ void check_launch(const char* what) {
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
   check_copy(v);
-  std::vector<CopyDesc> small, big;
+  // buckets reused across calls (capacity kept)
+  static thread_local std::vector<CopyDesc> small, big;
+  small.clear();
+  big.clear();
   for (auto& x : v) ((long)x.rows * x.cols <= 1024 ? small : big).push_back(x);
   prof_batch_tag() = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
@@ -167,7 +170,10 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   if (v0.empty()) return;
   check_gemm(v0);
-  std::vector<GemmDesc> small, v;
+  static thread_local std::vector<GemmDesc> small, v;
+  static thread_local std::vector<int> tp;
+  small.clear();
+  v.clear();
   for (auto& x : v0) {
     if (x.m <= 0 || x.n <= 0) continue;
     (x.m <= 32 && x.n <= 32 && x.k <= 128 ? small : v).push_back(x);
@@ -185,7 +191,7 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
     profiler().end(kk, st.stream, pe);
   }
   if (v.empty()) return;
-  std::vector<int> tp(v.size() + 1, 0);
+  tp.assign(v.size() + 1, 0);
   for (size_t i = 0; i < v.size(); ++i) {
     long t = (long)((v[i].m + 63) / 64) * ((v[i].n + 63) / 64);
     if (v[i].m <= 0 || v[i].n <= 0) t = 0;
@@ -261,6 +267,120 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   }
 }
 
+// Size buckets of the Householder QR launches.  A problem whose shared-memory
+// slot (block + norms, in the arithmetic type) is at most kQrWarpSlot bytes is
+// factorised by one warp; one of at most kQrCtaSmem bytes by one CTA with the
+// block in shared memory.  A taller block is first reduced in place: its rows
+// are cut into chunks that fit, each chunk is factorised (unpivoted), and the
+// stacked chunk R factors -- the same column space, column norms and R up to
+// signs -- are factorised as the logical matrix (rows addressed through
+// QrcpDesc::rb, rs), when they fit.  Anything else goes to the global-memory
+// kernels.
+static constexpr size_t kQrWarpSlot = 12 * 1024;
+static constexpr size_t kQrCtaSmem = 220 * 1024;
+static constexpr int kQrCtaThreads = 256;
+
+static void qr_smem_attrs() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int big = (int)kQrCtaSmem;
+    const int wmax = (int)(8 * kQrWarpSlot);
+    CK(cudaFuncSetAttribute(k_qr_cta<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cta<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cta<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cta<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_warp<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
+    CK(cudaFuncSetAttribute(k_qr_warp<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
+    CK(cudaFuncSetAttribute(k_qr_warp<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
+    CK(cudaFuncSetAttribute(k_qr_warp<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
+  });
+}
+
+// Launches problems that all fit in kQrCtaSmem: the warp bucket, then the CTA bucket.
+template <bool PIV>
+static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
+  const int tcb = prec == P32 ? 4 : 8;
+  std::vector<QrcpDesc> bw, bc;
+  size_t slot_w = 16, slot_c = 16;
+  for (auto& x : v) {
+    const size_t b = qr_slot_bytes(x.m, x.n, tcb);
+    if (b <= kQrWarpSlot) {
+      bw.push_back(x);
+      slot_w = std::max(slot_w, b);
+    } else {
+      bc.push_back(x);
+      slot_c = std::max(slot_c, b);
+    }
+  }
+  if (!bw.empty()) {
+    // warps per CTA: as many slots as fit in 48 KB, 1..8
+    const int nwp = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / slot_w));
+    const QrcpDesc* d = st.push(bw);
+    const unsigned grid = (unsigned)((bw.size() + nwp - 1) / nwp);
+    const size_t smem = slot_w * nwp;
+    if (prec == P32)
+      k_qr_warp<float, PIV><<<grid, 32 * nwp, smem, st.stream>>>(d, (int)bw.size(), (int)slot_w);
+    else
+      k_qr_warp<double, PIV><<<grid, 32 * nwp, smem, st.stream>>>(d, (int)bw.size(), (int)slot_w);
+    check_launch("k_qr_warp");
+  }
+  if (!bc.empty()) {
+    const QrcpDesc* d = st.push(bc);
+    if (prec == P32)
+      k_qr_cta<float, PIV><<<(unsigned)bc.size(), kQrCtaThreads, slot_c, st.stream>>>(d, (int)bc.size());
+    else
+      k_qr_cta<double, PIV><<<(unsigned)bc.size(), kQrCtaThreads, slot_c, st.stream>>>(d, (int)bc.size());
+    check_launch("k_qr_cta");
+  }
+}
+
+// Launches the shared-memory part of a QR batch (reducing tall blocks first);
+// returns the indices of the descriptors left for the global-memory kernel.
+template <bool PIV>
+static std::vector<size_t> launch_qr_smem(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
+  const int tcb = prec == P32 ? 4 : 8;
+  qr_smem_attrs();
+  std::vector<QrcpDesc> pre, fit;
+  std::vector<size_t> rest;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const QrcpDesc& x = v[i];
+    if (qr_slot_bytes(x.m, x.n, tcb) <= kQrCtaSmem) {
+      fit.push_back(x);
+      continue;
+    }
+    // largest chunk height c with a fitting slot
+    long c = (long)((kQrCtaSmem - sizeof(int) * (size_t)x.n - 16) / tcb) / std::max(1, x.n) - 2;
+    while (c > 0 && qr_slot_bytes((int)c, x.n, tcb) > kQrCtaSmem) --c;
+    if (x.rb > 0 || x.m <= x.n || c < x.n) {
+      rest.push_back(i);
+      continue;
+    }
+    const int nch = (int)((x.m + c - 1) / c);
+    const int last = x.m - (nch - 1) * (int)c;
+    const int mv = (nch - 1) * x.n + std::min(x.n, last);
+    if (qr_slot_bytes(mv, x.n, tcb) > kQrCtaSmem) {
+      rest.push_back(i);
+      continue;
+    }
+    for (int j = 0; j < nch; ++j) {
+      QrcpDesc q{};
+      q.A = x.A + (long)j * c;
+      q.ld = x.ld;
+      q.m = std::min((int)c, x.m - j * (int)c);
+      q.n = x.n;
+      pre.push_back(q);
+    }
+    QrcpDesc y = x;
+    y.m = mv;
+    y.rb = x.n;
+    y.rs = (int)c;
+    fit.push_back(y);
+  }
+  if (!pre.empty()) launch_qr_fitting<false>(st, pre, prec);
+  if (!fit.empty()) launch_qr_fitting<PIV>(st, fit, prec);
+  return rest;
+}
+
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
   if (v.empty()) return;
   for (auto& x : v) IFMM_REQUIRE(x.n <= 1024, IFMM_EINVAL, "QR wider than 1024 columns");
@@ -268,15 +388,29 @@ void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
     req(v[i].A, span(v[i].m, v[i].n, v[i].ld), "qr.A", i);
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qr ld too small");
   }
-  const QrDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
-  if (prec == P32)
-    k_qr<float><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
-  else
-    k_qr<double><<<(unsigned)v.size(), 512, 0, st.stream>>>(d, (int)v.size());
-  check_launch("k_qr");
+  std::vector<QrcpDesc> as(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    QrcpDesc q{};
+    q.A = v[i].A;
+    q.ld = v[i].ld;
+    q.m = v[i].m;
+    q.n = v[i].n;
+    as[i] = q;
+  }
+  const std::vector<size_t> rest = launch_qr_smem<false>(st, as, prec);
+  if (!rest.empty()) {
+    std::vector<QrDesc> g;
+    for (size_t i : rest) g.push_back(v[i]);
+    const QrDesc* d = st.push(g);
+    if (prec == P32)
+      k_qr<float><<<(unsigned)g.size(), 512, 0, st.stream>>>(d, (int)g.size());
+    else
+      k_qr<double><<<(unsigned)g.size(), 512, 0, st.stream>>>(d, (int)g.size());
+    check_launch("k_qr");
+  }
   profiler().end(kk, st.stream, pe);
 }
 
@@ -313,10 +447,6 @@ void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
 void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   if (v.empty()) return;
   for (auto& x : v) IFMM_REQUIRE(x.n <= 1024, IFMM_EINVAL, "pivoted QR wider than 1024 columns");
-  int nmax = 0;
-  for (auto& x : v) nmax = std::max(nmax, x.n);
-  const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
-  IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivoted QR too wide");
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_qrcp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -328,28 +458,41 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
     req(v[i].kout, sizeof(int), "qrcp.kout", i);
     if (v[i].ld < v[i].m) throw Error(IFMM_EINVAL, "qrcp ld too small");
   }
-  const QrcpDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
-  if (prec == P32)
-    k_qrcp<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size());
-  else
-    k_qrcp<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size());
-  check_launch("k_qrcp");
+  const std::vector<size_t> rest = launch_qr_smem<true>(st, v, prec);
+  if (!rest.empty()) {
+    std::vector<QrcpDesc> g;
+    int nmax = 0;
+    for (size_t i : rest) {
+      g.push_back(v[i]);
+      nmax = std::max(nmax, v[i].n);
+    }
+    const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
+    IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivoted QR too wide");
+    const QrcpDesc* d = st.push(g);
+    if (prec == P32)
+      k_qrcp<float><<<(unsigned)g.size(), 512, smem, st.stream>>>(d, (int)g.size());
+    else
+      k_qrcp<double><<<(unsigned)g.size(), 512, smem, st.stream>>>(d, (int)g.size());
+    check_launch("k_qrcp");
+  }
   profiler().end(kk, st.stream, pe);
 }
 
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
   if (v.empty()) return;
-  const int smem = 160 * 1024;
+  static constexpr int smem_cap = 160 * 1024;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    CK(cudaFuncSetAttribute(k_svd_rt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CK(cudaFuncSetAttribute(k_svd_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_svd_rt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+    CK(cudaFuncSetAttribute(k_svd_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
   });
+  int nmax = 1;
   for (size_t i = 0; i < v.size(); ++i) {
     IFMM_REQUIRE(v[i].n <= 1024, IFMM_EINVAL, "SVD wider than 1024 columns");
+    nmax = std::max(nmax, v[i].n);
     if (!registry().on) continue;
     const SvdRtDesc& x = v[i];
     req(x.A, span(x.n, x.n, x.ld) > 0 ? sizeof(double) : 0, "svd_rt.A", i);
@@ -358,14 +501,20 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     req(x.sig, sizeof(double) * x.n, "svd_rt.sig", i);
     req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
   }
+  // B is n x k with k <= n: n^2 elements bound what any problem of the batch
+  // keeps in shared memory (larger ones use their global work buffer); one
+  // warp per column pair of the widest problem
+  const int tcb = prec == P32 ? 4 : 8;
+  const int smem = (int)std::min<size_t>(smem_cap, ((size_t)nmax * nmax * tcb + 15) & ~(size_t)15);
+  const int threads = std::min(512, std::max(64, 32 * ((nmax + 1) / 2)));
   const SvdRtDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
-    k_svd_rt<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60, smem);
+    k_svd_rt<float><<<(unsigned)v.size(), threads, smem, st.stream>>>(d, (int)v.size(), 60, smem);
   else
-    k_svd_rt<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60, smem);
+    k_svd_rt<double><<<(unsigned)v.size(), threads, smem, st.stream>>>(d, (int)v.size(), 60, smem);
   check_launch("k_svd_rt");
   profiler().end(kk, st.stream, pe);
 }
