@@ -8,7 +8,7 @@
  * with Chebyshev-interpolation operators), eliminates it level by level from the
  * leaves (Algorithm 1) with the nodes of a level processed color by color
  * (Sec. 3, Algorithm 3 coloring at separation sigma), recompresses every far-field
- * fill-in at relative accuracy eps (Sec. 4.2), and applies the result as a direct
+ * fill-in at relative accuracy eps (Sec. 5.1), and applies the result as a direct
  * solve (Algorithm 2) or as the preconditioner of GMRES(m) (Algorithms 4 and 5).
  *
  * Conventions for every entry point:
@@ -66,6 +66,14 @@ typedef struct {
   int reserved;
 } ifmm_kernel;
 
+/* Arithmetic of the factorization outside the pivots (which are always FP64, as
+ * are the solve, GMRES and its residual):
+ *   FP64 - everything in FP64;
+ *   FP32 - Schur-complement GEMMs, transforms and recompression (pivoted QR,
+ *          Jacobi) computed in FP32 on FP64 storage;
+ *   BF16 - as FP32, with the Schur-complement GEMM operands rounded to bfloat16
+ *          (FP32 accumulation).  The fill-ins then carry bfloat16 rounding
+ *          (~4e-3 relative), so truncation at eps much below that keeps noise. */
 enum { IFMM_PREC_FP64 = 0, IFMM_PREC_FP32 = 1, IFMM_PREC_BF16 = 2 };
 enum { IFMM_RANK_SVD = 0, IFMM_RANK_REPLAY = 1, IFMM_RANK_LEARNED = 2 };
 
@@ -126,7 +134,7 @@ ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs,
 ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact* precond, const double* b,
                       double* x, int restart, double tol, int maxit, int* iters, double* relres, void* stream);
 
-/* Independent problems together (BASELINE's batched workload; the paper factors
+/* Independent problems together (a batch of many BEM problems; the paper factors
  * one problem at a time).  Problem i uses trees[i], kernels[i], opts[i]; out[i]
  * receives its factor.  nworkers host threads (<= 0: 8), each with its own CUDA
  * stream, take problems in index order, so kernels of different problems
@@ -172,8 +180,8 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
  *   - k->arith selects FP64 or float-pair sums, as for bem_matvec. */
 ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
 
-/* Rank predictor (BASELINE's learned part; Sec. 4.2 uses randomized SVD at a
- * prescribed accuracy, here a learned rank caps the pivoted-QR range finder).
+/* Rank predictor (the paper's Sec. 5.1 uses a randomized SVD at a prescribed
+ * accuracy; here a learned rank sets the width of a randomized range finder).
  * A multilayer perceptron 9 -> 64 -> 64 -> 64 -> 1 with ReLU hidden layers, FP32.
  * Inputs per recompression event: cell centre in [-1,1]^3 (3), block size
  * n_q / 256 (1), level / 10 (1), current rank / 64 (1), fill-in rows / 1024 (1),

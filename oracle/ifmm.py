@@ -6,7 +6,7 @@ a time, no blocking or fusion beyond what the steps below state.
 Passages followed: Eq. (1) (extended sparse system), Algorithm 1 (factorization,
 Sec. 2.3), Algorithm 2 (solve, Sec. 2.4), Sec. 3.2/3.3 (colors processed in
 order, nodes of a color independent; sigma=3 serializes the interaction-list
-updates), Sec. 4.2 (low-rank compression at relative error eps).
+updates), Sec. 5.1 (low-rank compression at relative error eps).
 
 Variables and rows of node i at level kappa (Eq. (1)):
     x_i (n_i)   particles / the children's multipoles,

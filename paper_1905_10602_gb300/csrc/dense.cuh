@@ -9,6 +9,7 @@
 // the descriptor.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,7 +57,17 @@ __global__ void k_copy_small(const CopyDesc* __restrict__ d, int nd) {
   }
 }
 
-template <typename TC>
+// RB: the operands are rounded to bfloat16 before the (FP32) multiply-add.
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+template <typename TC, bool RB>
+__device__ __forceinline__ TC stage_val(double v) {
+  if constexpr (RB)
+    return (TC)round_bf16((float)v);
+  else
+    return (TC)v;
+}
+
+template <typename TC, bool RB = false>
 __global__ void k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
   const int di = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (di >= nd) return;
@@ -68,7 +79,7 @@ __global__ void k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
     for (int q = 0; q < D.k; ++q) {
       const double a = D.ta ? D.A[q + (long)i * D.lda] : D.A[i + (long)q * D.lda];
       const double b = D.tb ? D.B[j + (long)q * D.ldb] : D.B[q + (long)j * D.ldb];
-      acc += (TC)a * (TC)b;
+      acc += stage_val<TC, RB>(a) * stage_val<TC, RB>(b);
     }
     double* o = D.C + i + (long)j * D.ldc;
     const double v = D.alpha * (double)acc;
@@ -80,7 +91,7 @@ __global__ void k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
 // 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, K in
 // slices of 16 staged through shared memory.  TC is the arithmetic type
 // (double for the FP64 path, float for the reduced-precision modes).
-template <typename TC>
+template <typename TC, bool RB = false>
 __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, const int* __restrict__ tile_ptr, int nd) {
   const int di = find_desc(tile_ptr, nd, blockIdx.x);
   const GemmDesc D = d[di];
@@ -103,14 +114,14 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
         const int r = row0 + i, c = k0 + kk;
         double v = 0.0;
         if (r < D.m && c < D.k) v = D.ta ? D.A[c + (long)r * D.lda] : D.A[r + (long)c * D.lda];
-        As[kk][i] = (TC)v;
+        As[kk][i] = stage_val<TC, RB>(v);
       }
       {
         const int kk = e & 15, j = e >> 4;
         const int r = k0 + kk, c = col0 + j;
         double v = 0.0;
         if (r < D.k && c < D.n) v = D.tb ? D.B[c + (long)r * D.ldb] : D.B[r + (long)c * D.ldb];
-        Bs[kk][j] = (TC)v;
+        Bs[kk][j] = stage_val<TC, RB>(v);
       }
     }
     __syncthreads();
@@ -760,6 +771,36 @@ __device__ __forceinline__ double warp_max_nan(double v) {
   return v;
 }
 
+// Applies H = I - tau v v^T (v_0 = 1, v_i = sc x_i) to the cnt <= G columns
+// j0.. of the trailing block (rows k..k+len-1, ld m) with one warp: G independent
+// dot products per row sweep and G interleaved butterfly reductions, so the
+// shared-memory and shuffle latencies of the columns overlap.
+template <typename TC, int G>
+__device__ __forceinline__ void reflect_group(TC* A, int m, int k, int len, const TC* x, TC sc, TC tau, int j0,
+                                              int cnt, int lane) {
+  TC* y[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) y[u] = A + k + (size_t)(j0 + (u < cnt ? u : cnt - 1)) * m;
+  TC acc[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) acc[u] = 0;
+  for (int i = lane; i < len; i += 32) {
+    const TC vi = (i == 0) ? (TC)1 : sc * x[i];
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc[u] += vi * y[u][i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+  for (int i = lane; i < len; i += 32) {
+    const TC vi = (i == 0) ? (TC)1 : sc * x[i];
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (u < cnt) y[u][i] -= (acc[u] * tau) * vi;
+  }
+}
+
 // physical row of logical row i (QrcpDesc::rb, rs)
 __device__ __forceinline__ long qr_row(const QrcpDesc& D, int i) {
   return D.rb > 0 ? (long)(i / D.rb) * D.rs + i % D.rb : (long)i;
@@ -863,30 +904,25 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
       tau = (alpha - x0) / alpha;
       sc = (TC)1 / (x0 - alpha);
     }
-    for (int j = k + 1; j < n; ++j) {
-      TC* y = A + k + (size_t)j * m;
-      TC nj = 0, rj = 0;
+    for (int j0 = k + 1; j0 < n; j0 += 4) {
+      const int cnt = min(4, n - j0);
+      if (tau != (TC)0) reflect_group<TC, 4>(A, m, k, len, x, sc, tau, j0, cnt, lane);
       if (PIV) {
-        nj = nrm[j];
-        rj = ref[j];
-      }
-      if (tau != (TC)0) {
-        TC dot = 0;
-        for (int i = lane; i < len; i += 32) dot += (i == 0 ? (TC)1 : sc * x[i]) * y[i];
-        dot = warp_sum_t<TC>(dot) * tau;
-        for (int i = lane; i < len; i += 32) y[i] -= dot * (i == 0 ? (TC)1 : sc * x[i]);
-      }
-      if (PIV) {
-        const TC r = __shfl_sync(0xffffffffu, lane == 0 ? y[0] : (TC)0, 0);
-        TC nv = nj - r * r;
-        if (!(nv > (TC)1e-2 * rj)) {  // two digits lost: recompute from the column
-          TC s2 = 0;
-          for (int i = lane; i < len; i += 32)
-            if (i > 0) s2 += y[i] * y[i];
-          nv = warp_sum_t<TC>(s2);
-          if (lane == 0) ref[j] = nv;
+        for (int u = 0; u < cnt; ++u) {
+          const int j = j0 + u;
+          const TC* y = A + k + (size_t)j * m;
+          const TC nj = nrm[j], rj = ref[j];
+          const TC r = __shfl_sync(0xffffffffu, lane == 0 ? y[0] : (TC)0, 0);
+          TC nv = nj - r * r;
+          if (!(nv > (TC)1e-2 * rj)) {  // two digits lost: recompute from the column
+            TC s2 = 0;
+            for (int i = lane; i < len; i += 32)
+              if (i > 0) s2 += y[i] * y[i];
+            nv = warp_sum_t<TC>(s2);
+            if (lane == 0) ref[j] = nv;
+          }
+          if (lane == 0) nrm[j] = nv;
         }
-        if (lane == 0) nrm[j] = nv;
       }
     }
     if (lane == 0) x[0] = alpha;
@@ -907,13 +943,13 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
   }
 }
 
-// One CTA (<= 256 threads) per problem, the block in dynamic shared memory.
+// One CTA (<= 1024 threads) per problem, the block in dynamic shared memory.
 // Per column step: one barrier for the pivot search, one after a column swap,
 // one for the reflector norm, one between the segment dot products and the
 // update, and one closing the step (plus one more in the rare step where a
 // downdated norm has to be recomputed).
 template <typename TC, bool PIV>
-__global__ void __launch_bounds__(256) k_qr_cta(const QrcpDesc* __restrict__ d, int nd) {
+__global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d, int nd) {
   if ((int)blockIdx.x >= nd) return;
   const QrcpDesc D = d[blockIdx.x];
   const int m = D.m, n = D.n;
@@ -924,11 +960,11 @@ __global__ void __launch_bounds__(256) k_qr_cta(const QrcpDesc* __restrict__ d, 
   TC* nrm = A + mn;
   TC* ref = nrm + n;
   int* jp = (int*)(ref + n);
-  __shared__ TC part[8];
+  __shared__ TC part[32];
   __shared__ unsigned char flag[1024];
-  __shared__ TC red_s[8], red_v[8];
-  __shared__ int red_i[8];
-  __shared__ double red_g[8];
+  __shared__ TC red_s[32], red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double red_g[32];
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   double gmax = 0.0;
@@ -1043,19 +1079,28 @@ __global__ void __launch_bounds__(256) k_qr_cta(const QrcpDesc* __restrict__ d, 
       if (S > smax) S = smax;
       if (S < 1) S = 1;
       if (S == 1) {
-        for (int j = k + 1 + w; j < n; j += nw) {
-          TC* y = A + k + (size_t)j * m;
-          TC dot = 0;
-          for (int i = lane; i < len; i += 32) dot += (i == 0 ? (TC)1 : sc * x[i]) * y[i];
-          dot = warp_sum_t<TC>(dot) * tau;
-          for (int i = lane; i < len; i += 32) y[i] -= dot * (i == 0 ? (TC)1 : sc * x[i]);
+        // groups of G consecutive columns, round-robin over the warps
+        const int G = ntr >= 4 * nw ? 4 : (ntr >= 2 * nw ? 2 : 1);
+        const int ng = (ntr + G - 1) / G;
+        for (int g = w; g < ng; g += nw) {
+          const int j0 = k + 1 + g * G;
+          const int cnt = min(G, n - j0);
+          if (G == 4)
+            reflect_group<TC, 4>(A, m, k, len, x, sc, tau, j0, cnt, lane);
+          else if (G == 2)
+            reflect_group<TC, 2>(A, m, k, len, x, sc, tau, j0, cnt, lane);
+          else
+            reflect_group<TC, 1>(A, m, k, len, x, sc, tau, j0, cnt, lane);
           if (PIV && lane == 0) {
-            const TC r = y[0];
-            const TC nv = nrm[j] - r * r;
-            nrm[j] = nv;
-            if (!(nv > (TC)1e-2 * ref[j])) {
-              flag[j] = 1;
-              need = 1;
+            for (int u = 0; u < cnt; ++u) {
+              const int j = j0 + u;
+              const TC r = A[k + (size_t)j * m];
+              const TC nv = nrm[j] - r * r;
+              nrm[j] = nv;
+              if (!(nv > (TC)1e-2 * ref[j])) {
+                flag[j] = 1;
+                need = 1;
+              }
             }
           }
         }
@@ -1135,6 +1180,56 @@ __global__ void __launch_bounds__(256) k_qr_cta(const QrcpDesc* __restrict__ d, 
       D.kout[0] = k;
       if (D.tail) D.tail[0] = (k < kmax && capped) ? tailv : 0.0;
     }
+  }
+}
+
+// ---------------------------------------------------------------- IL basis changes
+// One CTA per touched IL entry e of a color: M2L_ab <- T'_a M2L_ab T_b, with
+// the identity for an endpoint that was not re-based and a zero block when an
+// old rank is zero.  The block is staged in shared memory (it is overwritten in
+// place); md >= every rank involved is the stride of the staging tiles.
+template <typename TC>
+__global__ void __launch_bounds__(128) k_il_transform(const int* __restrict__ list, int nlist, IlTables t, int md) {
+  if ((int)blockIdx.x >= nlist) return;
+  const int e = list[blockIdx.x];
+  const int a = t.il_row[e], b = t.il[e];
+  const int ra = t.rbefore[a], rb = t.rbefore[b], na = t.newk[a], nb = t.newk[b];
+  const int ka = na >= 0 ? na : ra, kb = nb >= 0 ? nb : rb;
+  if (ka == 0 || kb == 0) return;
+  double* M = t.far[e];
+  const long ld = t.capr[a];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (ra == 0 || rb == 0) {
+    for (int x = tid; x < ka * kb; x += nt) M[(x % ka) + (long)(x / ka) * ld] = 0.0;
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char ism[];
+  TC* Ms = (TC*)ism;       // ra x rb, ld ra
+  TC* t1 = Ms + md * md;   // ka x rb, ld ka
+  for (int x = tid; x < ra * rb; x += nt) Ms[x] = (TC)M[(x % ra) + (long)(x / ra) * ld];
+  __syncthreads();
+  if (na >= 0) {
+    const double* Tp = t.Tp[a];
+    for (int x = tid; x < ka * rb; x += nt) {
+      const int i = x % ka, j = x / ka;
+      TC acc = 0;
+      for (int l = 0; l < ra; ++l) acc += (TC)Tp[i + (long)l * ka] * Ms[l + j * ra];
+      t1[x] = acc;
+    }
+  } else {
+    for (int x = tid; x < ka * rb; x += nt) t1[x] = Ms[x];
+  }
+  __syncthreads();
+  if (nb >= 0) {
+    const double* Tb = t.T[b];
+    for (int x = tid; x < ka * kb; x += nt) {
+      const int i = x % ka, j = x / ka;
+      TC acc = 0;
+      for (int l = 0; l < rb; ++l) acc += t1[i + l * ka] * (TC)Tb[l + (long)j * rb];
+      M[i + (long)j * ld] = (double)acc;
+    }
+  } else {
+    for (int x = tid; x < ka * kb; x += nt) M[(x % ka) + (long)(x / ka) * ld] = (double)t1[x];
   }
 }
 

@@ -110,6 +110,23 @@ struct SvdRtDesc {
   double* work;
 };
 
+// Interaction-list blocks of one level on the device, and the basis changes of
+// one color (phase B of a color, reading R7 of the oracle).  IL entry e is the
+// block M2L_ab, a = il_row[e], b = il[e], stored at far[e] with ld capr[a];
+// rbefore[x] is node x's rank before the color, newk[x] its new rank (-1: not
+// re-based), T[x] (rbefore x newk, ld rbefore) and Tp[x] (newk x rbefore, ld
+// newk) its transforms when re-based.
+struct IlTables {
+  const int* il_row;
+  const int* il;
+  double* const* far;
+  const int* capr;
+  const int* rbefore;
+  const int* newk;
+  const double* const* T;
+  const double* const* Tp;
+};
+
 // Random sketch matrix (m x s, ld m) of +-1 entries from a counter stream.
 struct SketchDesc {
   double* omega;

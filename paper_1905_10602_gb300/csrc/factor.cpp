@@ -54,6 +54,11 @@ struct Work {
   std::vector<int> il_row; // il_row[e] = a for the IL entry e = (a, b)
   std::vector<char> touched;  // per IL entry, cleared after every use
   std::vector<int> mark;      // per node, -1 outside a lookup scope
+  // device copies of the IL structure (phase-B kernel)
+  int* d_il_row = nullptr;
+  int* d_il = nullptr;
+  double** d_far = nullptr;
+  int* d_capr = nullptr;
   int slot(int p, int q) const {
     if (p == q) return slot_ptr[p];
     const int* b = LL->nbr.data() + LL->nbr_ptr[p];
@@ -81,7 +86,7 @@ struct Counter {
   double total() const { return gemm + inv + qr + svd + lu; }
 };
 
-// One recompression event (reading R4 of the oracle, Sec. 4.2): new orthonormal
+// One recompression event (reading R4 of the oracle, Sec. 5.1): new orthonormal
 // row basis (P2M) and column basis (L2P) of a live node from the SVDs of the
 // weighted old basis stacked with the far fill-ins.
 struct Event {
@@ -124,6 +129,7 @@ struct Factorizer {
   DeviceArena levelmem;
   int p, rc, maxrank;
   int prec = P64;  // arithmetic of Schur GEMMs and recompression (pivots stay FP64)
+  int gprec = P64; // arithmetic of the Schur-complement GEMMs (P16 in the BF16 mode)
   double* m2m_tab = nullptr;
   double* m2l_tab = nullptr;
   std::unordered_map<int64_t, int> replay;
@@ -138,7 +144,8 @@ struct Factorizer {
     std::vector<GemmDesc> gw, gx, gf, b1, b2, c1, c2, gt;
     std::vector<SvdRtDesc> sr;
     std::vector<InvDesc> inv;
-    std::vector<int> tl;
+    std::vector<int> tl, tlf;
+    std::vector<const double*> tn, tpn;
   } L;
   template <class V>
   static V& fresh(V& v) {
@@ -170,6 +177,7 @@ struct Factorizer {
     rc = F.rc;
     maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256;
     prec = F.o.precision == IFMM_PREC_FP64 ? P64 : P32;
+    gprec = F.o.precision == IFMM_PREC_BF16 ? P16 : prec;
     if (F.o.rank_mode == IFMM_RANK_LEARNED) {
       IFMM_REQUIRE(F.o.mlp != nullptr, IFMM_EINVAL, "learned rank mode needs the MLP weights");
       CK(cudaMalloc(&d_mlp, sizeof(float) * IFMM_MLP_NWEIGHTS));
@@ -647,6 +655,19 @@ struct Factorizer {
     for (int a = 0; a < nn; ++a)
       for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e)
         W.far[e] = levelmem.alloc((size_t)std::max(1, W.capr[a]) * std::max(1, W.capr[LL.il[e]]));
+    {
+      const size_t ne = std::max<size_t>(1, LL.il.size());
+      W.d_il_row = (int*)levelmem.alloc_bytes(sizeof(int) * ne);
+      W.d_il = (int*)levelmem.alloc_bytes(sizeof(int) * ne);
+      W.d_far = (double**)levelmem.alloc_bytes(sizeof(double*) * ne);
+      W.d_capr = (int*)levelmem.alloc_bytes(sizeof(int) * std::max(1, nn));
+      if (!LL.il.empty()) {
+        CK(cudaMemcpyAsync(W.d_il_row, W.il_row.data(), sizeof(int) * LL.il.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(W.d_il, LL.il.data(), sizeof(int) * LL.il.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(W.d_far, W.far.data(), sizeof(double*) * LL.il.size(), cudaMemcpyHostToDevice, s));
+      }
+      if (nn) CK(cudaMemcpyAsync(W.d_capr, W.capr.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s));
+    }
     W.P2M.assign(nn, nullptr);
     W.L2P.assign(nn, nullptr);
     W.M2M.assign(nn, nullptr);
@@ -1005,8 +1026,8 @@ struct Factorizer {
     launch_copy(st, cg);
     cnt.add_gemm(gx);
     cnt.add_gemm(gf);
-    launch_gemm(st, gx, prec);
-    launch_gemm(st, gf, prec);
+    launch_gemm(st, gx, gprec);
+    launch_gemm(st, gf, gprec);
     launch_copy(st, sc);
     phase("host_schur", tp);
     // ---- recompression events (snapshots: nothing below reads what phase A changes)
@@ -1078,6 +1099,10 @@ struct Factorizer {
         bc1.push_back(cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc));
       }
     }
+    // entries whose ranks all fit the fused kernel's tiles go to one launch;
+    // the rest (a rank above 64) keep per-block GEMM descriptors
+    auto& fast = fresh(L.tlf);
+    int md = 1;
     for (const int e : tl) {
       W.touched[e] = 0;
       const int a = W.il_row[e];
@@ -1085,6 +1110,12 @@ struct Factorizer {
       const int ra = r_before[a], rb = r_before[b];
       const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
       if (!ka || !kb) continue;
+      const int mx = std::max(std::max(ra, rb), std::max(ka, kb));
+      if (mx <= 64) {
+        fast.push_back(e);
+        md = std::max(md, mx);
+        continue;
+      }
       double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
       if (!ra || !rb) {
         bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
@@ -1105,6 +1136,24 @@ struct Factorizer {
     launch_copy(st, bc1);
     launch_gemm(st, b2, prec);
     launch_copy(st, bc2);
+    if (!fast.empty()) {
+      auto& tn = fresh(L.tn);
+      auto& tpn = fresh(L.tpn);
+      tn.assign(W.nn, nullptr);
+      tpn.assign(W.nn, nullptr);
+      for (auto& ev : evs) {
+        tn[ev.q] = ev.T;
+        tpn[ev.q] = ev.Tp;
+      }
+      for (const int e : fast) {
+        const int a = W.il_row[e], b = LL.il[e];
+        const int ra = r_before[a], rb = r_before[b];
+        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
+        if (ra && rb) cnt.gemm += 2.0 * ((newk[a] >= 0 ? (double)ka * rb * ra : 0.0) + (newk[b] >= 0 ? (double)ka * kb * rb : 0.0));
+      }
+      IlTables t{W.d_il_row, W.d_il, W.d_far, W.d_capr, st.push(r_before), st.push(newk), st.push(tn), st.push(tpn)};
+      launch_il_transform(st, fast, t, md, prec);
+    }
     phase("host_phase_b", tp);
     for (auto& ev : evs) W.r[ev.q] = ev.k;
     // ---- phase C: fill-in coefficients in the new bases

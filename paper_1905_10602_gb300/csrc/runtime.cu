@@ -64,7 +64,8 @@ static void check_gemm(const std::vector<GemmDesc>& v) {
 
 static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "gauss_jordan", "qr_fp64", "qr_fp32",
                                            "svd_fp64", "svd_fp32", "gemv", "gemv_sum", "p2p", "interp", "tables",
-                                           "matvec", "permute", "gauss_jordan_big", "solve_graph"};
+                                           "matvec", "permute", "gauss_jordan_big", "solve_graph",
+                                           "qr_global_fp64", "qr_global_fp32"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
 int& prof_level_tag() {
   static thread_local int t = -1;
@@ -144,6 +145,65 @@ void check_launch(const char* what) {
   if (e != cudaSuccess) throw Error(IFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Independent launches of one batch on side streams of the caller's stream:
+// fork() orders the side streams after everything already on the main stream
+// (descriptor uploads included), join() orders the main stream after them.
+// The side streams and events belong to the calling thread.
+struct ForkJoin {
+  static constexpr int kSide = 4;
+  cudaStream_t main;
+  int used = 0;
+  struct Side {
+    cudaStream_t s[kSide] = {};
+    cudaEvent_t done[kSide] = {};
+    cudaEvent_t fork = nullptr;
+    int dev = -1;
+    ~Side() {
+      if (dev < 0) return;
+      for (int i = 0; i < kSide; ++i) {
+        cudaStreamDestroy(s[i]);
+        cudaEventDestroy(done[i]);
+      }
+      cudaEventDestroy(fork);
+    }
+  };
+  static Side& side() {
+    static thread_local Side sd;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (sd.dev != dev) {
+      for (int i = 0; i < kSide; ++i) {
+        CK(cudaStreamCreateWithFlags(&sd.s[i], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&sd.done[i], cudaEventDisableTiming));
+      }
+      CK(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+      sd.dev = dev;
+    }
+    return sd;
+  }
+  explicit ForkJoin(cudaStream_t m) : main(m) {
+    CK(cudaEventRecord(side().fork, main));
+  }
+  // the i-th independent launch goes to stream(i)
+  cudaStream_t stream(int i) {
+    Side& sd = side();
+    const int k = i % kSide;
+    if (k >= used) {
+      CK(cudaStreamWaitEvent(sd.s[k], sd.fork, 0));
+      used = k + 1;
+    }
+    return sd.s[k];
+  }
+  void join() {
+    Side& sd = side();
+    for (int k = 0; k < used; ++k) {
+      CK(cudaEventRecord(sd.done[k], sd.s[k]));
+      CK(cudaStreamWaitEvent(main, sd.done[k], 0));
+    }
+    used = 0;
+  }
+};
+
 // ------------------------------------------------------------------ launchers
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
@@ -180,11 +240,13 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   }
   if (!small.empty()) {
     const GemmDesc* d = st.push(small);
-    const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
+    const int kk = prec == P64 ? KK_GEMM64 : KK_GEMM32;
     prof_batch_tag() = (long)small.size();
     cudaEvent_t pe = profiler().begin(kk, st.stream);
     if (prec == P32)
       k_gemm_small<float><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+    else if (prec == P16)
+      k_gemm_small<float, true><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
     else
       k_gemm_small<double><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
     check_launch("k_gemm_small");
@@ -203,10 +265,12 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   const GemmDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   const int* p = st.push(tp);
-  const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
+  const int kk = prec == P64 ? KK_GEMM64 : KK_GEMM32;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   if (prec == P32)
     k_gemm<float><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
+  else if (prec == P16)
+    k_gemm<float, true><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
   else
     k_gemm<double><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
   check_launch("k_gemm");
@@ -278,7 +342,6 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
 // kernels.
 static constexpr size_t kQrWarpSlot = 12 * 1024;
 static constexpr size_t kQrCtaSmem = 220 * 1024;
-static constexpr int kQrCtaThreads = 256;
 
 static void qr_smem_attrs() {
   static std::once_flag once;
@@ -300,38 +363,50 @@ static void qr_smem_attrs() {
 template <bool PIV>
 static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   const int tcb = prec == P32 ? 4 : 8;
-  std::vector<QrcpDesc> bw, bc;
-  size_t slot_w = 16, slot_c = 16;
+  // classes: warp per problem (slot <= kQrWarpSlot), then CTA per problem in
+  // shared-memory size classes (<= 24, 48, 96, 220 KB).  A launch reserves its
+  // largest slot for every CTA, so one large block must not set the occupancy of
+  // many small ones; classes with few CTAs per SM get more threads to hide the
+  // latency of each column step.  The classes run concurrently.
+  const size_t cls[5] = {kQrWarpSlot, 24 * 1024, 48 * 1024, 96 * 1024, kQrCtaSmem};
+  const int thr[5] = {0, 256, 256, 512, 1024};
+  std::vector<QrcpDesc> part[5];
+  size_t smax[5] = {16, 16, 16, 16, 16};
   for (auto& x : v) {
     const size_t b = qr_slot_bytes(x.m, x.n, tcb);
-    if (b <= kQrWarpSlot) {
-      bw.push_back(x);
-      slot_w = std::max(slot_w, b);
+    int c = 0;
+    while (c < 4 && b > cls[c]) ++c;
+    part[c].push_back(x);
+    smax[c] = std::max(smax[c], b);
+  }
+  const QrcpDesc* d[5] = {};
+  for (int c = 0; c < 5; ++c)
+    if (!part[c].empty()) d[c] = st.push(part[c]);
+  ForkJoin fj(st.stream);
+  int li = 0;
+  for (int c = 0; c < 5; ++c) {
+    if (part[c].empty()) continue;
+    const int nd = (int)part[c].size();
+    cudaStream_t s = fj.stream(li++);
+    if (c == 0) {
+      // warps per CTA: as many slots as fit in 48 KB, 1..8
+      const int nwp = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / smax[0]));
+      const unsigned grid = (unsigned)((nd + nwp - 1) / nwp);
+      const size_t smem = smax[0] * nwp;
+      if (prec == P32)
+        k_qr_warp<float, PIV><<<grid, 32 * nwp, smem, s>>>(d[0], nd, (int)smax[0]);
+      else
+        k_qr_warp<double, PIV><<<grid, 32 * nwp, smem, s>>>(d[0], nd, (int)smax[0]);
+      check_launch("k_qr_warp");
     } else {
-      bc.push_back(x);
-      slot_c = std::max(slot_c, b);
+      if (prec == P32)
+        k_qr_cta<float, PIV><<<(unsigned)nd, thr[c], smax[c], s>>>(d[c], nd);
+      else
+        k_qr_cta<double, PIV><<<(unsigned)nd, thr[c], smax[c], s>>>(d[c], nd);
+      check_launch("k_qr_cta");
     }
   }
-  if (!bw.empty()) {
-    // warps per CTA: as many slots as fit in 48 KB, 1..8
-    const int nwp = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / slot_w));
-    const QrcpDesc* d = st.push(bw);
-    const unsigned grid = (unsigned)((bw.size() + nwp - 1) / nwp);
-    const size_t smem = slot_w * nwp;
-    if (prec == P32)
-      k_qr_warp<float, PIV><<<grid, 32 * nwp, smem, st.stream>>>(d, (int)bw.size(), (int)slot_w);
-    else
-      k_qr_warp<double, PIV><<<grid, 32 * nwp, smem, st.stream>>>(d, (int)bw.size(), (int)slot_w);
-    check_launch("k_qr_warp");
-  }
-  if (!bc.empty()) {
-    const QrcpDesc* d = st.push(bc);
-    if (prec == P32)
-      k_qr_cta<float, PIV><<<(unsigned)bc.size(), kQrCtaThreads, slot_c, st.stream>>>(d, (int)bc.size());
-    else
-      k_qr_cta<double, PIV><<<(unsigned)bc.size(), kQrCtaThreads, slot_c, st.stream>>>(d, (int)bc.size());
-    check_launch("k_qr_cta");
-  }
+  fj.join();
 }
 
 // Launches the shared-memory part of a QR batch (reducing tall blocks first);
@@ -401,17 +476,21 @@ void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
     as[i] = q;
   }
   const std::vector<size_t> rest = launch_qr_smem<false>(st, as, prec);
+  profiler().end(kk, st.stream, pe);
   if (!rest.empty()) {
     std::vector<QrDesc> g;
     for (size_t i : rest) g.push_back(v[i]);
     const QrDesc* d = st.push(g);
+    prof_batch_tag() = (long)g.size();
+    const int kg = prec == P32 ? KK_QRG32 : KK_QRG64;
+    cudaEvent_t pg = profiler().begin(kg, st.stream);
     if (prec == P32)
       k_qr<float><<<(unsigned)g.size(), 512, 0, st.stream>>>(d, (int)g.size());
     else
       k_qr<double><<<(unsigned)g.size(), 512, 0, st.stream>>>(d, (int)g.size());
     check_launch("k_qr");
+    profiler().end(kg, st.stream, pg);
   }
-  profiler().end(kk, st.stream, pe);
 }
 
 void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
@@ -462,6 +541,7 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   const int kk = prec == P32 ? KK_QR32 : KK_QR64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   const std::vector<size_t> rest = launch_qr_smem<true>(st, v, prec);
+  profiler().end(kk, st.stream, pe);
   if (!rest.empty()) {
     std::vector<QrcpDesc> g;
     int nmax = 0;
@@ -472,13 +552,16 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
     const size_t smem = sizeof(double) * 2 * nmax + sizeof(int) * nmax + 16;
     IFMM_REQUIRE(smem <= 200 * 1024, IFMM_EINVAL, "pivoted QR too wide");
     const QrcpDesc* d = st.push(g);
+    prof_batch_tag() = (long)g.size();
+    const int kg = prec == P32 ? KK_QRG32 : KK_QRG64;
+    cudaEvent_t pg = profiler().begin(kg, st.stream);
     if (prec == P32)
       k_qrcp<float><<<(unsigned)g.size(), 512, smem, st.stream>>>(d, (int)g.size());
     else
       k_qrcp<double><<<(unsigned)g.size(), 512, smem, st.stream>>>(d, (int)g.size());
     check_launch("k_qrcp");
+    profiler().end(kg, st.stream, pg);
   }
-  profiler().end(kk, st.stream, pe);
 }
 
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
@@ -501,21 +584,64 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
     req(x.sig, sizeof(double) * x.n, "svd_rt.sig", i);
     req(x.work, sizeof(double) * (size_t)x.n * x.n, "svd_rt.work", i);
   }
-  // B is n x k with k <= n: n^2 elements bound what any problem of the batch
-  // keeps in shared memory (larger ones use their global work buffer); one
-  // warp per column pair of the widest problem
+  // B is n x k with k <= n: n^2 elements bound what a problem keeps in shared
+  // memory (larger ones use their global work buffer).  The batch is launched in
+  // width classes so that a wide problem does not set the shared memory (and so
+  // the occupancy) of many narrow ones; one warp per column pair of the widest
+  // problem of a class
   const int tcb = prec == P32 ? 4 : 8;
-  const int smem = (int)std::min<size_t>(smem_cap, ((size_t)nmax * nmax * tcb + 15) & ~(size_t)15);
-  const int threads = std::min(512, std::max(64, 32 * ((nmax + 1) / 2)));
-  const SvdRtDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
   cudaEvent_t pe = profiler().begin(kk, st.stream);
+  const int wcls[4] = {16, 48, 128, 1024};
+  std::vector<SvdRtDesc> part[4];
+  int nmx[4] = {1, 1, 1, 1};
+  for (auto& x : v) {
+    int c = 0;
+    while (c < 3 && x.n > wcls[c]) ++c;
+    part[c].push_back(x);
+    nmx[c] = std::max(nmx[c], x.n);
+  }
+  (void)nmax;
+  const SvdRtDesc* d[4] = {};
+  for (int c = 0; c < 4; ++c)
+    if (!part[c].empty()) d[c] = st.push(part[c]);
+  ForkJoin fj(st.stream);
+  int li = 0;
+  for (int c = 0; c < 4; ++c) {
+    if (part[c].empty()) continue;
+    const int smem = (int)std::min<size_t>(smem_cap, ((size_t)nmx[c] * nmx[c] * tcb + 15) & ~(size_t)15);
+    const int threads = std::min(512, std::max(64, 32 * ((nmx[c] + 1) / 2)));
+    const unsigned g = (unsigned)part[c].size();
+    cudaStream_t s = fj.stream(li++);
+    if (prec == P32)
+      k_svd_rt<float><<<g, threads, smem, s>>>(d[c], (int)g, 60, smem);
+    else
+      k_svd_rt<double><<<g, threads, smem, s>>>(d[c], (int)g, 60, smem);
+    check_launch("k_svd_rt");
+  }
+  fj.join();
+  profiler().end(kk, st.stream, pe);
+}
+
+void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec) {
+  if (list.empty()) return;
+  IFMM_REQUIRE(md >= 1 && md <= 64, IFMM_EINVAL, "IL transform tile out of range");
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    CK(cudaFuncSetAttribute(k_il_transform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
+    CK(cudaFuncSetAttribute(k_il_transform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 4));
+  });
+  const int* d = st.push(list);
+  prof_batch_tag() = (long)list.size();
+  const int kk = prec == P32 ? KK_GEMM32 : KK_GEMM64;
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
+  const unsigned g = (unsigned)list.size();
   if (prec == P32)
-    k_svd_rt<float><<<(unsigned)v.size(), threads, smem, st.stream>>>(d, (int)v.size(), 60, smem);
+    k_il_transform<float><<<g, 128, 2 * md * md * sizeof(float), st.stream>>>(d, (int)g, t, md);
   else
-    k_svd_rt<double><<<(unsigned)v.size(), threads, smem, st.stream>>>(d, (int)v.size(), 60, smem);
-  check_launch("k_svd_rt");
+    k_il_transform<double><<<g, 128, 2 * md * md * sizeof(double), st.stream>>>(d, (int)g, t, md);
+  check_launch("k_il_transform");
   profiler().end(kk, st.stream, pe);
 }
 

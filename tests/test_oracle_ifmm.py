@@ -37,7 +37,7 @@ def test_exact_other_surfaces():
 
 
 def test_error_scales_with_eps():
-    """Sec. 4.2: the compression error is controlled by eps; ||M A~ x - x|| falls
+    """Sec. 5.1: the compression error is controlled by eps; ||M A~ x - x|| falls
     roughly in proportion to eps."""
     pts = fibonacci_sphere(2048, 1)
     x = np.random.default_rng(0).standard_normal(len(pts))
