@@ -9,6 +9,7 @@
 // the descriptor.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -1175,6 +1176,268 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
     D.A[qr_row(D, i) + (long)j * ld] = (double)v * s_out;
   }
   if (PIV) {
+    for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
+    if (tid == 0) {
+      D.kout[0] = k;
+      if (D.tail) D.tail[0] = (k < kmax && capped) ? tailv : 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Householder QR across a cluster
+// The same factorisations as k_qr_cta for blocks too large for one CTA's shared
+// memory: the rows are split over the R CTAs of a thread-block cluster (CTA r
+// holds logical rows [r*chunk, (r+1)*chunk) of all n columns, chunk = ceil(m/R)),
+// and the CTAs exchange through distributed shared memory.  Every CTA keeps the
+// column norms, the pivot order and the reflector scalars replicated, computed by
+// the same operations in the same order, so every decision (pivot, stop, norm
+// recompute) is identical cluster-wide.  Per column step there are two cluster
+// barriers: after the partial reflector norms (plus the diagonal entry from the
+// CTA that owns row k), and after the partial dot products (plus the owner's row k,
+// from which every CTA forms row k of R for the norm downdate).  The exchange
+// buffers alternate between even and odd steps, so a buffer is rewritten only
+// after every CTA has passed the barrier that follows its last read.
+// Slot: A (chunk x n, ld chunk) | nrm, ref (n) | xd (2n) | xr (2n) | xs (8), in TC | jp (n ints).
+__host__ __device__ __forceinline__ size_t qr_cluster_slot_bytes(int m, int n, int R, int tc_bytes) {
+  const size_t chunk = ((size_t)m + R - 1) / R;
+  return ((chunk * n + 6 * (size_t)n + 8) * tc_bytes + sizeof(int) * (size_t)n + 15) & ~(size_t)15;
+}
+
+template <typename TC, bool PIV>
+__global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__ d, int nd) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int R = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int pi = (int)(blockIdx.x / R);
+  const QrcpDesc D = d[pi < nd ? pi : nd - 1];
+  const int m = D.m, n = D.n;
+  const long ld = D.ld;
+  const int chunk = (m + R - 1) / R;
+  const int r0 = min(m, rank * chunk), ml = min(m, r0 + chunk) - r0;
+  const int mlp = chunk > 0 ? chunk : 1;
+  extern __shared__ __align__(16) unsigned char qsm[];
+  TC* A = (TC*)qsm;
+  TC* nrm = A + (size_t)mlp * n;
+  TC* ref = nrm + n;
+  TC* xd = ref + n;
+  TC* xr = xd + 2 * n;
+  TC* xs = xr + 2 * n;
+  int* jp = (int*)(xs + 8);
+  __shared__ unsigned char flag[1024];
+  __shared__ TC red_s[32], red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double red_g[32];
+  __shared__ double xg;
+  const int tid = threadIdx.x, nt_ = blockDim.x;
+  const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
+  // power-of-two scale from the cluster-wide largest magnitude
+  double gmax = 0.0;
+  for (int e = tid; e < ml * n; e += nt_) {
+    const double a = fabs(D.A[(r0 + e % ml) + (long)(e / ml) * ld]);
+    gmax = (a > gmax || a != a) ? a : gmax;
+  }
+  gmax = warp_max_nan(gmax);
+  if (lane == 0) red_g[w] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    double g = 0.0;
+    for (int i = 0; i < nw; ++i) g = (red_g[i] > g || red_g[i] != red_g[i]) ? red_g[i] : g;
+    xg = g;
+  }
+  for (int j = tid; j < n; j += nt_) flag[j] = 0;
+  cl.sync();
+  gmax = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double g = *cl.map_shared_rank(&xg, r);
+    gmax = (g > gmax || g != g) ? g : gmax;
+  }
+  const double s_in = pow2_scale(gmax);
+  for (int e = tid; e < ml * n; e += nt_) {
+    const int li = e % ml, j = e / ml;
+    A[li + (size_t)j * mlp] = (TC)(D.A[(r0 + li) + (long)j * ld] * s_in);
+  }
+  __syncthreads();
+  if (PIV) {
+    for (int j = w; j < n; j += nw) {
+      const TC* c = A + (size_t)j * mlp;
+      TC ss = 0;
+      for (int i = lane; i < ml; i += 32) ss += c[i] * c[i];
+      ss = warp_sum_t<TC>(ss);
+      if (lane == 0) xd[j] = ss;
+    }
+    cl.sync();
+    for (int j = tid; j < n; j += nt_) {
+      TC s = 0;
+      for (int r = 0; r < R; ++r) s += cl.map_shared_rank(xd, r)[j];
+      nrm[j] = s;
+      ref[j] = s;
+      jp[j] = j;
+    }
+    __syncthreads();
+  }
+  const int kmax = m < n ? m : n;
+  TC tau2 = 0, first = 0;
+  double tailv = 0.0;
+  bool capped = false;
+  int k = 0;
+  for (; k < kmax; ++k) {
+    const int buf = k & 1;
+    if (PIV) {
+      TC best = -1;
+      int bi = n;
+      for (int j = k + tid; j < n; j += nt_) {
+        const TC v = nrm[j];
+        if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const TC ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        red_v[w] = best;
+        red_i[w] = bi;
+      }
+      __syncthreads();
+      best = -1;
+      bi = n;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > best || (red_v[i] == best && red_i[i] < bi)) { best = red_v[i]; bi = red_i[i]; }
+      if (k == 0) {
+        tau2 = (TC)(D.tau_rel * D.tau_rel) * best;
+        first = best;
+      }
+      bool stop = !(best > tau2) || !(best > (TC)0) || bi >= n;
+      if (!stop && D.kcap > 0 && k >= D.kcap) {
+        stop = true;
+        capped = true;
+        tailv = (first > (TC)0) ? sqrt((double)best / (double)first) : 0.0;
+      }
+      if (stop) break;
+      if (bi != k) {
+        TC* ck = A + (size_t)k * mlp;
+        TC* cp = A + (size_t)bi * mlp;
+        for (int i = tid; i < ml; i += nt_) {
+          const TC t = ck[i];
+          ck[i] = cp[i];
+          cp[i] = t;
+        }
+        if (tid == 0) {
+          TC t = nrm[k]; nrm[k] = nrm[bi]; nrm[bi] = t;
+          t = ref[k]; ref[k] = ref[bi]; ref[bi] = t;
+          const int q = jp[k]; jp[k] = jp[bi]; jp[bi] = q;
+        }
+        __syncthreads();
+      }
+    }
+    const int owner = k / chunk;
+    const int lk = k - r0;  // local row of k (in [0, ml) on the owner)
+    // local rows li >= l0 hold logical rows >= k
+    const int l0 = max(0, k - r0);
+    const TC* xk = A + (size_t)k * mlp;
+    TC ss = 0;
+    for (int li = l0 + tid; li < ml; li += nt_)
+      if (r0 + li > k) ss += xk[li] * xk[li];
+    ss = warp_sum_t<TC>(ss);
+    if (lane == 0) red_s[w] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      TC s = 0;
+      for (int i = 0; i < nw; ++i) s += red_s[i];
+      xs[4 * buf] = s;
+      if (rank == owner) xs[4 * buf + 1] = xk[lk];
+    }
+    cl.sync();
+    ss = 0;
+    for (int r = 0; r < R; ++r) ss += cl.map_shared_rank(xs, r)[4 * buf];
+    const TC x0 = cl.map_shared_rank(xs, owner)[4 * buf + 1];
+    const TC nr = sqrt(x0 * x0 + ss);
+    TC alpha = x0, tau = 0, sc = 0;
+    if (!(nr == (TC)0 || ss == (TC)0)) {
+      alpha = (x0 >= (TC)0) ? -nr : nr;
+      tau = (alpha - x0) / alpha;
+      sc = (TC)1 / (x0 - alpha);
+    }
+    const int ntr = n - k - 1;
+    TC* xdb = xd + (size_t)buf * n;
+    TC* xrb = xr + (size_t)buf * n;
+    if (ntr > 0 && tau != (TC)0) {
+      for (int j = k + 1 + w; j < n; j += nw) {
+        const TC* y = A + (size_t)j * mlp;
+        TC acc = 0;
+        for (int li = l0 + lane; li < ml; li += 32) {
+          const TC vi = (r0 + li == k) ? (TC)1 : sc * xk[li];
+          acc += vi * y[li];
+        }
+        acc = warp_sum_t<TC>(acc);
+        if (lane == 0) xdb[j] = acc;
+      }
+    }
+    if (rank == owner)
+      for (int j = k + 1 + tid; j < n; j += nt_) xrb[j] = A[lk + (size_t)j * mlp];
+    cl.sync();
+    int need = 0;
+    if (ntr > 0) {
+      const TC* xro = cl.map_shared_rank(xrb, owner);
+      for (int j = k + 1 + w; j < n; j += nw) {
+        TC dj = 0;
+        if (tau != (TC)0) {
+          for (int r = 0; r < R; ++r) dj += cl.map_shared_rank(xdb, r)[j];
+          dj *= tau;
+          TC* y = A + (size_t)j * mlp;
+          for (int li = l0 + lane; li < ml; li += 32) {
+            const TC vi = (r0 + li == k) ? (TC)1 : sc * xk[li];
+            y[li] -= dj * vi;
+          }
+        }
+        if (PIV && lane == 0) {
+          const TC rkj = xro[j] - dj;  // row k of R: the owner's row k minus d_j v_k, v_k = 1
+          const TC nv = nrm[j] - rkj * rkj;
+          nrm[j] = nv;
+          if (!(nv > (TC)1e-2 * ref[j])) {
+            flag[j] = 1;
+            need = 1;
+          }
+        }
+      }
+    }
+    const int any = __syncthreads_or(need);
+    if (PIV && any) {  // two digits lost (identically in every CTA): recompute
+      TC* xdo = xd + (size_t)(buf ^ 1) * n;
+      for (int j = k + 1 + w; j < n; j += nw) {
+        if (!flag[j]) continue;
+        const TC* y = A + (size_t)j * mlp;
+        TC s2 = 0;
+        for (int li = l0 + lane; li < ml; li += 32)
+          if (r0 + li > k) s2 += y[li] * y[li];
+        s2 = warp_sum_t<TC>(s2);
+        if (lane == 0) xdo[j] = s2;
+      }
+      cl.sync();
+      for (int j = k + 1 + tid; j < n; j += nt_) {
+        if (!flag[j]) continue;
+        TC s = 0;
+        for (int r = 0; r < R; ++r) s += cl.map_shared_rank(xdo, r)[j];
+        nrm[j] = s;
+        ref[j] = s;
+        flag[j] = 0;
+      }
+    }
+    if (rank == owner && tid == 0) A[lk + (size_t)k * mlp] = alpha;
+    __syncthreads();
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+  const double s_out = 1.0 / s_in;
+  for (int e = tid; e < ml * n; e += nt_) {
+    const int li = e % ml, j = e / ml;
+    const int i = r0 + li;
+    const TC v = (j < k && i > j) ? (TC)0 : A[li + (size_t)j * mlp];
+    D.A[i + (long)j * ld] = (double)v * s_out;
+  }
+  if (PIV && rank == 0) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
     if (tid == 0) {
       D.kout[0] = k;

@@ -65,7 +65,7 @@ static void check_gemm(const std::vector<GemmDesc>& v) {
 static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "gauss_jordan", "qr_fp64", "qr_fp32",
                                            "svd_fp64", "svd_fp32", "gemv", "gemv_sum", "p2p", "interp", "tables",
                                            "matvec", "permute", "gauss_jordan_big", "solve_graph",
-                                           "qr_global_fp64", "qr_global_fp32"};
+                                           "qr_global_fp64", "qr_global_fp32", "qr_cluster_fp64", "qr_cluster_fp32"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
 int& prof_level_tag() {
   static thread_local int t = -1;
@@ -342,6 +342,17 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
 // kernels.
 static constexpr size_t kQrWarpSlot = 12 * 1024;
 static constexpr size_t kQrCtaSmem = 220 * 1024;
+// Shared memory a QR problem may use per CTA; IFMM_QR_CTA_LIMIT_KB (<= 220)
+// lowers it, which routes smaller problems through the tall reduction, the
+// cluster and the global-memory kernels (used by the tests of those paths).
+static size_t qr_cta_limit() {
+  static const size_t lim = [] {
+    const char* e = getenv("IFMM_QR_CTA_LIMIT_KB");
+    const long kb = e ? atol(e) : 0;
+    return (kb >= 4 && kb <= 220) ? (size_t)kb * 1024 : kQrCtaSmem;
+  }();
+  return lim;
+}
 
 static void qr_smem_attrs() {
   static std::once_flag once;
@@ -356,19 +367,56 @@ static void qr_smem_attrs() {
     CK(cudaFuncSetAttribute(k_qr_warp<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
     CK(cudaFuncSetAttribute(k_qr_warp<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
     CK(cudaFuncSetAttribute(k_qr_warp<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wmax));
+    CK(cudaFuncSetAttribute(k_qr_cluster<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cluster<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cluster<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    CK(cudaFuncSetAttribute(k_qr_cluster<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   });
 }
 
+// A cluster launch of k_qr_cluster (R CTAs per problem); false when no cluster
+// of that shape and shared memory can be resident (the caller then falls back).
+template <typename TC, bool PIV>
+static bool launch_qr_cluster(const QrcpDesc* d, int nd, int R, size_t smem, cudaStream_t s, bool probe_only) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nd * R), 1, 1);
+  cfg.blockDim = dim3(512, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)R;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (probe_only) {
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_qr_cluster<TC, PIV>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return ncl > 0;
+  }
+  CK(cudaLaunchKernelEx(&cfg, k_qr_cluster<TC, PIV>, d, nd));
+  return true;
+}
+
 // Launches problems that all fit in kQrCtaSmem: the warp bucket, then the CTA bucket.
+static constexpr int kQrClusterSizes[3] = {2, 4, 8};
+
 template <bool PIV>
-static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
+static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int prec,
+                              const std::vector<QrcpDesc>* clus = nullptr) {
   const int tcb = prec == P32 ? 4 : 8;
   // classes: warp per problem (slot <= kQrWarpSlot), then CTA per problem in
   // shared-memory size classes (<= 24, 48, 96, 220 KB).  A launch reserves its
   // largest slot for every CTA, so one large block must not set the occupancy of
   // many small ones; classes with few CTAs per SM get more threads to hide the
   // latency of each column step.  The classes run concurrently.
-  const size_t cls[5] = {kQrWarpSlot, 24 * 1024, 48 * 1024, 96 * 1024, kQrCtaSmem};
+  const size_t lim = qr_cta_limit();
+  const size_t cls[5] = {std::min(kQrWarpSlot, lim), std::min<size_t>(24 * 1024, lim), std::min<size_t>(48 * 1024, lim),
+                         std::min<size_t>(96 * 1024, lim), lim};
   const int thr[5] = {0, 256, 256, 512, 1024};
   std::vector<QrcpDesc> part[5];
   size_t smax[5] = {16, 16, 16, 16, 16};
@@ -382,8 +430,26 @@ static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int
   const QrcpDesc* d[5] = {};
   for (int c = 0; c < 5; ++c)
     if (!part[c].empty()) d[c] = st.push(part[c]);
+  const QrcpDesc* dcl[3] = {};
+  size_t scl[3] = {16, 16, 16};
+  for (int c = 0; clus && c < 3; ++c) {
+    if (clus[c].empty()) continue;
+    dcl[c] = st.push(clus[c]);
+    for (auto& x : clus[c]) scl[c] = std::max(scl[c], qr_cluster_slot_bytes(x.m, x.n, kQrClusterSizes[c], tcb));
+  }
   ForkJoin fj(st.stream);
   int li = 0;
+  for (int c = 0; clus && c < 3; ++c) {
+    if (clus[c].empty()) continue;
+    cudaStream_t s = fj.stream(li++);
+    const int nd = (int)clus[c].size();
+    if (prec == P32)
+      launch_qr_cluster<float, PIV>(dcl[c], nd, kQrClusterSizes[c], scl[c], s, false);
+    else
+      launch_qr_cluster<double, PIV>(dcl[c], nd, kQrClusterSizes[c], scl[c], s, false);
+    check_launch("k_qr_cluster");
+    profiler().count(prec == P32 ? KK_QRC32 : KK_QRC64, 1);
+  }
   for (int c = 0; c < 5; ++c) {
     if (part[c].empty()) continue;
     const int nd = (int)part[c].size();
@@ -414,18 +480,19 @@ static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int
 template <bool PIV>
 static std::vector<size_t> launch_qr_smem(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   const int tcb = prec == P32 ? 4 : 8;
+  const size_t lim = qr_cta_limit();
   qr_smem_attrs();
   std::vector<QrcpDesc> pre, fit;
   std::vector<size_t> rest;
   for (size_t i = 0; i < v.size(); ++i) {
     const QrcpDesc& x = v[i];
-    if (qr_slot_bytes(x.m, x.n, tcb) <= kQrCtaSmem) {
+    if (qr_slot_bytes(x.m, x.n, tcb) <= lim) {
       fit.push_back(x);
       continue;
     }
     // largest chunk height c with a fitting slot
-    long c = (long)((kQrCtaSmem - sizeof(int) * (size_t)x.n - 16) / tcb) / std::max(1, x.n) - 2;
-    while (c > 0 && qr_slot_bytes((int)c, x.n, tcb) > kQrCtaSmem) --c;
+    long c = (long)((lim - sizeof(int) * (size_t)x.n - 16) / tcb) / std::max(1, x.n) - 2;
+    while (c > 0 && qr_slot_bytes((int)c, x.n, tcb) > lim) --c;
     if (x.rb > 0 || x.m <= x.n || c < x.n) {
       rest.push_back(i);
       continue;
@@ -433,7 +500,7 @@ static std::vector<size_t> launch_qr_smem(DescStage& st, const std::vector<QrcpD
     const int nch = (int)((x.m + c - 1) / c);
     const int last = x.m - (nch - 1) * (int)c;
     const int mv = (nch - 1) * x.n + std::min(x.n, last);
-    if (qr_slot_bytes(mv, x.n, tcb) > kQrCtaSmem) {
+    if (qr_slot_bytes(mv, x.n, tcb) > lim) {
       rest.push_back(i);
       continue;
     }
@@ -451,9 +518,38 @@ static std::vector<size_t> launch_qr_smem(DescStage& st, const std::vector<QrcpD
     y.rs = (int)c;
     fit.push_back(y);
   }
+  // what neither fits nor reduces goes to a cluster of 2, 4 or 8 CTAs when its
+  // rows fit their shared memory (rows addressed plainly: rb == 0)
+  std::vector<QrcpDesc> clus[3];
+  std::vector<size_t> left;
+  for (size_t i : rest) {
+    const QrcpDesc& x = v[i];
+    int c = -1;
+    if (x.rb == 0)
+      for (int q = 0; q < 3 && c < 0; ++q)
+        if (qr_cluster_slot_bytes(x.m, x.n, kQrClusterSizes[q], tcb) <= lim) c = q;
+    if (c >= 0) {
+      // residency of the largest cluster slot of each size (probed once)
+      static std::mutex mu;
+      static int ok_cache[2][2][3] = {};  // 0 unknown, 1 yes, -1 no
+      int& ok = ok_cache[prec == P32 ? 0 : 1][PIV ? 1 : 0][c];
+      std::lock_guard<std::mutex> lock(mu);
+      if (ok == 0) {
+        const bool r = prec == P32
+                           ? launch_qr_cluster<float, PIV>(nullptr, 1, kQrClusterSizes[c], kQrCtaSmem, st.stream, true)
+                           : launch_qr_cluster<double, PIV>(nullptr, 1, kQrClusterSizes[c], kQrCtaSmem, st.stream, true);
+        ok = r ? 1 : -1;
+      }
+      if (ok < 0) c = -1;
+    }
+    if (c >= 0)
+      clus[c].push_back(x);
+    else
+      left.push_back(i);
+  }
   if (!pre.empty()) launch_qr_fitting<false>(st, pre, prec);
-  if (!fit.empty()) launch_qr_fitting<PIV>(st, fit, prec);
-  return rest;
+  launch_qr_fitting<PIV>(st, fit, prec, clus);
+  return left;
 }
 
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {

@@ -176,7 +176,7 @@ enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 // the launching stream around every launch.
 enum KernelKind {
   KK_COPY = 0, KK_GEMM64, KK_GEMM32, KK_INV, KK_QR64, KK_QR32, KK_SVD64, KK_SVD32, KK_GEMV, KK_GEMV_SUM, KK_P2P,
-  KK_INTERP, KK_TABLES, KK_MATVEC, KK_PERM, KK_GJ_BIG, KK_SOLVE_GRAPH, KK_QRG64, KK_QRG32, KK_COUNT
+  KK_INTERP, KK_TABLES, KK_MATVEC, KK_PERM, KK_GJ_BIG, KK_SOLVE_GRAPH, KK_QRG64, KK_QRG32, KK_QRC64, KK_QRC32, KK_COUNT
 };
 struct Profiler {
   bool timing = false;
