@@ -1496,6 +1496,54 @@ __global__ void __launch_bounds__(128) k_il_transform(const int* __restrict__ li
   }
 }
 
+// One CTA per (event, side): gathers the weight stack of ZGatherDesc from the
+// level's IL blocks on the device.
+__global__ void __launch_bounds__(256) k_zgather(const ZGatherDesc* __restrict__ d, int nd, ZTables t) {
+  if ((int)blockIdx.x >= nd) return;
+  const ZGatherDesc D = d[blockIdx.x];
+  const int q = D.q, rq = t.r[q];
+  const long ldz = D.ldz;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int off = 0;
+  for (int e = t.il_ptr[q]; e < t.il_ptr[q + 1]; ++e) {
+    const int l = t.il[e], rl = t.r[l];
+    if (rl == 0) continue;
+    if (D.side == 0) {
+      const double* src = t.far[t.il_T[e]];
+      const long lds = t.capr[l];
+      for (int x = tid; x < rl * rq; x += nt) {
+        const int i = x % rl, j = x / rl;
+        D.Z[off + i + j * ldz] = src[i + j * lds];
+      }
+    } else {
+      const double* src = t.far[e];
+      const long lds = t.capr[q];
+      for (int x = tid; x < rl * rq; x += nt) {
+        const int i = x % rl, j = x / rl;
+        D.Z[off + i + j * ldz] = src[j + i * lds];
+      }
+    }
+    off += rl;
+  }
+  if (t.tail) {
+    const int rc = t.rc;
+    if (D.side == 0) {
+      const double* src = t.M2M[q];
+      for (int x = tid; x < rc * rq; x += nt) {
+        const int i = x % rc, j = x / rc;
+        D.Z[off + i + j * ldz] = src[i + (long)j * rc];
+      }
+    } else {
+      const double* src = t.L2L[q];
+      const long lds = t.capr[q];
+      for (int x = tid; x < rc * rq; x += nt) {
+        const int i = x % rc, j = x / rc;
+        D.Z[off + i + j * ldz] = src[j + i * lds];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- Jacobi on P R_k^T
 // B (n x k, column-major, ld n) lives in dynamic shared memory when it fits in
 // smem_bytes, else in the descriptor's global work buffer.  Columns are rotated

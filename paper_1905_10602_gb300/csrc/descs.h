@@ -127,6 +127,26 @@ struct IlTables {
   const double* const* Tp;
 };
 
+// Weight stack Z of one side of a recompression event of node q (reading R4 of
+// the oracle): for l in IL_q with a nonzero rank, in IL order, the block M2L_lq
+// (side 0) or M2L_ql^T (side 1), r_l rows each; then, when the level has a
+// parent (tail != 0), M2M_q (side 0) or L2L_q^T (side 1), rc rows.  Z has ld ldz.
+struct ZGatherDesc {
+  double* Z;
+  int ldz, q, side, pad;
+};
+struct ZTables {
+  const int* il_ptr;
+  const int* il;
+  const int* il_T;
+  double* const* far;
+  const int* capr;
+  const int* r;
+  double* const* M2M;
+  double* const* L2L;
+  int rc, tail;
+};
+
 // Random sketch matrix (m x s, ld m) of +-1 entries from a counter stream.
 struct SketchDesc {
   double* omega;

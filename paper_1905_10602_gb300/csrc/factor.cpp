@@ -59,6 +59,10 @@ struct Work {
   int* d_il = nullptr;
   double** d_far = nullptr;
   int* d_capr = nullptr;
+  int* d_il_ptr = nullptr;
+  int* d_il_T = nullptr;
+  double** d_M2M = nullptr;
+  double** d_L2L = nullptr;
   int slot(int p, int q) const {
     if (p == q) return slot_ptr[p];
     const int* b = LL->nbr.data() + LL->nbr_ptr[p];
@@ -118,6 +122,8 @@ struct Event {
   bool rnd[2] = {false, false};  // randomized range finder (learned mode)
   double* Y[2] = {nullptr, nullptr};
   int my[2] = {0, 0};
+  int zq = -1;  // >= 0: weight stacks gathered on the device for node zq (z lists unused)
+  int mzd = 0;  //   their height
 };
 
 struct Factorizer {
@@ -145,6 +151,7 @@ struct Factorizer {
     std::vector<SvdRtDesc> sr;
     std::vector<InvDesc> inv;
     std::vector<int> tl, tlf;
+    std::vector<ZGatherDesc> zg;
     std::vector<const double*> tn, tpn;
   } L;
   template <class V>
@@ -225,8 +232,9 @@ struct Factorizer {
   // from ev.b before they are overwritten.
   void run_events(std::vector<Event>& evs, Work& W, const std::vector<double*>& P2M_out,
                   const std::vector<double*>& L2P_out, const std::vector<int>& P2M_ld, const std::vector<int>& L2P_ld,
-                  std::vector<InvDesc>* inv_check, int n_inv) {
+                  std::vector<InvDesc>* inv_check, int n_inv, const ZTables* zt = nullptr) {
     auto& cz = fresh(L.cz);
+    auto& zg = fresh(L.zg);
     auto& cf = fresh(L.cf);
     auto& qz = fresh(L.qz);
     auto& qp = fresh(L.qp);
@@ -269,7 +277,10 @@ struct Factorizer {
       const int n = ev.n, r0 = ev.r_old;
       for (int side = 0; side < 2; ++side) {
         int mz = 0;
-        for (auto& z : ev.z[side]) mz += z.rows;
+        if (ev.zq >= 0)
+          mz = ev.mzd;
+        else
+          for (auto& z : ev.z[side]) mz += z.rows;
         int mf = 0;
         for (auto& f : ev.f[side]) mf += f.rows;
         ev.nominal_rows[side] = r0 + mf;
@@ -291,10 +302,15 @@ struct Factorizer {
         double* Z = nullptr;
         if (mw > 0) {
           Z = scratch.alloc((size_t)mz * r0);
-          int off = 0;
-          for (auto& z : ev.z[side]) {
-            cz.push_back(cpy(z.p, z.ld, Z + off, mz, z.rows, z.cols, 1.0, 0.0, z.trans));
-            off += z.rows;
+          if (ev.zq >= 0) {
+            IFMM_REQUIRE(zt, IFMM_EINVAL, "internal: device weight stack without tables");
+            zg.push_back(ZGatherDesc{Z, mz, ev.zq, side, 0});
+          } else {
+            int off = 0;
+            for (auto& z : ev.z[side]) {
+              cz.push_back(cpy(z.p, z.ld, Z + off, mz, z.rows, z.cols, 1.0, 0.0, z.trans));
+              off += z.rows;
+            }
           }
           if (!pathA) {
             qz.push_back(QrDesc{Z, mz, mz, r0});
@@ -361,6 +377,7 @@ struct Factorizer {
     CK(cudaMemsetAsync(kall, 0, sizeof(int) * (evs.size() * 2 + 0), s));
     CK(cudaMemsetAsync(tail_all, 0, sizeof(double) * (evs.size() * 2 + 1), s));
     launch_copy(st, cz);
+    if (!zg.empty()) launch_zgather(st, zg, *zt);
     launch_qr(st, qz, prec);
     cnt.add_gemm(gw);
     launch_gemm(st, gw, prec);
@@ -678,6 +695,20 @@ struct Factorizer {
       if (kappa > 2) {
         W.M2M[i] = levelmem.alloc((size_t)rc * std::max(1, W.capr[i]));
         W.L2L[i] = levelmem.alloc((size_t)rc * std::max(1, W.capr[i]));
+      }
+    }
+    {
+      const size_t ne = std::max<size_t>(1, LL.il.size());
+      W.d_il_ptr = (int*)levelmem.alloc_bytes(sizeof(int) * (nn + 1));
+      W.d_il_T = (int*)levelmem.alloc_bytes(sizeof(int) * ne);
+      W.d_M2M = (double**)levelmem.alloc_bytes(sizeof(double*) * std::max(1, nn));
+      W.d_L2L = (double**)levelmem.alloc_bytes(sizeof(double*) * std::max(1, nn));
+      CK(cudaMemcpyAsync(W.d_il_ptr, LL.il_ptr.data(), sizeof(int) * (nn + 1), cudaMemcpyHostToDevice, s));
+      if (!LL.il.empty())
+        CK(cudaMemcpyAsync(W.d_il_T, W.il_T.data(), sizeof(int) * LL.il.size(), cudaMemcpyHostToDevice, s));
+      if (nn) {
+        CK(cudaMemcpyAsync(W.d_M2M, W.M2M.data(), sizeof(double*) * nn, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(W.d_L2L, W.L2L.data(), sizeof(double*) * nn, cudaMemcpyHostToDevice, s));
       }
     }
     // stage-0 near blocks and the initial bases (r_cheb columns / rows)
@@ -1040,20 +1071,15 @@ struct Factorizer {
       ev.r_old = W.r[q];
       ev.n = W.n[q];
       const int rq = W.r[q];
-      ev.z[0].reserve(LL.il_ptr[q + 1] - LL.il_ptr[q] + 1);
-      ev.z[1].reserve(LL.il_ptr[q + 1] - LL.il_ptr[q] + 1);
-      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
-        const int l = LL.il[e];
-        const int rl = W.r[l];
-        if (!rl || !rq) continue;
-        const int fl = W.il_T[e];
-        ev.z[0].push_back(Blk{W.far[fl], W.capr[l], rl, rq, 0});      // M2L_lq
-        ev.z[1].push_back(Blk{W.far[e], W.capr[q], rl, rq, 1});       // M2L_ql^T
+      // weight stacks [M2L_lq (l in IL_q); M2M_q] and [M2L_ql^T; L2L_q^T],
+      // gathered on the device (k_zgather): only their height is needed here
+      int mzd = 0;
+      if (rq) {
+        for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) mzd += W.r[LL.il[e]];
+        if (W.kappa > 2) mzd += rc;
       }
-      if (W.kappa > 2 && rq) {
-        ev.z[0].push_back(Blk{W.M2M[q], rc, rc, rq, 0});
-        ev.z[1].push_back(Blk{W.L2L[q], W.capr[q], rc, rq, 1});
-      }
+      ev.zq = q;
+      ev.mzd = mzd;
       ev.b[0] = Blk{W.P2M[q], W.capr[q], rq, W.n[q], 0};
       ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
       ev.f[0] = std::move(rowfill_v[slot_of[q]]);
@@ -1066,7 +1092,9 @@ struct Factorizer {
     }
     phase("host_events", tp);
     const double w0 = t_wait;
-    run_events(evs, W, po, lo, pld, lld, nullptr, ng);
+    const ZTables zt{W.d_il_ptr, W.d_il, W.d_il_T, W.d_far, W.d_capr, st.push(W.r), W.d_M2M, W.d_L2L, rc,
+                     W.kappa > 2 ? 1 : 0};
+    run_events(evs, W, po, lo, pld, lld, nullptr, ng, &zt);
     F.stat_add("host_run_events_wait", t_wait - w0);
     phase("host_run_events", tp);
     // ---- phase B: re-express blocks that touch a re-based node

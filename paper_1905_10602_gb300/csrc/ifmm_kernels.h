@@ -41,6 +41,8 @@ void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, dou
 void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info);
 // phase-B basis changes of the touched IL entries `list` (every rank <= md <= 64)
 void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec);
+// recompression weight stacks gathered on the device from the IL tables
+void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTables& t);
 void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n);
 void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n);
 void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n);

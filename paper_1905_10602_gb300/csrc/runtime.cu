@@ -741,6 +741,16 @@ void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTa
   profiler().end(kk, st.stream, pe);
 }
 
+void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTables& t) {
+  if (v.empty()) return;
+  const ZGatherDesc* d = st.push(v);
+  prof_batch_tag() = (long)v.size();
+  cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
+  k_zgather<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), t);
+  check_launch("k_zgather");
+  profiler().end(KK_COPY, st.stream, pe);
+}
+
 void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v) {
   if (v.empty()) return;
   const SketchDesc* d = st.push(v);
