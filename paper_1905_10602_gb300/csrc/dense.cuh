@@ -68,23 +68,61 @@ __device__ __forceinline__ TC stage_val(double v) {
     return (TC)v;
 }
 
+// One warp per GEMM with m, n <= 32 (any k), four warps per CTA.  The operands
+// are staged in chunks of 16 along k through the warp's shared memory (one
+// load and conversion per element); lane j accumulates column j of C in
+// registers, reading the A chunk by broadcast.
 template <typename TC, bool RB = false>
-__global__ void k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
-  const int di = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(128) k_gemm_small(const GemmDesc* __restrict__ d, int nd) {
+  constexpr int KC = 16;
+  __shared__ TC As[4][32][KC + 1];
+  __shared__ TC Bs[4][KC][33];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int di = blockIdx.x * 4 + w;
   if (di >= nd) return;
   const GemmDesc D = d[di];
-  const int total = D.m * D.n;
-  for (int e = lane; e < total; e += 32) {
-    const int i = e % D.m, j = e / D.m;
-    TC acc = 0;
-    for (int q = 0; q < D.k; ++q) {
-      const double a = D.ta ? D.A[q + (long)i * D.lda] : D.A[i + (long)q * D.lda];
-      const double b = D.tb ? D.B[j + (long)q * D.ldb] : D.B[q + (long)j * D.ldb];
-      acc += stage_val<TC, RB>(a) * stage_val<TC, RB>(b);
+  const int m = D.m, n = D.n;
+  TC acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = (TC)0;
+  for (int k0 = 0; k0 < D.k; k0 += KC) {
+    const int kc = min(KC, D.k - k0);
+    // A chunk: row i = lane, columns k0..k0+kc-1 (rows >= m and columns >= kc zero)
+    for (int kk = 0; kk < KC; ++kk) {
+      double v = 0.0;
+      if (lane < m && kk < kc) {
+        const int c = k0 + kk;
+        v = D.ta ? D.A[c + (long)lane * D.lda] : D.A[lane + (long)c * D.lda];
+      }
+      As[w][lane][kk] = stage_val<TC, RB>(v);
     }
-    double* o = D.C + i + (long)j * D.ldc;
-    const double v = D.alpha * (double)acc;
-    *o = (D.beta == 0.0) ? v : v + D.beta * (*o);
+    // B chunk: rows k0..k0+kc-1 (kk = lane % 16), columns j
+    for (int x = lane; x < KC * 32; x += 32) {
+      const int kk = x % KC, j = x / KC;
+      double v = 0.0;
+      if (kk < kc && j < n) {
+        const int r = k0 + kk;
+        v = D.tb ? D.B[j + (long)r * D.ldb] : D.B[r + (long)j * D.ldb];
+      }
+      Bs[w][kk][j] = stage_val<TC, RB>(v);
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      const TC b = Bs[w][kk][lane];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] += As[w][i][kk] * b;
+    }
+    __syncwarp();
+  }
+  if (lane < n) {
+    double* o = D.C + (long)lane * D.ldc;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i >= m) break;
+      const double v = D.alpha * (double)acc[i];
+      o[i] = (D.beta == 0.0) ? v : v + D.beta * o[i];
+    }
   }
 }
 
@@ -1444,6 +1482,147 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
       if (D.tail) D.tail[0] = (k < kmax && capped) ? tailv : 0.0;
     }
   }
+}
+
+// ---------------------------------------------------------------- Gauss-Jordan across a cluster
+// The inverse of k_inv (partial pivoting, in place, the row interchanges undone
+// as column interchanges at the end) with the rows split over the R CTAs of a
+// thread-block cluster (CTA r holds rows [r*chunk, (r+1)*chunk), chunk =
+// ceil(n/R), all n columns, column-major with ld chunk), so that a color with
+// few large pivot blocks still occupies many SMs of GB300's narrow FP64 pipes.
+// Step k: each CTA publishes its best |A(i,k)|, i >= k (barrier 1); every CTA
+// picks the same pivot row p (ties: smallest i); the CTAs owning rows k and p
+// publish copies of them (barrier 2); every CTA forms the scaled pivot row from
+// the copy of row p and eliminates column k from its rows, the owner of p first
+// taking in the copy of row k.  Exchange buffers alternate between even and odd
+// steps.  Every element sees the same operations as in k_inv.
+// Slot: A (chunk x n) | ck (chunk) | prow (n) | xrk, xrp (2 x n each) | xv (2),
+// in double | piv (n), xi (2) ints.
+__host__ __device__ __forceinline__ size_t inv_cluster_slot_bytes(int n, int R) {
+  const size_t chunk = ((size_t)n + R - 1) / R;
+  return ((chunk * n + chunk + 5 * (size_t)n + 2) * sizeof(double) + sizeof(int) * ((size_t)n + 2) + 15) &
+         ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(512) k_inv_cluster(const InvDesc* __restrict__ d, int nd) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int R = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int pi = (int)(blockIdx.x / R);
+  const InvDesc D = d[pi < nd ? pi : nd - 1];
+  const int n = D.n;
+  const long ld = D.ld;
+  const int chunk = (n + R - 1) / R;
+  const int r0 = min(n, rank * chunk), ml = min(n, r0 + chunk) - r0;
+  const int cp = chunk > 0 ? chunk : 1;
+  extern __shared__ __align__(16) unsigned char ism2[];
+  double* A = (double*)ism2;
+  double* ck = A + (size_t)cp * n;
+  double* prow = ck + cp;
+  double* xrk = prow + n;
+  double* xrp = xrk + 2 * n;
+  double* xv = xrp + 2 * n;
+  int* piv = (int*)(xv + 2);
+  int* xi = piv + n;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  for (int j = w; j < n; j += nw)
+    for (int li = lane; li < ml; li += 32) A[li + (size_t)j * cp] = D.A[(r0 + li) + (long)j * ld];
+  __syncthreads();
+  int bad = 0;
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    double best = -1.0;
+    int bi = n;
+    for (int li = max(0, k - r0) + tid; li < ml; li += nt) {
+      const double v = fabs(A[li + (size_t)k * cp]);
+      const int i = r0 + li;
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) {
+      red_v[w] = best;
+      red_i[w] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = -1.0;
+      int bb = n;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > bv || (red_v[i] == bv && red_i[i] < bb)) { bv = red_v[i]; bb = red_i[i]; }
+      xv[b] = bv;
+      xi[b] = bb;
+    }
+    cl.sync();
+    double bv = -1.0;
+    int p = n;
+    for (int r = 0; r < R; ++r) {
+      const double v = cl.map_shared_rank(xv, r)[b];
+      const int i = cl.map_shared_rank(xi, r)[b];
+      if (v > bv || (v == bv && i < p)) { bv = v; p = i; }
+    }
+    if (!(bv > 0.0) || p >= n) {  // the same decision in every CTA
+      bad = k + 1;
+      break;
+    }
+    if (tid == 0) piv[k] = p;
+    const int ok = k / chunk, op = p / chunk;
+    if (rank == ok)
+      for (int j = tid; j < n; j += nt) xrk[(size_t)b * n + j] = A[(k - r0) + (size_t)j * cp];
+    if (rank == op)
+      for (int j = tid; j < n; j += nt) xrp[(size_t)b * n + j] = A[(p - r0) + (size_t)j * cp];
+    cl.sync();
+    const double* rp = cl.map_shared_rank(xrp, op) + (size_t)b * n;
+    const double inv = 1.0 / rp[k];
+    for (int j = tid; j < n; j += nt) prow[j] = (j == k) ? inv : rp[j] * inv;
+    if (rank == op && p != k) {
+      const double* rk = cl.map_shared_rank(xrk, ok) + (size_t)b * n;
+      for (int j = tid; j < n; j += nt) A[(p - r0) + (size_t)j * cp] = rk[j];
+    }
+    __syncthreads();
+    // multipliers of column k, saved before column k itself is overwritten
+    for (int li = tid; li < ml; li += nt) ck[li] = A[li + (size_t)k * cp];
+    __syncthreads();
+    for (int j = w; j < n; j += nw) {
+      const double pj = prow[j];
+      double* col = A + (size_t)j * cp;
+      for (int li = lane; li < ml; li += 32) {
+        if (r0 + li == k) continue;
+        const double a = (j == k) ? 0.0 : col[li];
+        col[li] = a - ck[li] * pj;
+      }
+    }
+    __syncthreads();
+    if (rank == ok)
+      for (int j = tid; j < n; j += nt) A[(k - r0) + (size_t)j * cp] = prow[j];
+    __syncthreads();
+  }
+  if (!bad) {
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k)
+        for (int li = tid; li < ml; li += nt) {
+          const double t = A[li + (size_t)k * cp];
+          A[li + (size_t)k * cp] = A[li + (size_t)p * cp];
+          A[li + (size_t)p * cp] = t;
+        }
+      __syncthreads();
+    }
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+  if (!bad)
+    for (int j = w; j < n; j += nw)
+      for (int li = lane; li < ml; li += 32) D.A[(r0 + li) + (long)j * ld] = A[li + (size_t)j * cp];
+  if (rank == 0 && tid == 0) D.info[0] = bad;
 }
 
 // ---------------------------------------------------------------- IL basis changes

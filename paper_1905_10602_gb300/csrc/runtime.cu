@@ -236,7 +236,7 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   v.clear();
   for (auto& x : v0) {
     if (x.m <= 0 || x.n <= 0) continue;
-    (x.m <= 32 && x.n <= 32 && x.k <= 128 ? small : v).push_back(x);
+    (x.m <= 32 && x.n <= 32 ? small : v).push_back(x);
   }
   if (!small.empty()) {
     const GemmDesc* d = st.push(small);
@@ -244,11 +244,11 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
     prof_batch_tag() = (long)small.size();
     cudaEvent_t pe = profiler().begin(kk, st.stream);
     if (prec == P32)
-      k_gemm_small<float><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<float><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
     else if (prec == P16)
-      k_gemm_small<float, true><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<float, true><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
     else
-      k_gemm_small<double><<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<double><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
     check_launch("k_gemm_small");
     profiler().end(kk, st.stream, pe);
   }
@@ -277,20 +277,106 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   profiler().end(kk, st.stream, pe);
 }
 
+// A cluster launch of k_inv_cluster (R CTAs per matrix); false when no cluster of
+// that shape and shared memory can be resident.
+static bool launch_inv_cluster(const InvDesc* d, int nd, int R, size_t smem, cudaStream_t s, bool probe_only) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nd * R), 1, 1);
+  cfg.blockDim = dim3(512, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)R;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (probe_only) {
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_inv_cluster, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return ncl > 0;
+  }
+  CK(cudaLaunchKernelEx(&cfg, k_inv_cluster, d, nd));
+  return true;
+}
+
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   if (v.empty()) return;
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
     req(v[i].A, span(v[i].n, v[i].n, v[i].ld), "inv.A", i);
     req(v[i].info, sizeof(int), "inv.info", i);
   }
-  // size classes: shared-memory Gauss-Jordan for n <= 64 and n <= 160, the
-  // batched multi-CTA variant above
+  // Size classes.  Blocks of n <= 32: one CTA each in shared memory.  Larger
+  // ones: the FP64 elimination of one block on one SM is bound by that SM's FP64
+  // pipe, so when a color has fewer large blocks than SMs each block is spread
+  // over a cluster of R CTAs (R ~ SMs / blocks, at most 8, and at least what its
+  // rows need to fit); R = 1 is one CTA in shared memory (n <= 160).  Blocks that
+  // fit no cluster take the batched multi-CTA kernels below.
+  static constexpr int kInvCta = 0;
+  static constexpr size_t kInvClusterSmem = 220 * 1024;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+    CK(cudaFuncSetAttribute(k_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvClusterSmem));
   });
-  std::vector<InvDesc> cls[3];
-  for (auto& x : v) cls[x.n <= 64 ? 0 : (x.n <= 160 ? 1 : 2)].push_back(x);
+  static int cl_ok[4] = {0, 0, 0, 0};  // per R = 1, 2, 4, 8: 0 unknown, 1 yes, -1 no
+  static std::mutex cl_mu;
+  int nbig = 0;
+  for (auto& x : v) nbig += x.n > 32;
+  int rwant = 1;
+  while (rwant < 8 && nbig * rwant * 2 <= 152) rwant *= 2;
+  std::vector<InvDesc> cls[3], ccl[4];
+  size_t csm[4] = {16, 16, 16, 16};
+  for (auto& x : v) {
+    if (x.n <= 32) {
+      cls[0].push_back(x);
+      continue;
+    }
+    int R = rwant, q = 0;
+    while ((1 << q) < R) ++q;
+    while (q < 4 && inv_cluster_slot_bytes(x.n, 1 << q) > kInvClusterSmem) ++q;
+    if (q == 0 && x.n <= 160) {
+      cls[1].push_back(x);
+      continue;
+    }
+    if (q == 0) q = 1;
+    bool ok = false;
+    if (q < 4) {
+      std::lock_guard<std::mutex> lock(cl_mu);
+      if (cl_ok[q] == 0)
+        cl_ok[q] = launch_inv_cluster(nullptr, 1, 1 << q, kInvClusterSmem, st.stream, true) ? 1 : -1;
+      ok = cl_ok[q] > 0;
+    }
+    if (ok) {
+      ccl[q].push_back(x);
+      csm[q] = std::max(csm[q], inv_cluster_slot_bytes(x.n, 1 << q));
+    } else {
+      cls[x.n <= 160 ? 1 : 2].push_back(x);
+    }
+  }
+  (void)kInvCta;
+  const InvDesc* dcl[4] = {};
+  for (int q = 1; q < 4; ++q)
+    if (!ccl[q].empty()) dcl[q] = st.push(ccl[q]);
+  int ncl = 0;
+  for (int q = 1; q < 4; ++q) ncl += (int)ccl[q].size();
+  if (ncl) {
+    prof_batch_tag() = (long)ncl;
+    cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
+    ForkJoin fj(st.stream);
+    int li = 0;
+    for (int q = 1; q < 4; ++q) {
+      if (ccl[q].empty()) continue;
+      launch_inv_cluster(dcl[q], (int)ccl[q].size(), 1 << q, csm[q], fj.stream(li++), false);
+      check_launch("k_inv_cluster");
+    }
+    fj.join();
+    profiler().end(KK_INV, st.stream, pe);
+  }
   for (int c = 0; c < 2; ++c) {
     if (cls[c].empty()) continue;
     int nmax = 0;
