@@ -32,14 +32,15 @@ __global__ void k_copy(const CopyDesc* __restrict__ d, int nd) {
   const int b = blockIdx.x;
   if (b >= nd) return;
   const CopyDesc D = d[b];
-  const long total = (long)D.rows * D.cols;
-  for (long e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = (int)(e % D.rows), j = (int)(e / D.rows);
-    double v = 0.0;
-    if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
-    double* o = D.dst + i + (long)j * D.ldd;
-    *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
-  }
+  // warps over columns, lanes over rows (no per-element index division)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x >> 5; j < D.cols; j += nw)
+    for (int i = lane; i < D.rows; i += 32) {
+      double v = 0.0;
+      if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
+      double* o = D.dst + i + (long)j * D.ldd;
+      *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
+    }
 }
 
 // ---------------------------------------------------------------- small problems
@@ -234,11 +235,13 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
   __shared__ int red_i[32];
   __shared__ int s_p;
   __shared__ int s_bad;
+  __shared__ double s_inv;
   if (threadIdx.x == 0) s_bad = 0;
-  if (in_smem)
-    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) A[e] = D.A[(e % n) + (e / n) * (long)D.ld];
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (in_smem)
+    for (int j = w; j < n; j += nw)
+      for (int i = lane; i < n; i += 32) A[i + (long)j * n] = D.A[i + (long)j * D.ld];
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
     int bi = n;
@@ -272,8 +275,10 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
         A[k + j * ld] = A[p + j * ld];
         A[p + j * ld] = t;
       }
+    // the reciprocal of the pivot once (an FP64 divide is a long FP64 sequence)
+    if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];
     __syncthreads();
-    const double inv = 1.0 / A[k + k * ld];
+    const double inv = s_inv;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const double v = (j == k) ? inv : A[k + j * ld] * inv;
       rowk[j] = v;
@@ -281,12 +286,15 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i + k * ld];
     __syncthreads();
-    const long total = (long)n * n;
-    for (long e = threadIdx.x; e < total; e += blockDim.x) {
-      const int i = (int)(e % n), j = (int)(e / n);
-      if (i == k) continue;
-      const double a = (j == k) ? 0.0 : A[i + j * ld];
-      A[i + j * ld] = a - colk[i] * rowk[j];
+    // warps over columns, lanes over rows (no per-element index division)
+    for (int j = w; j < n; j += nw) {
+      const double rj = rowk[j];
+      double* cj = A + (long)j * ld;
+      for (int i = lane; i < n; i += 32) {
+        if (i == k) continue;
+        const double a = (j == k) ? 0.0 : cj[i];
+        cj[i] = a - colk[i] * rj;
+      }
     }
     __syncthreads();
   }
@@ -305,7 +313,8 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
     __syncthreads();
   }
   if (in_smem)
-    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) D.A[(e % n) + (e / n) * (long)D.ld] = A[e];
+    for (int j = w; j < n; j += nw)
+      for (int i = lane; i < n; i += 32) D.A[i + (long)j * D.ld] = A[i + (long)j * n];
   if (threadIdx.x == 0) D.info[0] = 0;
 }
 
@@ -365,8 +374,10 @@ __global__ void k_gjb_pivot(const InvDesc* __restrict__ d, int nd, int k, double
       A[k + j * ld] = A[p + j * ld];
       A[p + j * ld] = t;
     }
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];  // once: an FP64 divide is a long FP64 sequence
   __syncthreads();
-  const double inv = 1.0 / A[k + k * ld];
+  const double inv = s_inv;
   for (int j = threadIdx.x; j < n; j += blockDim.x) rowk[j] = (j == k) ? inv : A[k + j * ld] * inv;
   for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i + k * ld];
 }
@@ -382,14 +393,18 @@ __global__ void k_gjb_update(const InvDesc* __restrict__ d, int nd, int k, const
   const long ld = D.ld;
   const double* rowk = work + work_off[b];
   const double* colk = rowk + n;
-  const long total = (long)n * n;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i == k) {
-      A[i + j * ld] = rowk[j];
-    } else {
-      const double a = (j == k) ? 0.0 : A[i + j * ld];
-      A[i + j * ld] = a - colk[i] * rowk[j];
+  // columns over (CTA, warp), lanes over rows (no per-element index division)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = blockIdx.x * nw + (threadIdx.x >> 5); j < n; j += gridDim.x * nw) {
+    const double rj = rowk[j];
+    double* cj = A + (long)j * ld;
+    for (int i = lane; i < n; i += 32) {
+      if (i == k) {
+        cj[i] = rj;
+      } else {
+        const double a = (j == k) ? 0.0 : cj[i];
+        cj[i] = a - colk[i] * rj;
+      }
     }
   }
 }
@@ -1527,12 +1542,15 @@ __global__ void __launch_bounds__(512) k_inv_cluster(const InvDesc* __restrict__
   int* xi = piv + n;
   __shared__ double red_v[32];
   __shared__ int red_i[32];
+  __shared__ double s_inv;
+  __shared__ int s_p;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
   for (int j = w; j < n; j += nw)
     for (int li = lane; li < ml; li += 32) A[li + (size_t)j * cp] = D.A[(r0 + li) + (long)j * ld];
   __syncthreads();
   int bad = 0;
+  const int tot = ml * n;
   for (int k = 0; k < n; ++k) {
     const int b = k & 1;
     double best = -1.0;
@@ -1562,18 +1580,31 @@ __global__ void __launch_bounds__(512) k_inv_cluster(const InvDesc* __restrict__
       xi[b] = bb;
     }
     cl.sync();
-    double bv = -1.0;
-    int p = n;
-    for (int r = 0; r < R; ++r) {
-      const double v = cl.map_shared_rank(xv, r)[b];
-      const int i = cl.map_shared_rank(xi, r)[b];
-      if (v > bv || (v == bv && i < p)) { bv = v; p = i; }
+    // one warp reads the R candidates and decides (the same decision in every CTA)
+    if (w == 0) {
+      double v = -1.0;
+      int i = n;
+      if (lane < R) {
+        v = cl.map_shared_rank(xv, lane)[b];
+        i = cl.map_shared_rank(xi, lane)[b];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+      }
+      if (lane == 0) {
+        s_p = (!(v > 0.0) || i >= n) ? -1 : i;
+        if (s_p >= 0) piv[k] = i;
+      }
     }
-    if (!(bv > 0.0) || p >= n) {  // the same decision in every CTA
+    __syncthreads();
+    const int p = s_p;
+    if (p < 0) {
       bad = k + 1;
       break;
     }
-    if (tid == 0) piv[k] = p;
     const int ok = k / chunk, op = p / chunk;
     if (rank == ok)
       for (int j = tid; j < n; j += nt) xrk[(size_t)b * n + j] = A[(k - r0) + (size_t)j * cp];
@@ -1581,28 +1612,36 @@ __global__ void __launch_bounds__(512) k_inv_cluster(const InvDesc* __restrict__
       for (int j = tid; j < n; j += nt) xrp[(size_t)b * n + j] = A[(p - r0) + (size_t)j * cp];
     cl.sync();
     const double* rp = cl.map_shared_rank(xrp, op) + (size_t)b * n;
-    const double inv = 1.0 / rp[k];
-    for (int j = tid; j < n; j += nt) prow[j] = (j == k) ? inv : rp[j] * inv;
-    if (rank == op && p != k) {
-      const double* rk = cl.map_shared_rank(xrk, ok) + (size_t)b * n;
+    if (tid == 0) s_inv = 1.0 / rp[k];  // once per CTA: an FP64 divide is a long FP64 sequence
+    // multipliers of column k (the owner of p takes in the copy of row k there)
+    const double* rk = (rank == op && p != k) ? cl.map_shared_rank(xrk, ok) + (size_t)b * n : nullptr;
+    for (int li = tid; li < ml; li += nt) ck[li] = (rk && r0 + li == p) ? rk[k] : A[li + (size_t)k * cp];
+    if (rk)
       for (int j = tid; j < n; j += nt) A[(p - r0) + (size_t)j * cp] = rk[j];
-    }
     __syncthreads();
-    // multipliers of column k, saved before column k itself is overwritten
-    for (int li = tid; li < ml; li += nt) ck[li] = A[li + (size_t)k * cp];
+    const double inv = s_inv;
+    for (int j = tid; j < n; j += nt) prow[j] = (j == k) ? inv : rp[j] * inv;
     __syncthreads();
-    for (int j = w; j < n; j += nw) {
-      const double pj = prow[j];
-      double* col = A + (size_t)j * cp;
-      for (int li = lane; li < ml; li += 32) {
-        if (r0 + li == k) continue;
-        const double a = (j == k) ? 0.0 : col[li];
-        col[li] = a - ck[li] * pj;
+    // eliminate column k from every local row but k; (li, j) walked with
+    // incremental indices; the owner of k writes the scaled pivot row
+    {
+      int li = tid % max(ml, 1), j = tid / max(ml, 1);
+      const int di = nt % max(ml, 1), dj = nt / max(ml, 1);
+      for (int e = tid; e < tot; e += nt) {
+        const int i = r0 + li;
+        double* a = A + li + (size_t)j * cp;
+        if (i == k)
+          *a = prow[j];
+        else
+          *a = ((j == k) ? 0.0 : *a) - ck[li] * prow[j];
+        li += di;
+        j += dj;
+        if (li >= ml) {
+          li -= ml;
+          ++j;
+        }
       }
     }
-    __syncthreads();
-    if (rank == ok)
-      for (int j = tid; j < n; j += nt) A[(k - r0) + (size_t)j * cp] = prow[j];
     __syncthreads();
   }
   if (!bad) {

@@ -404,7 +404,7 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     const InvDesc* d = st.push(L);
     const long* o = st.push(off);
     const int nb = (int)L.size();
-    const int gx = (int)std::max<long>(1, std::min<long>((long)nmax * nmax / 1024 + 1, 64));
+    const int gx = (int)std::max<long>(1, std::min<long>(((long)nmax + 7) / 8, 64));
     prof_batch_tag() = (long)nb;
     cudaEvent_t pe = profiler().begin(KK_GJ_BIG, st.stream, 2L * nmax + 1);
     for (int k = 0; k < nmax; ++k) {
@@ -1285,8 +1285,10 @@ __global__ void k_gj_pivot(double* A, long ld, int n, int k, int* piv, double* r
       A[k + j * ld] = A[p + j * ld];
       A[p + j * ld] = t;
     }
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];  // once: an FP64 divide is a long FP64 sequence
   __syncthreads();
-  const double inv = 1.0 / A[k + k * ld];
+  const double inv = s_inv;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const double v = (j == k) ? inv : A[k + j * ld] * inv;
     rowk[j] = v;
@@ -1297,14 +1299,21 @@ __global__ void k_gj_pivot(double* A, long ld, int n, int k, int* piv, double* r
 __global__ void k_gj_update(double* A, long ld, int n, int k, const double* rowk, const double* colk,
                             const int* info) {
   if (info[0] != 0) return;
-  const long total = (long)n * n;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i == k) {
-      A[i + j * ld] = rowk[j];
-    } else {
-      const double a = (j == k) ? 0.0 : A[i + j * ld];
-      A[i + j * ld] = a - colk[i] * rowk[j];
+  // (column, 256-row segment) items over (CTA, warp), lanes over rows
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nseg = (n + 255) / 256;
+  for (int it = blockIdx.x * nw + (threadIdx.x >> 5); it < n * nseg; it += gridDim.x * nw) {
+    const int j = it / nseg, seg = it % nseg;
+    const double rj = rowk[j];
+    double* cj = A + (long)j * ld;
+    const int i1 = min(n, (seg + 1) * 256);
+    for (int i = seg * 256 + lane; i < i1; i += 32) {
+      if (i == k) {
+        cj[i] = rj;
+      } else {
+        const double a = (j == k) ? 0.0 : cj[i];
+        cj[i] = a - colk[i] * rj;
+      }
     }
   }
 }
@@ -1327,7 +1336,7 @@ __global__ void k_gj_colswap(double* A, long ld, int n, const int* piv, const in
 void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info) {
   // d_work_int: n ints (pivots); d_work: 2n doubles; d_info: 1 int (zeroed here)
   CK(cudaMemsetAsync(d_info, 0, sizeof(int), s));
-  const int upd_blocks = (int)std::min<long>(152L * 8, ((long)n * n + 255) / 256);
+  const int upd_blocks = (int)std::max<long>(1, std::min<long>(152L * 8, ((long)n * ((n + 255) / 256) + 7) / 8));
   cudaEvent_t pe = profiler().begin(KK_GJ_BIG, s, 2L * n + 1);
   for (int k = 0; k < n; ++k) {
     k_gj_pivot<<<1, 1024, 0, s>>>(A, ld, n, k, d_work_int, d_work, d_work + n, d_info);
