@@ -233,6 +233,14 @@ const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
  * resets the per-kernel counters and, if timing != 0, brackets every later kernel
  * launch (or solve graph launch) with CUDA events on its stream.  Timing adds
  * event records between launches; leave it off for production runs. */
+/* Diagnostic: the binary64 -> binary32 conversion the FP32 kernels use on their
+ * FP64 storage (integer operations on the IEEE-754 fields, GB300's FP64 pipe
+ * being narrow), applied on the device to n host doubles x scaled by 2^shift:
+ * f[i] = x[i] * 2^shift rounded to nearest (ties away from zero; below the
+ * binary32 normal range -> signed zero, above it -> infinity), back[i] = f[i] *
+ * 2^-shift as a double (exact).  |shift| <= 200, n <= 2^26; host arrays. */
+ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, double* back);
+
 ifmm_status ifmm_profile(int timing);
 
 /* Counter `index` (0..): kernel name, kernels launched so far (a solve graph

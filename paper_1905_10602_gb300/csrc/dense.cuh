@@ -32,14 +32,16 @@ __global__ void k_copy(const CopyDesc* __restrict__ d, int nd) {
   const int b = blockIdx.x;
   if (b >= nd) return;
   const CopyDesc D = d[b];
-  // warps over columns, lanes over rows (no per-element index division)
+  // warps over columns, lanes over rows (no per-element index division); the
+  // common alpha = 1, beta in {0, 1} cases take no FP64 multiply
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int mode = (D.alpha == 1.0 && D.beta == 0.0) ? 0 : ((D.alpha == 1.0 && D.beta == 1.0) ? 1 : 2);
   for (int j = threadIdx.x >> 5; j < D.cols; j += nw)
     for (int i = lane; i < D.rows; i += 32) {
       double v = 0.0;
       if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
       double* o = D.dst + i + (long)j * D.ldd;
-      *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
+      *o = mode == 0 ? v : (mode == 1 ? *o + v : ((D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o)));
     }
 }
 
@@ -50,13 +52,63 @@ __global__ void k_copy_small(const CopyDesc* __restrict__ d, int nd) {
   if (di >= nd) return;
   const CopyDesc D = d[di];
   const int total = D.rows * D.cols;
+  const int mode = (D.alpha == 1.0 && D.beta == 0.0) ? 0 : ((D.alpha == 1.0 && D.beta == 1.0) ? 1 : 2);
   for (int e = lane; e < total; e += 32) {
     const int i = e % D.rows, j = e / D.rows;
     double v = 0.0;
     if (D.src) v = D.trans ? D.src[j + (long)i * D.lds] : D.src[i + (long)j * D.lds];
     double* o = D.dst + i + (long)j * D.ldd;
-    *o = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o);
+    *o = mode == 0 ? v : (mode == 1 ? *o + v : ((D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*o)));
   }
+}
+
+// ---------------------------------------------------------------- FP64 <-> FP32 on the integer pipes
+// GB300 executes double arithmetic and double<->float conversions on its narrow
+// FP64 pipe (about 2 operations per clock per SM).  The FP32 kernels read and
+// write FP64 storage, so they convert with integer operations on the IEEE-754
+// fields instead, folding an optional power-of-two scale 2^sh into the
+// exponent.  d2f_pow2 rounds to nearest with ties away from zero (IEEE binary64
+// -> binary32 keeps the top 23 of 52 fraction bits; the first dropped bit
+// decides); results below the binary32 normal range become signed zero, above it
+// infinity; NaN and infinity inputs and non-normal outputs of f2d_pow2 take the
+// hardware conversion (rare).
+__device__ __forceinline__ float d2f_pow2(double d, int sh) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ah = hi & 0x7fffffffu, sg = hi & 0x80000000u;
+  if (ah >= 0x7ff00000u) return (float)d;
+  const int e = (int)(ah >> 20) + sh;  // biased binary64 exponent after scaling
+  if (ah < 0x00100000u || e <= 896) return __uint_as_float(sg);
+  if (e >= 1151) return __uint_as_float(sg | 0x7f800000u);
+  unsigned f = ((unsigned)(e - 896) << 23) | ((ah & 0x000fffffu) << 3) | (lo >> 29);
+  f += (lo >> 28) & 1u;  // a carry into the exponent is the correct rounding
+  return __uint_as_float(sg | f);
+}
+__device__ __forceinline__ double f2d_pow2(float f, int sh) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7fffffffu, sg = u & 0x80000000u;
+  if (a == 0) return __hiloint2double((int)sg, 0);
+  const int e = (int)(a >> 23) + 896 + sh;  // biased binary64 exponent
+  if (a < 0x00800000u || a >= 0x7f800000u || e <= 0 || e >= 2047) return ldexp((double)f, sh);
+  return __hiloint2double((int)(sg | ((unsigned)e << 20) | ((a & 0x007fffffu) >> 3)), (int)(a << 29));
+}
+// biased binary64 exponent of |d| (0 for zero and subnormals, 2047 for inf/NaN)
+__device__ __forceinline__ int dexp(double d) { return (int)(((unsigned)__double2hiint(d) & 0x7fffffffu) >> 20); }
+
+// value of a double as the arithmetic type TC, times 2^sh
+template <typename TC>
+__device__ __forceinline__ TC ld_tc(double d, int sh = 0) {
+  if constexpr (sizeof(TC) == 4)
+    return d2f_pow2(d, sh);
+  else
+    return sh ? ldexp(d, sh) : d;
+}
+// a TC value times 2^sh, as a double
+template <typename TC>
+__device__ __forceinline__ double st_tc(TC v, int sh = 0) {
+  if constexpr (sizeof(TC) == 4)
+    return f2d_pow2(v, sh);
+  else
+    return sh ? ldexp(v, sh) : v;
 }
 
 // RB: the operands are rounded to bfloat16 before the (FP32) multiply-add.
@@ -64,9 +116,9 @@ __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(_
 template <typename TC, bool RB>
 __device__ __forceinline__ TC stage_val(double v) {
   if constexpr (RB)
-    return (TC)round_bf16((float)v);
+    return (TC)round_bf16(d2f_pow2(v, 0));
   else
-    return (TC)v;
+    return ld_tc<TC>(v);
 }
 
 // One warp per GEMM with m, n <= 32 (any k), four warps per CTA.  The operands
@@ -118,11 +170,13 @@ __global__ void __launch_bounds__(128) k_gemm_small(const GemmDesc* __restrict__
   }
   if (lane < n) {
     double* o = D.C + (long)lane * D.ldc;
+    const TC al = ld_tc<TC>(D.alpha);
+    const int bm = D.beta == 0.0 ? 0 : (D.beta == 1.0 ? 1 : 2);
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       if (i >= m) break;
-      const double v = D.alpha * (double)acc[i];
-      o[i] = (D.beta == 0.0) ? v : v + D.beta * o[i];
+      const double v = st_tc<TC>(al * acc[i]);
+      o[i] = bm == 0 ? v : (bm == 1 ? o[i] + v : v + D.beta * o[i]);
     }
   }
 }
@@ -179,6 +233,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
     }
     __syncthreads();
   }
+  const TC al = ld_tc<TC>(D.alpha);
+  const int bm = D.beta == 0.0 ? 0 : (D.beta == 1.0 ? 1 : 2);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = row0 + ty + 16 * i;
@@ -188,8 +244,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
       const int c = col0 + tx + 16 * j;
       if (c >= D.n) continue;
       double* o = D.C + r + (long)c * D.ldc;
-      const double v = D.alpha * (double)acc[i][j];
-      *o = (D.beta == 0.0) ? v : v + D.beta * (*o);
+      const double v = st_tc<TC>(al * acc[i][j]);
+      *o = bm == 0 ? v : (bm == 1 ? *o + v : v + D.beta * (*o));
     }
   }
 }
@@ -816,6 +872,10 @@ __device__ __forceinline__ double pow2_scale(double gmax) {
   return ldexp(1.0, -e);
 }
 
+// exponent shift that brings a block whose largest |entry| has biased binary64
+// exponent emax into [0.5, 1) (0 for an all-zero block or one with inf/NaN)
+__device__ __forceinline__ int pow2_shift(int emax) { return (emax <= 0 || emax >= 2047) ? 0 : 1022 - emax; }
+
 __device__ __forceinline__ double warp_max_nan(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -876,13 +936,10 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
   TC* nrm = A + mn;
   TC* ref = nrm + n;
   int* jp = (int*)(ref + n);
-  double gmax = 0.0;
-  for (int e = lane; e < mn; e += 32) {
-    const double a = fabs(D.A[qr_row(D, e % m) + (long)(e / m) * ld]);
-    gmax = (a > gmax || a != a) ? a : gmax;
-  }
-  const double s_in = pow2_scale(warp_max_nan(gmax));
-  for (int e = lane; e < mn; e += 32) A[e] = (TC)(D.A[qr_row(D, e % m) + (long)(e / m) * ld] * s_in);
+  int em = 0;
+  for (int e = lane; e < mn; e += 32) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
+  const int sh = pow2_shift((int)__reduce_max_sync(0xffffffffu, (unsigned)em));
+  for (int e = lane; e < mn; e += 32) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
   __syncwarp();
   if (PIV) {
     for (int j = 0; j < n; ++j) {
@@ -982,11 +1039,10 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
     if (lane == 0) x[0] = alpha;
     __syncwarp();
   }
-  const double s_out = 1.0 / s_in;
   for (int e = lane; e < mn; e += 32) {
     const int i = e % m, j = e / m;
     const TC v = (j < k && i > j) ? (TC)0 : A[e];
-    D.A[qr_row(D, i) + (long)j * ld] = (double)v * s_out;
+    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
   }
   if (PIV) {
     for (int j = lane; j < n; j += 32) D.jpvt[j] = jp[j];
@@ -1021,18 +1077,15 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
   __shared__ double red_g[32];
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
-  double gmax = 0.0;
-  for (int e = tid; e < mn; e += nt_) {
-    const double a = fabs(D.A[qr_row(D, e % m) + (long)(e / m) * ld]);
-    gmax = (a > gmax || a != a) ? a : gmax;
-  }
-  gmax = warp_max_nan(gmax);
-  if (lane == 0) red_g[w] = gmax;
+  int em = 0;
+  for (int e = tid; e < mn; e += nt_) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
+  em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+  if (lane == 0) red_i[w] = em;
   __syncthreads();
-  gmax = 0.0;
-  for (int i = 0; i < nw; ++i) gmax = (red_g[i] > gmax || red_g[i] != red_g[i]) ? red_g[i] : gmax;
-  const double s_in = pow2_scale(gmax);
-  for (int e = tid; e < mn; e += nt_) A[e] = (TC)(D.A[qr_row(D, e % m) + (long)(e / m) * ld] * s_in);
+  em = 0;
+  for (int i = 0; i < nw; ++i) em = max(em, red_i[i]);
+  const int sh = pow2_shift(em);
+  for (int e = tid; e < mn; e += nt_) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
   for (int j = tid; j < n; j += nt_) flag[j] = 0;
   __syncthreads();
   if (PIV) {
@@ -1222,11 +1275,10 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
     if (tid == 0) x[0] = alpha;
   }
   __syncthreads();
-  const double s_out = 1.0 / s_in;
   for (int e = tid; e < mn; e += nt_) {
     const int i = e % m, j = e / m;
     const TC v = (j < k && i > j) ? (TC)0 : A[e];
-    D.A[qr_row(D, i) + (long)j * ld] = (double)v * s_out;
+    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
   }
   if (PIV) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
@@ -1281,34 +1333,28 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   __shared__ TC red_s[32], red_v[32];
   __shared__ int red_i[32];
   __shared__ double red_g[32];
-  __shared__ double xg;
+  __shared__ int xg;
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   // power-of-two scale from the cluster-wide largest magnitude
-  double gmax = 0.0;
-  for (int e = tid; e < ml * n; e += nt_) {
-    const double a = fabs(D.A[(r0 + e % ml) + (long)(e / ml) * ld]);
-    gmax = (a > gmax || a != a) ? a : gmax;
-  }
-  gmax = warp_max_nan(gmax);
-  if (lane == 0) red_g[w] = gmax;
+  int em = 0;
+  for (int e = tid; e < ml * n; e += nt_) em = max(em, dexp(D.A[(r0 + e % ml) + (long)(e / ml) * ld]));
+  em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+  if (lane == 0) red_i[w] = em;
   __syncthreads();
   if (tid == 0) {
-    double g = 0.0;
-    for (int i = 0; i < nw; ++i) g = (red_g[i] > g || red_g[i] != red_g[i]) ? red_g[i] : g;
+    int g = 0;
+    for (int i = 0; i < nw; ++i) g = max(g, red_i[i]);
     xg = g;
   }
   for (int j = tid; j < n; j += nt_) flag[j] = 0;
   cl.sync();
-  gmax = 0.0;
-  for (int r = 0; r < R; ++r) {
-    const double g = *cl.map_shared_rank(&xg, r);
-    gmax = (g > gmax || g != g) ? g : gmax;
-  }
-  const double s_in = pow2_scale(gmax);
+  em = 0;
+  for (int r = 0; r < R; ++r) em = max(em, *cl.map_shared_rank(&xg, r));
+  const int sh = pow2_shift(em);
   for (int e = tid; e < ml * n; e += nt_) {
     const int li = e % ml, j = e / ml;
-    A[li + (size_t)j * mlp] = (TC)(D.A[(r0 + li) + (long)j * ld] * s_in);
+    A[li + (size_t)j * mlp] = ld_tc<TC>(D.A[(r0 + li) + (long)j * ld], sh);
   }
   __syncthreads();
   if (PIV) {
@@ -1483,12 +1529,11 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   }
   // no CTA leaves while another may still read its shared memory
   cl.sync();
-  const double s_out = 1.0 / s_in;
   for (int e = tid; e < ml * n; e += nt_) {
     const int li = e % ml, j = e / ml;
     const int i = r0 + li;
     const TC v = (j < k && i > j) ? (TC)0 : A[li + (size_t)j * mlp];
-    D.A[i + (long)j * ld] = (double)v * s_out;
+    D.A[i + (long)j * ld] = st_tc<TC>(v, -sh);
   }
   if (PIV && rank == 0) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
@@ -1687,14 +1732,18 @@ __global__ void __launch_bounds__(128) k_il_transform(const int* __restrict__ li
   extern __shared__ __align__(16) unsigned char ism[];
   TC* Ms = (TC*)ism;       // ra x rb, ld ra
   TC* t1 = Ms + md * md;   // ka x rb, ld ka
-  for (int x = tid; x < ra * rb; x += nt) Ms[x] = (TC)M[(x % ra) + (long)(x / ra) * ld];
-  __syncthreads();
+  TC* X = t1 + md * md;    // T'_a (ka x ra, ld ka), then T_b (rb x kb, ld rb)
+  for (int x = tid; x < ra * rb; x += nt) Ms[x] = ld_tc<TC>(M[(x % ra) + (long)(x / ra) * ld]);
   if (na >= 0) {
     const double* Tp = t.Tp[a];
+    for (int x = tid; x < ka * ra; x += nt) X[x] = ld_tc<TC>(Tp[x]);
+  }
+  __syncthreads();
+  if (na >= 0) {
     for (int x = tid; x < ka * rb; x += nt) {
       const int i = x % ka, j = x / ka;
       TC acc = 0;
-      for (int l = 0; l < ra; ++l) acc += (TC)Tp[i + (long)l * ka] * Ms[l + j * ra];
+      for (int l = 0; l < ra; ++l) acc += X[i + l * ka] * Ms[l + j * ra];
       t1[x] = acc;
     }
   } else {
@@ -1703,14 +1752,16 @@ __global__ void __launch_bounds__(128) k_il_transform(const int* __restrict__ li
   __syncthreads();
   if (nb >= 0) {
     const double* Tb = t.T[b];
+    for (int x = tid; x < rb * kb; x += nt) X[x] = ld_tc<TC>(Tb[x]);
+    __syncthreads();
     for (int x = tid; x < ka * kb; x += nt) {
       const int i = x % ka, j = x / ka;
       TC acc = 0;
-      for (int l = 0; l < rb; ++l) acc += t1[i + l * ka] * (TC)Tb[l + (long)j * rb];
-      M[i + (long)j * ld] = (double)acc;
+      for (int l = 0; l < rb; ++l) acc += t1[i + l * ka] * X[l + j * rb];
+      M[i + (long)j * ld] = st_tc<TC>(acc);
     }
   } else {
-    for (int x = tid; x < ka * kb; x += nt) M[(x % ka) + (long)(x / ka) * ld] = (double)t1[x];
+    for (int x = tid; x < ka * kb; x += nt) M[(x % ka) + (long)(x / ka) * ld] = st_tc<TC>(t1[x]);
   }
 }
 
@@ -1775,39 +1826,36 @@ __global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps
   int k = D.kin[0];
   k = k < 0 ? 0 : (k > n ? n : k);
   extern __shared__ double smraw[];
-  __shared__ double nrm[1024];
+  __shared__ TC nrm[1024];
+  __shared__ TC rnv[1024];
   __shared__ int ord[1024];
-  __shared__ double s_gmax[32];
+  __shared__ int s_em[32];
   __shared__ int s_rot;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   const bool in_smem = (size_t)n * k * sizeof(TC) <= (size_t)smem_bytes;
   TC* B = in_smem ? (TC*)smraw : (TC*)D.work;
   const long ld = D.ld;
-  double gmax = 0.0;
-  for (long e = threadIdx.x; e < (long)n * k; e += blockDim.x) {
-    const int pos = (int)(e % n), i = (int)(e / n);
-    double v;
-    if (D.jpvt) {
-      v = (i <= pos) ? D.A[i + pos * ld] : 0.0;
-      B[D.jpvt[pos] + (long)i * n] = (TC)v;
-    } else {  // explicit n x k matrix: orthonormal basis of its range
-      v = D.A[pos + (long)i * ld];
-      B[pos + (long)i * n] = (TC)v;
+  // B = P R_k^T (or the explicit matrix), scaled by a power of two 2^sh that
+  // brings its largest entry into [0.5, 1); warps over columns, lanes over rows
+  int em = 0;
+  for (int i = w; i < k; i += nw)
+    for (int pos = lane; pos < n; pos += 32) {
+      const double v = D.jpvt ? ((i <= pos) ? D.A[i + (long)pos * ld] : 0.0) : D.A[pos + (long)i * ld];
+      em = max(em, dexp(v));
     }
-    const double a = fabs(v);
-    gmax = (a > gmax || a != a) ? a : gmax;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, gmax, o);
-    gmax = (ov > gmax || ov != ov) ? ov : gmax;
-  }
-  if (lane == 0) s_gmax[w] = gmax;
+  em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+  if (lane == 0) s_em[w] = em;
   __syncthreads();
-  gmax = 0.0;
-  for (int i = 0; i < nw; ++i) gmax = (s_gmax[i] > gmax || s_gmax[i] != s_gmax[i]) ? s_gmax[i] : gmax;
-  const double gscale = (gmax > 0.0 && gmax < 1e300) ? 1.0 / gmax : 1.0;
-  for (long e = threadIdx.x; e < (long)n * k; e += blockDim.x) B[e] = (TC)((double)B[e] * gscale);
+  em = 0;
+  for (int i = 0; i < nw; ++i) em = max(em, s_em[i]);
+  const int sh = pow2_shift(em);
+  for (int i = w; i < k; i += nw)
+    for (int pos = lane; pos < n; pos += 32) {
+      if (D.jpvt)
+        B[D.jpvt[pos] + (long)i * n] = ld_tc<TC>((i <= pos) ? D.A[i + (long)pos * ld] : 0.0, sh);
+      else
+        B[pos + (long)i * n] = ld_tc<TC>(D.A[pos + (long)i * ld], sh);
+    }
   __syncthreads();
   const TC tol = sizeof(TC) == 8 ? (TC)1e-15 : (TC)4e-7;
   const TC tiny = sizeof(TC) == 8 ? (TC)1e-300 : (TC)1e-36;
@@ -1852,33 +1900,41 @@ __global__ void k_svd_rt(const SvdRtDesc* __restrict__ d, int nd, int max_sweeps
     __syncthreads();
     if (!rotated) break;
   }
+  // column norms (the singular values times 2^sh) in the arithmetic type, the
+  // descending order (NaN last), and the reciprocals once per column
   for (int j = w; j < k; j += nw) {
     const TC* g = B + (long)j * n;
-    double s2 = 0.0;
-    for (int i = lane; i < n; i += 32) s2 += (double)g[i] * (double)g[i];
-    s2 = warp_sum(s2);
-    if (lane == 0) nrm[j] = sqrt(s2);
+    TC s2 = 0;
+    for (int i = lane; i < n; i += 32) s2 += g[i] * g[i];
+    s2 = warp_sum_t<TC>(s2);
+    if (lane == 0) {
+      const TC v = sqrt(s2);
+      nrm[j] = v;
+      rnv[j] = (v > (TC)0) ? (TC)1 / v : (TC)0;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     int rank = 0;
-    const double v = (nrm[j] == nrm[j]) ? nrm[j] : -1.0;
+    const TC v = (nrm[j] == nrm[j]) ? nrm[j] : (TC)-1;
     for (int q = 0; q < k; ++q) {
-      const double u = (nrm[q] == nrm[q]) ? nrm[q] : -1.0;
+      const TC u = (nrm[q] == nrm[q]) ? nrm[q] : (TC)-1;
       rank += (u > v) || (u == v && q < j);
     }
     ord[rank] = j;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = (j < k) ? nrm[ord[j]] / gscale : 0.0;
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    double v = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = (j < k) ? st_tc<TC>(nrm[ord[j]], -sh) : 0.0;
+  for (int j = w; j < n; j += nw) {
+    double* vj = D.V + (long)j * D.ldv;
     if (j < k) {
-      const double s2 = nrm[ord[j]];
-      v = (s2 > 0.0) ? (double)B[i + (long)ord[j] * n] / s2 : 0.0;
+      const int c = ord[j];
+      const TC r = rnv[c];
+      const TC* g = B + (long)c * n;
+      for (int i = lane; i < n; i += 32) vj[i] = st_tc<TC>(g[i] * r);
+    } else {
+      for (int i = lane; i < n; i += 32) vj[i] = 0.0;
     }
-    D.V[i + (long)j * D.ldv] = v;
   }
 }
 

@@ -811,8 +811,8 @@ void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTa
   IFMM_REQUIRE(md >= 1 && md <= 64, IFMM_EINVAL, "IL transform tile out of range");
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    CK(cudaFuncSetAttribute(k_il_transform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
-    CK(cudaFuncSetAttribute(k_il_transform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 4));
+    CK(cudaFuncSetAttribute(k_il_transform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 64 * 64 * 8));
+    CK(cudaFuncSetAttribute(k_il_transform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 64 * 64 * 4));
   });
   const int* d = st.push(list);
   prof_batch_tag() = (long)list.size();
@@ -820,9 +820,9 @@ void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTa
   cudaEvent_t pe = profiler().begin(kk, st.stream);
   const unsigned g = (unsigned)list.size();
   if (prec == P32)
-    k_il_transform<float><<<g, 128, 2 * md * md * sizeof(float), st.stream>>>(d, (int)g, t, md);
+    k_il_transform<float><<<g, 128, 3 * md * md * sizeof(float), st.stream>>>(d, (int)g, t, md);
   else
-    k_il_transform<double><<<g, 128, 2 * md * md * sizeof(double), st.stream>>>(d, (int)g, t, md);
+    k_il_transform<double><<<g, 128, 3 * md * md * sizeof(double), st.stream>>>(d, (int)g, t, md);
   check_launch("k_il_transform");
   profiler().end(kk, st.stream, pe);
 }
@@ -1405,6 +1405,14 @@ void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, dou
 }
 
 // raw launches with device-resident descriptors (solve plans, graph capture)
+__global__ void k_conv_check(const double* x, int n, int sh, float* f, double* back) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = d2f_pow2(x[i], sh);
+  f[i] = v;
+  back[i] = f2d_pow2(v, -sh);
+}
+
 void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n) {
   if (n) k_copy<<<n, 256, 0, s>>>(d, n);
 }
@@ -1419,6 +1427,34 @@ void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t
 
 extern "C" {
 const char* ifmm_last_error(void) { return ifmm::last_error(); }
+
+ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, double* back) {
+  try {
+    IFMM_REQUIRE(x && f && back && n >= 0 && n <= (1 << 26), IFMM_EINVAL, "bad arguments");
+    IFMM_REQUIRE(shift >= -200 && shift <= 200, IFMM_EINVAL, "shift out of range");
+    if (n == 0) return IFMM_OK;
+    double *dx = nullptr, *db = nullptr;
+    float* df = nullptr;
+    CK(cudaMalloc(&dx, sizeof(double) * n));
+    CK(cudaMalloc(&db, sizeof(double) * n));
+    CK(cudaMalloc(&df, sizeof(float) * n));
+    cudaError_t e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      ifmm::k_conv_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, (int)n, shift, df, db);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(f, df, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(back, db, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(db);
+    cudaFree(df);
+    CK(e);
+    return IFMM_OK;
+  } catch (const ifmm::Error& e) {
+    ifmm::set_last_error(e.what());
+    return e.code;
+  }
+}
 
 ifmm_status ifmm_profile(int timing) {
   try {

@@ -63,6 +63,7 @@ _sig = {
     "ifmm_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "ifmm_mlp_train": [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp],
     "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
+    "ifmm_convert_check": [_vp, _i64, ctypes.c_int, _vp, _vp],
 }
 for _name, _args in _sig.items():
     getattr(lib, _name).argtypes = _args
@@ -261,6 +262,17 @@ def ifmm_profile_query() -> dict:
         out[name.value.decode()] = (int(n.value), float(ms.value))
         i += 1
     return out
+
+
+def ifmm_convert_check(x: np.ndarray, shift: int = 0):
+    """(f, back): the FP32 kernels' binary64 -> binary32 conversion of x * 2^shift
+    on the device, and f * 2^-shift widened back (diagnostic)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.empty(x.shape, dtype=np.float32)
+    back = np.empty(x.shape, dtype=np.float64)
+    _check(lib.ifmm_convert_check(x.ctypes.data_as(ctypes.c_void_p), x.size, int(shift),
+                                  f.ctypes.data_as(ctypes.c_void_p), back.ctypes.data_as(ctypes.c_void_p)))
+    return f, back
 
 
 def bem_matvec_noalloc(tree: Tree, x, y, kernel: Kernel | None = None, stream=None) -> None:
