@@ -240,7 +240,9 @@ def main():
         ms = float(t.item())
     fact, its, rel = last
     stats = ifmm.ifmm_fact_stats(fact)
-    launches = sum(n for n, _ in prof.values()) // args.steps
+    # kernels the library launched (every launch is counted as it is issued;
+    # a solve-graph replay counts its kernel nodes)
+    launches = prof.pop("kernels", (0, 0.0))[0] // args.steps
     # dominant kernel of the step and its roofline (ALU-bound dense kernels)
     flops_of = {"svd_fp32": stats["flops_svd"], "svd_fp64": stats["flops_svd"], "qr_fp32": stats["flops_qr"],
                 "qr_fp64": stats["flops_qr"], "gemm_fp32": stats["flops_gemm"], "gemm_fp64": stats["flops_gemm"],
@@ -345,11 +347,13 @@ def run_batch(args, rank, world, dist, ifmm, torch):
     torch.cuda.synchronize()
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
+    ifmm.ifmm_profile(False)  # launch counts only (no per-launch events)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         its, rel = step()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
+    launches = ifmm.ifmm_profile_query().get("kernels", (0, 0.0))[0] // args.steps
     clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([dt], device="cuda")
@@ -362,7 +366,8 @@ def run_batch(args, rank, world, dist, ifmm, torch):
                                   "GMRES(30) to 1e-8, 8 worker streams", "precision": args.precision,
                       "global_batch": 64 * world},
            "problems_per_s": 64 * world / dt, "max_gmres_iterations": max(its), "max_relres": max(rel),
-           "timing": "host wall clock around the batched calls (several streams)", "clocks": clk}
+           "timing": "host wall clock around the batched calls (several streams)", "gpu_launches": int(launches),
+           "clocks": clk}
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0

@@ -65,7 +65,7 @@ static void check_gemm(const std::vector<GemmDesc>& v) {
 static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "gauss_jordan", "qr_fp64", "qr_fp32",
                                            "svd_fp64", "svd_fp32", "gemv", "gemv_sum", "p2p", "interp", "tables",
                                            "matvec", "permute", "gauss_jordan_big", "solve_graph",
-                                           "qr_global_fp64", "qr_global_fp32", "qr_cluster_fp64", "qr_cluster_fp32"};
+                                           "qr_global_fp64", "qr_global_fp32", "qr_cluster_fp64", "qr_cluster_fp32", "kernels"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
 int& prof_level_tag() {
   static thread_local int t = -1;
@@ -140,9 +140,11 @@ void Profiler::reset() {
   }
 }
 
-void check_launch(const char* what) {
+// checks the launches just issued and counts them (profile kind "kernels")
+void check_launch(const char* what, long nkernels) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(IFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  profiler().count(KK_ALL, nkernels);
 }
 
 // Independent launches of one batch on side streams of the caller's stream:
@@ -223,7 +225,7 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
     const CopyDesc* d = st.push(big);
     k_copy<<<(unsigned)big.size(), 256, 0, st.stream>>>(d, (int)big.size());
   }
-  check_launch("k_copy");
+  check_launch("k_copy", (long)!small.empty() + (long)!big.empty());
   profiler().end(KK_COPY, st.stream, pe);
 }
 
@@ -412,7 +414,7 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
       k_gjb_update<<<dim3(gx, nb), 256, 0, st.stream>>>(d, nb, k, work, o);
     }
     k_gjb_colswap<<<nb, 256, 0, st.stream>>>(d, nb, work, o);
-    check_launch("k_gjb");
+    check_launch("k_gjb", 2L * nmax + 1);
     profiler().end(KK_GJ_BIG, st.stream, pe);
   }
 }
@@ -1136,7 +1138,7 @@ int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, con
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  check_launch("autotune_matvec_df");
+  check_launch("autotune_matvec_df", 9);
   return pick;
 }
 
@@ -1343,7 +1345,7 @@ void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, doub
     k_gj_update<<<upd_blocks, 256, 0, s>>>(A, ld, n, k, d_work, d_work + n, d_info);
   }
   k_gj_colswap<<<1, 1024, 0, s>>>(A, ld, n, d_work_int, d_info);
-  check_launch("big_inverse");
+  check_launch("big_inverse", 2L * n + 1);
   profiler().end(KK_GJ_BIG, s, pe);
 }
 

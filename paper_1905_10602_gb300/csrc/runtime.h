@@ -176,7 +176,7 @@ enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 // the launching stream around every launch.
 enum KernelKind {
   KK_COPY = 0, KK_GEMM64, KK_GEMM32, KK_INV, KK_QR64, KK_QR32, KK_SVD64, KK_SVD32, KK_GEMV, KK_GEMV_SUM, KK_P2P,
-  KK_INTERP, KK_TABLES, KK_MATVEC, KK_PERM, KK_GJ_BIG, KK_SOLVE_GRAPH, KK_QRG64, KK_QRG32, KK_QRC64, KK_QRC32, KK_COUNT
+  KK_INTERP, KK_TABLES, KK_MATVEC, KK_PERM, KK_GJ_BIG, KK_SOLVE_GRAPH, KK_QRG64, KK_QRG32, KK_QRC64, KK_QRC32, KK_ALL, KK_COUNT
 };
 struct Profiler {
   bool timing = false;
@@ -208,7 +208,8 @@ void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec);
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec);
 void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v);
 void launch_frob(DescStage& st, const std::vector<FrobDesc>& v);
-void check_launch(const char* what);
+// checks the launches just issued and counts nkernels of them (profile kind "kernels")
+void check_launch(const char* what, long nkernels = 1);
 
 inline CopyDesc cpy(const double* src, int lds, double* dst, int ldd, int rows, int cols, double alpha = 1.0,
                     double beta = 0.0, int trans = 0) {

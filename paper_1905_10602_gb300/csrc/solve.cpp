@@ -266,6 +266,7 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
     cudaEvent_t pe = profiler().begin(KK_SOLVE_GRAPH, s, (long)P.prog.size());
     CK(cudaGraphLaunch(P.graph, s));
     profiler().end(KK_SOLVE_GRAPH, s, pe);
+    profiler().count(KK_ALL, (long)P.prog.size());
   }
   CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
