@@ -1033,6 +1033,40 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   const float e = fmaf(a.h, b.h, -p);
   return df_quick(p, e + (a.h * b.l + a.l * b.h));
 }
+// a - (bh + bl) with a two-sum of the high parts; the low part is left
+// unnormalised (its consumer squares it)
+__device__ __forceinline__ df df_diff(df a, float bh, float bl) {
+  const df s = df_two_sum(a.h, -bh);
+  return {s.h, s.l + (a.l - bl)};
+}
+// d^2 for d = h + l: h^2 exactly as a pair (FMA), plus 2 h l (l^2 is below
+// the pair's precision)
+__device__ __forceinline__ df df_sq(df d) {
+  const float p = d.h * d.h;
+  return {p, fmaf(d.h, d.h, -p) + 2.f * d.h * d.l};
+}
+__device__ __forceinline__ df df_sum3(df a, df b, df c) {
+  const df s = df_two_sum(a.h, b.h);
+  const df u = df_two_sum(s.h, c.h);
+  return df_quick(u.h, u.l + (s.l + (a.l + b.l + c.l)));
+}
+// 1/sqrt(x) as a pair: y0 = rsqrtf(x.h), one Newton step y0 + y0 (1 - x y0^2)/2
+// with the residual formed from the exact products (1 - x y0^2 is ~1e-7, so
+// its rounding is far below the pair's precision)
+__device__ __forceinline__ df df_rsqrt_fast(df x) {
+  const float y0 = rsqrtf(x.h);
+  const float th = y0 * y0;
+  const float tl = fmaf(y0, y0, -th);
+  const float uh = x.h * th;
+  const float ul = fmaf(x.h, th, -uh) + fmaf(x.h, tl, x.l * th);
+  const float e = (1.f - uh) - ul;
+  return {y0, 0.5f * y0 * e};
+}
+// acc + (ph + pl): two-sum of the high parts, low parts added
+__device__ __forceinline__ df df_acc(df acc, float ph, float pl) {
+  const df s = df_two_sum(acc.h, ph);
+  return df_quick(s.h, s.l + (acc.l + pl));
+}
 __device__ __forceinline__ df df_rsqrt(df x) {
   const float y0 = rsqrtf(x.h);
   const df yy = df_mul({y0, 0.f}, {y0, 0.f});
@@ -1087,11 +1121,18 @@ __global__ void __launch_bounds__(BS) k_matvec_df(const float* __restrict__ pts,
     __syncthreads();
     const int cnt = min((int)blockDim.x, n - j0);
     for (int t = 0; t < cnt; ++t) {
-      const df dx = df_sub(px, {s[0][t], s[1][t]});
-      const df dy = df_sub(py, {s[2][t], s[3][t]});
-      const df dz = df_sub(pz, {s[4][t], s[5][t]});
-      const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
-      if (j0 + t != i) acc = df_add(acc, df_mul({s[6][t], s[7][t]}, df_rsqrt(r2)));
+      // d = p_i - p_j per axis: two-sum of the high parts plus the low parts
+      // (not renormalised: it is squared next)
+      const df dx = df_diff(px, s[0][t], s[1][t]);
+      const df dy = df_diff(py, s[2][t], s[3][t]);
+      const df dz = df_diff(pz, s[4][t], s[5][t]);
+      // r^2 = sum d^2: FMA two-product of the high parts, 2 h l for the rest
+      const df r2 = df_sum3(df_sq(dx), df_sq(dy), df_sq(dz));
+      const df w = df_rsqrt_fast(r2);
+      // q_j / r as a pair, added with a two-sum
+      const float ph = s[6][t] * w.h;
+      const float pl = fmaf(s[6][t], w.h, -ph) + fmaf(s[6][t], w.l, s[7][t] * w.h);
+      if (j0 + t != i) acc = df_acc(acc, ph, pl);
     }
     __syncthreads();
   }
