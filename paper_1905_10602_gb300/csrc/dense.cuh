@@ -1813,6 +1813,58 @@ __global__ void __launch_bounds__(256) k_zgather(const ZGatherDesc* __restrict__
   }
 }
 
+// One CTA per (eliminated node, neighbour a): adds the row block of neighbour a
+// of F into its near blocks (ScatterDesc).  The slot of (q, q2) is found by a
+// binary search of q2 in q's sorted neighbour list.
+__global__ void __launch_bounds__(256) k_schur_scatter(const ScatterDesc* __restrict__ d, int nd, ScatterTables t) {
+  const int di = blockIdx.x;
+  if (di >= nd) return;
+  const ScatterDesc D = d[di];
+  const int i = D.i;
+  const int c0 = t.nbr_ptr[i], deg = t.nbr_ptr[i + 1] - c0;
+  const int a = blockIdx.y;
+  if (a >= deg) return;
+  __shared__ int roff[32], dims[32], cl[32];
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int b = 0; b < deg && b < 32; ++b) {
+      const int q = t.nbr[c0 + b];
+      const int dq = t.elim[q] ? t.r[q] : t.n[q];
+      cl[b] = q;
+      roff[b] = off;
+      dims[b] = dq;
+      off += dq;
+    }
+  }
+  __syncthreads();
+  const int q = cl[a], mq = dims[a];
+  if (mq == 0 || t.n[i] == 0) return;
+  const int q0 = t.nbr_ptr[q], q1 = t.nbr_ptr[q + 1];
+  const long ldd = t.n[q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = 0; b < deg; ++b) {
+    const int q2 = cl[b], mq2 = dims[b];
+    if (mq2 == 0) continue;
+    int slot = -1;
+    if (q2 == q) {
+      slot = t.slot_ptr[q];
+    } else {
+      int lo = q0, hi = q1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (t.nbr[mid] < q2) lo = mid + 1; else hi = mid;
+      }
+      if (lo < q1 && t.nbr[lo] == q2) slot = t.slot_ptr[q] + 1 + (lo - q0);
+    }
+    if (slot < 0) continue;  // a far pair: consumed by the recompression
+    const int stg = t.elim[q] + t.elim[q2];
+    double* dst = (stg == 0 ? t.nb0 : (stg == 1 ? t.nb1 : t.nb2))[slot];
+    const double* src = D.F + roff[a] + (long)roff[b] * D.M;
+    for (int j = w; j < mq2; j += nw)
+      for (int x = lane; x < mq; x += 32) dst[x + (long)j * ldd] += src[x + (long)j * D.M];
+  }
+}
+
 // ---------------------------------------------------------------- Jacobi on P R_k^T
 // B (n x k, column-major, ld n) lives in dynamic shared memory when it fits in
 // smem_bytes, else in the descriptor's global work buffer.  Columns are rotated

@@ -147,6 +147,27 @@ struct ZTables {
   int rc, tail;
 };
 
+// Schur-complement scatter of one eliminated node i (Algorithm 1, reading R2 of
+// the oracle): F (M x M, ld M) holds -L Pi^-1 U over i's neighbours in CSR
+// order, each neighbour q owning dim(q) rows and columns (dim = r if q is
+// eliminated, else n); every block (q, q2) with q2 = q or q2 a neighbour of q
+// is added to the current near block of stage elim[q] + elim[q2] (ld n[q]).
+struct ScatterDesc {
+  const double* F;
+  int M, i;
+};
+struct ScatterTables {
+  const int* nbr_ptr;
+  const int* nbr;
+  const int* slot_ptr;
+  const int* n;
+  const int* r;
+  const unsigned char* elim;
+  double* const* nb0;
+  double* const* nb1;
+  double* const* nb2;
+};
+
 // Random sketch matrix (m x s, ld m) of +-1 entries from a counter stream.
 struct SketchDesc {
   double* omega;

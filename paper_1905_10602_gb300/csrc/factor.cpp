@@ -63,6 +63,12 @@ struct Work {
   int* d_il_T = nullptr;
   double** d_M2M = nullptr;
   double** d_L2L = nullptr;
+  // device copies of the near structure (Schur scatter kernel)
+  int* d_nbr_ptr = nullptr;
+  int* d_nbr = nullptr;
+  int* d_slot_ptr = nullptr;
+  int* d_n = nullptr;
+  double** d_nb[3] = {nullptr, nullptr, nullptr};
   int slot(int p, int q) const {
     if (p == q) return slot_ptr[p];
     const int* b = LL->nbr.data() + LL->nbr_ptr[p];
@@ -152,6 +158,8 @@ struct Factorizer {
     std::vector<InvDesc> inv;
     std::vector<int> tl, tlf;
     std::vector<ZGatherDesc> zg;
+    std::vector<ScatterDesc> scat;
+    std::vector<unsigned char> el8;
     std::vector<const double*> tn, tpn;
   } L;
   template <class V>
@@ -668,6 +676,22 @@ struct Factorizer {
         W.nb[2][sl] = levelmem.alloc(sz);
       }
     }
+    {
+      W.d_nbr_ptr = (int*)levelmem.alloc_bytes(sizeof(int) * (nn + 1));
+      W.d_nbr = (int*)levelmem.alloc_bytes(sizeof(int) * std::max<size_t>(1, LL.nbr.size()));
+      W.d_slot_ptr = (int*)levelmem.alloc_bytes(sizeof(int) * (nn + 1));
+      W.d_n = (int*)levelmem.alloc_bytes(sizeof(int) * std::max(1, nn));
+      CK(cudaMemcpyAsync(W.d_nbr_ptr, LL.nbr_ptr.data(), sizeof(int) * (nn + 1), cudaMemcpyHostToDevice, s));
+      if (!LL.nbr.empty())
+        CK(cudaMemcpyAsync(W.d_nbr, LL.nbr.data(), sizeof(int) * LL.nbr.size(), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(W.d_slot_ptr, W.slot_ptr.data(), sizeof(int) * (nn + 1), cudaMemcpyHostToDevice, s));
+      if (nn) CK(cudaMemcpyAsync(W.d_n, W.n.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s));
+      for (int s3 = 0; s3 < 3; ++s3) {
+        W.d_nb[s3] = (double**)levelmem.alloc_bytes(sizeof(double*) * std::max(1, nslots));
+        if (nslots)
+          CK(cudaMemcpyAsync(W.d_nb[s3], W.nb[s3].data(), sizeof(double*) * nslots, cudaMemcpyHostToDevice, s));
+      }
+    }
     W.far.assign(LL.il.size(), nullptr);
     for (int a = 0; a < nn; ++a)
       for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e)
@@ -945,6 +969,12 @@ struct Factorizer {
     // ---- Schur complements of the cliques
     auto& cg = fresh(L.cg);
     auto& sc = fresh(L.sc);
+    auto& scat = fresh(L.scat);
+    int maxdeg = 0;
+    // near-structure state of this color for the scatter kernel (before the
+    // color's own nodes count as eliminated; their neighbours are not in it)
+    auto& el8 = fresh(L.el8);
+    el8.assign(W.elim.begin(), W.elim.end());
     auto& gx = fresh(L.gx);
     auto& gf = fresh(L.gf);
     struct FarFill {
@@ -1015,6 +1045,8 @@ struct Factorizer {
         gx.push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));   // X = L [A11 A12]
         gf.push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));   // F = -X[:, :ni] U
         if (ri) gf.push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
+        scat.push_back(ScatterDesc{Fm, M, i});
+        maxdeg = std::max(maxdeg, q1 - q0);
       }
       for (size_t a = 0; a < nf.nb.size(); ++a) {
         const int q = nf.nb[a];
@@ -1039,8 +1071,7 @@ struct Factorizer {
           const double* src = Fm + roff[a] + (long)roff[b2] * M;
           const int sl = W.mark[q2];
           if (sl >= 0) {
-            const int stg = W.elim[q] + W.elim[q2];
-            sc.push_back(cpy(src, M, W.nb[stg][sl], W.n[q], mq, mq2, 1.0, 1.0));
+            // near pair: added on the device (k_schur_scatter)
           } else {
             const int fx = W.farix(q, q2);
             IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
@@ -1060,6 +1091,11 @@ struct Factorizer {
     launch_gemm(st, gx, gprec);
     launch_gemm(st, gf, gprec);
     launch_copy(st, sc);
+    if (!scat.empty()) {
+      const ScatterTables tt{W.d_nbr_ptr, W.d_nbr, W.d_slot_ptr, W.d_n, st.push(W.r), st.push(el8),
+                             W.d_nb[0], W.d_nb[1], W.d_nb[2]};
+      launch_schur_scatter(st, scat, tt, maxdeg);
+    }
     phase("host_schur", tp);
     // ---- recompression events (snapshots: nothing below reads what phase A changes)
     std::vector<Event> evs;

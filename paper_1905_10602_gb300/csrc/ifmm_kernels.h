@@ -43,6 +43,8 @@ void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, doub
 void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec);
 // recompression weight stacks gathered on the device from the IL tables
 void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTables& t);
+// Schur-complement blocks of the eliminated nodes added into their near blocks
+void launch_schur_scatter(DescStage& st, const std::vector<ScatterDesc>& v, const ScatterTables& t, int maxdeg);
 void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n);
 void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n);
 void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n);

@@ -839,6 +839,17 @@ void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTab
   profiler().end(KK_COPY, st.stream, pe);
 }
 
+void launch_schur_scatter(DescStage& st, const std::vector<ScatterDesc>& v, const ScatterTables& t, int maxdeg) {
+  if (v.empty() || maxdeg <= 0) return;
+  IFMM_REQUIRE(maxdeg <= 32, IFMM_EINVAL, "more than 32 neighbours");
+  const ScatterDesc* d = st.push(v);
+  prof_batch_tag() = (long)v.size();
+  cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
+  k_schur_scatter<<<dim3((unsigned)v.size(), (unsigned)maxdeg), 256, 0, st.stream>>>(d, (int)v.size(), t);
+  check_launch("k_schur_scatter");
+  profiler().end(KK_COPY, st.stream, pe);
+}
+
 void launch_sketch(DescStage& st, const std::vector<SketchDesc>& v) {
   if (v.empty()) return;
   const SketchDesc* d = st.push(v);
