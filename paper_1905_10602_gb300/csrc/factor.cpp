@@ -20,6 +20,8 @@
 // solve needs stay untouched once a stage ends.
 #include <algorithm>
 #include <chrono>
+#include <exception>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -38,6 +40,42 @@ struct Blk {
   int ld, rows, cols, trans;
 };
 
+// host threads for a loop over n independent items (1 below 64 items)
+static int host_threads(int n) {
+  static const int hw = [] {
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(8u, h / 2));
+  }();
+  return n < 64 ? 1 : std::min(hw, n / 32);
+}
+// f(t) for t in [0, nth) on nth threads (t = 0 on the caller); the first
+// exception any of them threw is rethrown after all have finished
+template <class Fn>
+static void parallel_ranges(int nth, Fn&& f) {
+  if (nth <= 1) {
+    f(0);
+    return;
+  }
+  std::vector<std::exception_ptr> ex(nth);
+  std::vector<std::thread> th;
+  for (int t = 1; t < nth; ++t)
+    th.emplace_back([&, t] {
+      try {
+        f(t);
+      } catch (...) {
+        ex[t] = std::current_exception();
+      }
+    });
+  try {
+    f(0);
+  } catch (...) {
+    ex[0] = std::current_exception();
+  }
+  for (auto& x : th) x.join();
+  for (auto& e : ex)
+    if (e) std::rethrow_exception(e);
+}
+
 static inline int64_t key3(int a, int b, int c) { return ((int64_t)a << 40) | ((int64_t)b << 20) | (int64_t)c; }
 
 struct Work {
@@ -54,6 +92,7 @@ struct Work {
   std::vector<int> il_row; // il_row[e] = a for the IL entry e = (a, b)
   std::vector<char> touched;  // per IL entry, cleared after every use
   std::vector<int> mark;      // per node, -1 outside a lookup scope
+  std::vector<std::vector<int>> marks;  // one such array per host thread
   // device copies of the IL structure (phase-B kernel)
   int* d_il_row = nullptr;
   int* d_il = nullptr;
@@ -177,9 +216,12 @@ struct Factorizer {
   // host wall time of a factorization phase, accumulated into a stat
   void phase(const char* name, std::chrono::steady_clock::time_point& t) {
     const auto now = std::chrono::steady_clock::now();
-    F.stat_add(name, std::chrono::duration<double>(now - t).count());
+    const double dt = std::chrono::duration<double>(now - t).count();
+    F.stat_add(name, dt);
+    F.stat_add(std::string(name) + "_L" + std::to_string(cur_level), dt);
     t = now;
   }
+  int cur_level = 0;
   void wait() {
     auto a = std::chrono::steady_clock::now();
     CK(cudaStreamSynchronize(s));
@@ -655,12 +697,18 @@ struct Factorizer {
     W.il_T.assign(LL.il.size(), -1);
     W.touched.assign(LL.il.size(), 0);
     W.mark.assign(nn, -1);
-    for (int a = 0; a < nn; ++a)
-      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
-        W.il_row[e] = a;
-        W.il_T[e] = W.farix(LL.il[e], a);
-        IFMM_REQUIRE(W.il_T[e] >= 0, IFMM_EINVAL, "internal: interaction list not symmetric");
-      }
+    {
+      const int nt = host_threads(nn);
+      parallel_ranges(nt, [&](int t) {
+        const int a0 = (int)((long)nn * t / nt), a1 = (int)((long)nn * (t + 1) / nt);
+        for (int a = a0; a < a1; ++a)
+          for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+            W.il_row[e] = a;
+            W.il_T[e] = W.farix(LL.il[e], a);
+            IFMM_REQUIRE(W.il_T[e] >= 0, IFMM_EINVAL, "internal: interaction list not symmetric");
+          }
+      });
+    }
     // near slots
     W.slot_ptr.assign(nn + 1, 0);
     for (int i = 0; i < nn; ++i) W.slot_ptr[i + 1] = W.slot_ptr[i] + 1 + (LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]);
@@ -693,9 +741,22 @@ struct Factorizer {
       }
     }
     W.far.assign(LL.il.size(), nullptr);
-    for (int a = 0; a < nn; ++a)
-      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e)
-        W.far[e] = levelmem.alloc((size_t)std::max(1, W.capr[a]) * std::max(1, W.capr[LL.il[e]]));
+    {
+      // one allocation for every far block of the level (256-byte granules, as
+      // the arena's own), carved in IL order
+      auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };
+      size_t tot = 0;
+      for (int a = 0; a < nn; ++a)
+        for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e)
+          tot += rup((size_t)std::max(1, W.capr[a]) * std::max(1, W.capr[LL.il[e]]));
+      double* blk = tot ? levelmem.alloc(tot) : nullptr;
+      size_t off = 0;
+      for (int a = 0; a < nn; ++a)
+        for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+          W.far[e] = blk + off;
+          off += rup((size_t)std::max(1, W.capr[a]) * std::max(1, W.capr[LL.il[e]]));
+        }
+    }
     {
       const size_t ne = std::max<size_t>(1, LL.il.size());
       W.d_il_row = (int*)levelmem.alloc_bytes(sizeof(int) * ne);
@@ -853,23 +914,35 @@ struct Factorizer {
         gg.push_back(gmm(m2m_tab + o * rc2, rc, 1, m2m_tab + o * rc2, rc, 0, gm + o * rc2, rc, rc, rc, rc, 1.0, 0.0));
       cnt.add_gemm(gg);
       launch_gemm(st, gg, P64);
-      std::vector<double*> dst;
-      std::vector<const double*> terms;
-      std::vector<int> first{0};
+      std::vector<double*> dst(2 * (size_t)nn);
+      std::vector<int> first(2 * (size_t)nn + 1, 0);
       rz_row.resize(nn);
       rz_col.resize(nn);
+      double* Rall = scratch.alloc(std::max<size_t>(1, 2 * (size_t)nn * ((rc2 + 31) & ~(size_t)31)));
       for (int q = 0; q < nn; ++q)
         for (int side = 0; side < 2; ++side) {
-          double* R = scratch.alloc((size_t)rc2);
+          const size_t x = 2 * (size_t)q + side;
+          double* R = Rall + x * ((rc2 + 31) & ~(size_t)31);
           (side == 0 ? rz_row : rz_col)[q] = R;
-          dst.push_back(R);
-          for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
-            const int l = LL.il[e];
-            terms.push_back(side == 0 ? gk + off_index(l, q) * rc2 : gk + (343 + off_index(q, l)) * rc2);
-          }
-          if (kappa > 2) terms.push_back(gm + octant(q) * rc2);
-          first.push_back((int)terms.size());
+          dst[x] = R;
+          first[x + 1] = first[x] + (LL.il_ptr[q + 1] - LL.il_ptr[q]) + (kappa > 2 ? 1 : 0);
         }
+      std::vector<const double*> terms((size_t)first.back());
+      {
+        const int nt = host_threads(nn);
+        parallel_ranges(nt, [&](int t) {
+          const int a0 = (int)((long)nn * t / nt), a1 = (int)((long)nn * (t + 1) / nt);
+          for (int q = a0; q < a1; ++q)
+            for (int side = 0; side < 2; ++side) {
+              size_t y = (size_t)first[2 * (size_t)q + side];
+              for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+                const int l = LL.il[e];
+                terms[y++] = side == 0 ? gk + off_index(l, q) * rc2 : gk + (343 + off_index(q, l)) * rc2;
+              }
+              if (kappa > 2) terms[y++] = gm + octant(q) * rc2;
+            }
+        });
+      }
       launch_gram_sum(st, dst, terms, first, rc);
       launch_chol(st, dst, rc, 1e-13);
     }
@@ -1001,87 +1074,141 @@ struct Factorizer {
       }
       return slot_of[q];
     };
-    for (int g = 0; g < ng; ++g) {
-      const int i = grp[g];
-      cur_i = i;
-      const int ni = W.n[i], ri = W.r[i], m = ni + ri;
-      const int q0 = LL.nbr_ptr[i], q1 = LL.nbr_ptr[i + 1];
-      NodeFactor& nf = LF.nf[i];
-      nf.piinv = Pi[g];
-      nf.n = ni;
-      nf.r = ri;
+    // The per-node work runs on host threads over contiguous node ranges.  What
+    // each node produces (descriptors, far pairs) is merged afterwards in node
+    // order, so launches, re-base order and results are those of a serial loop.
+    struct FarRec {
+      int q, q2;
+      const double* src;
+      int M, mq, mq2, fx;
+    };
+    // scratch of every node (L, U, X, F, Yr), one allocation in node order
+    std::vector<double*> nbase(ng, nullptr);
+    {
+      auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };  // the arena's 256-byte granules
+      std::vector<size_t> offs(ng, 0);
+      size_t tot = 0;
+      for (int g = 0; g < ng; ++g) {
+        const int i = grp[g];
+        const int ni = W.n[i], ri = W.r[i], m = ni + ri;
+        int M = 0;
+        for (int e = LL.nbr_ptr[i]; e < LL.nbr_ptr[i + 1]; ++e) M += W.dim(LL.nbr[e]);
+        offs[g] = tot;
+        if (M && m)
+          tot += rup((size_t)M * std::max(1, ni)) + rup((size_t)std::max(1, ni) * M) + rup((size_t)M * m) +
+                 rup((size_t)M * M) + rup((size_t)std::max(1, ri) * M);
+      }
+      double* blk = tot ? scratch.alloc(tot) : nullptr;
+      for (int g = 0; g < ng; ++g) nbase[g] = blk ? blk + offs[g] : nullptr;
+    }
+    const int nth = host_threads(ng);
+    if ((int)W.marks.size() < nth) W.marks.resize(nth);
+    for (int t = 0; t < nth; ++t)
+      if ((int)W.marks[t].size() != W.nn) W.marks[t].assign(W.nn, -1);
+    std::vector<std::vector<CopyDesc>> cg_t(nth), sc_t(nth);
+    std::vector<std::vector<GemmDesc>> gx_t(nth), gf_t(nth);
+    std::vector<std::vector<ScatterDesc>> scat_t(nth);
+    std::vector<std::vector<FarRec>> far_g(ng);
+    std::vector<int> maxdeg_t(nth, 0);
+    parallel_ranges(nth, [&](int t) {
+      std::vector<int>& mark = W.marks[t];
+      auto& cgv = cg_t[t];
+      auto& scv = sc_t[t];
+      const int g0 = (int)((long)ng * t / nth), g1 = (int)((long)ng * (t + 1) / nth);
       std::vector<int> roff, dims;
-      int M = 0;
-      for (int e = q0; e < q1; ++e) {
-        const int q = LL.nbr[e];
-        roff.push_back(M);
-        dims.push_back(W.dim(q));
-        M += W.dim(q);
-        nf.nb.push_back(q);
-        nf.was_elim.push_back(W.elim[q]);
-        const int sq = W.slot(q, i), si = W.slot(i, q);
-        nf.lcol.push_back(W.nb[W.elim[q]][sq]);
-        nf.lcol_ld.push_back(W.n[q]);
-        nf.lcol_rows.push_back(W.dim(q));
-        nf.urow.push_back(W.nb[W.elim[q]][si]);
-        nf.urow_cols.push_back(W.dim(q));
-      }
-      // -A22 -> self block of R_i x y_i
-      if (ri) sc.push_back(cpy(Pi[g] + ni + (long)ni * m, m, W.nb[2][W.slot(i, i)], ni, ri, ri, -1.0, 0.0));
-      if (M == 0 || m == 0) continue;
-      double* L = scratch.alloc((size_t)M * std::max(1, ni));
-      double* U = scratch.alloc((size_t)std::max(1, ni) * M);
-      double* X = scratch.alloc((size_t)M * m);
-      double* Fm = scratch.alloc((size_t)M * M);
-      double* Yr = scratch.alloc((size_t)std::max(1, ri) * M);
-      for (size_t a = 0; a < nf.nb.size(); ++a) {
-        const int q = nf.nb[a];
-        if (ni && dims[a]) {
-          cg.push_back(cpy(nf.lcol[a], W.n[q], L + roff[a], M, dims[a], ni));
-          cg.push_back(cpy(nf.urow[a], ni, U + (long)roff[a] * ni, ni, ni, dims[a]));
+      for (int g = g0; g < g1; ++g) {
+        const int i = grp[g];
+        const int ni = W.n[i], ri = W.r[i], m = ni + ri;
+        const int q0 = LL.nbr_ptr[i], q1 = LL.nbr_ptr[i + 1];
+        NodeFactor& nf = LF.nf[i];
+        nf.piinv = Pi[g];
+        nf.n = ni;
+        nf.r = ri;
+        roff.clear();
+        dims.clear();
+        int M = 0;
+        for (int e = q0; e < q1; ++e) {
+          const int q = LL.nbr[e];
+          roff.push_back(M);
+          dims.push_back(W.dim(q));
+          M += W.dim(q);
+          nf.nb.push_back(q);
+          nf.was_elim.push_back(W.elim[q]);
+          const int sq = W.slot(q, i), si = W.slot(i, q);
+          nf.lcol.push_back(W.nb[W.elim[q]][sq]);
+          nf.lcol_ld.push_back(W.n[q]);
+          nf.lcol_rows.push_back(W.dim(q));
+          nf.urow.push_back(W.nb[W.elim[q]][si]);
+          nf.urow_cols.push_back(W.dim(q));
         }
-      }
-      if (ni) {
-        gx.push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));   // X = L [A11 A12]
-        gf.push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));   // F = -X[:, :ni] U
-        if (ri) gf.push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
-        scat.push_back(ScatterDesc{Fm, M, i});
-        maxdeg = std::max(maxdeg, q1 - q0);
-      }
-      for (size_t a = 0; a < nf.nb.size(); ++a) {
-        const int q = nf.nb[a];
-        const int mq = dims[a];
-        // O(1) slot lookups of q's near blocks in the pair loop below
-        W.mark[q] = W.slot_ptr[q];
-        for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) W.mark[LL.nbr[e]] = W.slot_ptr[q] + 1 + (e - LL.nbr_ptr[q]);
-        // row-var(q) x y_i  <- L A12
-        if (mq && ri && ni)
-          sc.push_back(cpy(X + roff[a] + (long)ni * M, M, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
-        else if (mq && ri)
-          sc.push_back(cpy(nullptr, 0, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
-        // R_i x col-var(q)  <- A21 U
-        if (mq && ri && ni)
-          sc.push_back(cpy(Yr + (long)roff[a] * ri, ri, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
-        else if (mq && ri)
-          sc.push_back(cpy(nullptr, 0, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
-        for (size_t b2 = 0; b2 < nf.nb.size(); ++b2) {
-          const int q2 = nf.nb[b2];
-          const int mq2 = dims[b2];
-          if (!mq || !mq2 || !ni) continue;
-          const double* src = Fm + roff[a] + (long)roff[b2] * M;
-          const int sl = W.mark[q2];
-          if (sl >= 0) {
-            // near pair: added on the device (k_schur_scatter)
-          } else {
-            const int fx = W.farix(q, q2);
-            IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
-            fills.push_back(FarFill{q, q2, src, M, mq, mq2, fx});
-            if (!W.elim[q]) colfill_v[rebase_slot(q)].push_back(Blk{src, M, mq2, W.n[q], 1});
-            if (!W.elim[q2]) rowfill_v[rebase_slot(q2)].push_back(Blk{src, M, mq, W.n[q2], 0});
+        // -A22 -> self block of R_i x y_i
+        if (ri) scv.push_back(cpy(Pi[g] + ni + (long)ni * m, m, W.nb[2][W.slot(i, i)], ni, ri, ri, -1.0, 0.0));
+        if (M == 0 || m == 0) continue;
+        auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };
+        double* L = nbase[g];
+        double* U = L + rup((size_t)M * std::max(1, ni));
+        double* X = U + rup((size_t)std::max(1, ni) * M);
+        double* Fm = X + rup((size_t)M * m);
+        double* Yr = Fm + rup((size_t)M * M);
+        for (size_t a = 0; a < nf.nb.size(); ++a) {
+          const int q = nf.nb[a];
+          if (ni && dims[a]) {
+            cgv.push_back(cpy(nf.lcol[a], W.n[q], L + roff[a], M, dims[a], ni));
+            cgv.push_back(cpy(nf.urow[a], ni, U + (long)roff[a] * ni, ni, ni, dims[a]));
           }
         }
-        W.mark[q] = -1;
-        for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) W.mark[LL.nbr[e]] = -1;
+        if (ni) {
+          gx_t[t].push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));  // X = L [A11 A12]
+          gf_t[t].push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));  // F = -X[:, :ni] U
+          if (ri) gf_t[t].push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
+          scat_t[t].push_back(ScatterDesc{Fm, M, i});
+          maxdeg_t[t] = std::max(maxdeg_t[t], q1 - q0);
+        }
+        for (size_t a = 0; a < nf.nb.size(); ++a) {
+          const int q = nf.nb[a];
+          const int mq = dims[a];
+          // O(1) slot lookups of q's near blocks in the pair loop below
+          mark[q] = W.slot_ptr[q];
+          for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) mark[LL.nbr[e]] = W.slot_ptr[q] + 1 + (e - LL.nbr_ptr[q]);
+          // row-var(q) x y_i  <- L A12
+          if (mq && ri && ni)
+            scv.push_back(cpy(X + roff[a] + (long)ni * M, M, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
+          else if (mq && ri)
+            scv.push_back(cpy(nullptr, 0, W.nb[W.elim[q] + 1][W.slot(q, i)], W.n[q], mq, ri));
+          // R_i x col-var(q)  <- A21 U
+          if (mq && ri && ni)
+            scv.push_back(cpy(Yr + (long)roff[a] * ri, ri, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
+          else if (mq && ri)
+            scv.push_back(cpy(nullptr, 0, W.nb[1 + W.elim[q]][W.slot(i, q)], ni, ri, mq));
+          for (size_t b2 = 0; b2 < nf.nb.size(); ++b2) {
+            const int q2 = nf.nb[b2];
+            const int mq2 = dims[b2];
+            if (!mq || !mq2 || !ni) continue;
+            if (mark[q2] >= 0) continue;  // near pair: added on the device (k_schur_scatter)
+            const int fx = W.farix(q, q2);
+            IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
+            far_g[g].push_back(FarRec{q, q2, Fm + roff[a] + (long)roff[b2] * M, M, mq, mq2, fx});
+          }
+          mark[q] = -1;
+          for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) mark[LL.nbr[e]] = -1;
+        }
+      }
+    });
+    for (int t = 0; t < nth; ++t) {
+      cg.insert(cg.end(), cg_t[t].begin(), cg_t[t].end());
+      sc.insert(sc.end(), sc_t[t].begin(), sc_t[t].end());
+      gx.insert(gx.end(), gx_t[t].begin(), gx_t[t].end());
+      gf.insert(gf.end(), gf_t[t].begin(), gf_t[t].end());
+      scat.insert(scat.end(), scat_t[t].begin(), scat_t[t].end());
+      maxdeg = std::max(maxdeg, maxdeg_t[t]);
+    }
+    // far pairs in node order: the fill-in lists and the re-base order
+    for (int g = 0; g < ng; ++g) {
+      cur_i = grp[g];
+      for (const FarRec& f : far_g[g]) {
+        fills.push_back(FarFill{f.q, f.q2, f.src, f.M, f.mq, f.mq2, f.fx});
+        if (!W.elim[f.q]) colfill_v[rebase_slot(f.q)].push_back(Blk{f.src, f.M, f.mq2, W.n[f.q], 1});
+        if (!W.elim[f.q2]) rowfill_v[rebase_slot(f.q2)].push_back(Blk{f.src, f.M, f.mq, W.n[f.q2], 0});
       }
     }
     for (int g = 0; g < ng; ++g) W.elim[grp[g]] = 1;
@@ -1144,16 +1271,8 @@ struct Factorizer {
     auto& b2 = fresh(L.b2);
     auto& bc1 = fresh(L.bc1);
     auto& bc2 = fresh(L.bc2);
-    auto& tl = fresh(L.tl);  // IL entries with an endpoint re-based in this color
     for (auto& ev : evs) {
       const int q = ev.q;
-      for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
-        for (const int x : {e, W.il_T[e]})
-          if (!W.touched[x]) {
-            W.touched[x] = 1;
-            tl.push_back(x);
-          }
-      }
       if (W.kappa > 2 && ev.k && ev.r_old) {
         double* t1 = scratch.alloc((size_t)rc * ev.k);
         double* t2 = scratch.alloc((size_t)rc * ev.k);
@@ -1163,37 +1282,70 @@ struct Factorizer {
         bc1.push_back(cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc));
       }
     }
-    // entries whose ranks all fit the fused kernel's tiles go to one launch;
-    // the rest (a rank above 64) keep per-block GEMM descriptors
+    // IL entries with an endpoint re-based in this color, each once: an event of
+    // node q takes its row entries (q, l), and the transposes (l, q) whose other
+    // end l is not re-based (else l's event takes them).  Entries whose ranks
+    // all fit the fused kernel's tiles go to one launch; the rest (a rank above
+    // 64) keep per-block GEMM descriptors.  The events are split over host
+    // threads; the lists are joined in event order.
+    const int nev = (int)evs.size();
+    const int nthb = host_threads(nev);
+    std::vector<std::vector<int>> fast_t(nthb), slow_t(nthb);
+    std::vector<int> md_t(nthb, 1);
+    std::vector<double> fl_t(nthb, 0.0);
+    parallel_ranges(nthb, [&](int t) {
+      const int e0 = (int)((long)nev * t / nthb), e1 = (int)((long)nev * (t + 1) / nthb);
+      auto take = [&](int e) {
+        const int a = W.il_row[e];
+        const int b = LL.il[e];
+        const int ra = r_before[a], rb = r_before[b];
+        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
+        if (!ka || !kb) return;
+        const int mx = std::max(std::max(ra, rb), std::max(ka, kb));
+        if (mx <= 64) {
+          fast_t[t].push_back(e);
+          md_t[t] = std::max(md_t[t], mx);
+          if (ra && rb)
+            fl_t[t] += 2.0 * ((newk[a] >= 0 ? (double)ka * rb * ra : 0.0) + (newk[b] >= 0 ? (double)ka * kb * rb : 0.0));
+        } else {
+          slow_t[t].push_back(e);
+        }
+      };
+      for (int x = e0; x < e1; ++x) {
+        const int q = evs[x].q;
+        for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) {
+          take(e);
+          if (newk[LL.il[e]] < 0) take(W.il_T[e]);
+        }
+      }
+    });
     auto& fast = fresh(L.tlf);
     int md = 1;
-    for (const int e : tl) {
-      W.touched[e] = 0;
-      const int a = W.il_row[e];
-      const int b = LL.il[e];
-      const int ra = r_before[a], rb = r_before[b];
-      const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
-      if (!ka || !kb) continue;
-      const int mx = std::max(std::max(ra, rb), std::max(ka, kb));
-      if (mx <= 64) {
-        fast.push_back(e);
-        md = std::max(md, mx);
-        continue;
-      }
-      double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
-      if (!ra || !rb) {
-        bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
-        continue;
-      }
-      if (newk[a] >= 0)
-        b1.push_back(gmm(evof[a]->Tp, ka, 0, W.far[e], W.capr[a], 0, t1, ka, ka, rb, ra, 1.0, 0.0));
-      else
-        bc1.push_back(cpy(W.far[e], W.capr[a], t1, ka, ka, rb));
-      if (newk[b] >= 0)
-        b2.push_back(gmm(t1, ka, 0, evof[b]->T, rb, 0, W.far[e], W.capr[a], ka, kb, rb, 1.0, 0.0));
-      else
-        bc2.push_back(cpy(t1, ka, W.far[e], W.capr[a], ka, kb));
+    for (int t = 0; t < nthb; ++t) {
+      fast.insert(fast.end(), fast_t[t].begin(), fast_t[t].end());
+      md = std::max(md, md_t[t]);
+      cnt.gemm += fl_t[t];
     }
+    for (int t = 0; t < nthb; ++t)
+      for (const int e : slow_t[t]) {
+        const int a = W.il_row[e];
+        const int b = LL.il[e];
+        const int ra = r_before[a], rb = r_before[b];
+        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
+        double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
+        if (!ra || !rb) {
+          bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
+          continue;
+        }
+        if (newk[a] >= 0)
+          b1.push_back(gmm(evof[a]->Tp, ka, 0, W.far[e], W.capr[a], 0, t1, ka, ka, rb, ra, 1.0, 0.0));
+        else
+          bc1.push_back(cpy(W.far[e], W.capr[a], t1, ka, ka, rb));
+        if (newk[b] >= 0)
+          b2.push_back(gmm(t1, ka, 0, evof[b]->T, rb, 0, W.far[e], W.capr[a], ka, kb, rb, 1.0, 0.0));
+        else
+          bc2.push_back(cpy(t1, ka, W.far[e], W.capr[a], ka, kb));
+      }
     cnt.add_gemm(b1);
     cnt.add_gemm(b2);
     launch_gemm(st, b1, prec);
@@ -1208,12 +1360,6 @@ struct Factorizer {
       for (auto& ev : evs) {
         tn[ev.q] = ev.T;
         tpn[ev.q] = ev.Tp;
-      }
-      for (const int e : fast) {
-        const int a = W.il_row[e], b = LL.il[e];
-        const int ra = r_before[a], rb = r_before[b];
-        const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
-        if (ra && rb) cnt.gemm += 2.0 * ((newk[a] >= 0 ? (double)ka * rb * ra : 0.0) + (newk[b] >= 0 ? (double)ka * kb * rb : 0.0));
       }
       IlTables t{W.d_il_row, W.d_il, W.d_far, W.d_capr, st.push(r_before), st.push(newk), st.push(tn), st.push(tpn)};
       launch_il_transform(st, fast, t, md, prec);
@@ -1302,6 +1448,7 @@ struct Factorizer {
       DeviceArena child_mem;
       child_mem.swap(levelmem);
       prof_level_tag() = kappa;
+      cur_level = kappa;
       auto ti = std::chrono::steady_clock::now();
       init_level(*W, kappa, prev.get());
       phase("host_init", ti);
