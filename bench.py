@@ -2,7 +2,7 @@
 """Benchmark: IFMM factorization + preconditioned GMRES solve on one GB300.
 
 One step = ifmm_factor (operator initialisation, leaf-to-root elimination with
-colors, recompression, top-level LU) followed by bem_gmres (GMRES(30) to a true
+colors, recompression, top-level explicit inverse) followed by bem_gmres (GMRES(30) to a true
 relative residual of 1e-8, right-preconditioned by the IFMM solve, direct-sum
 matvec), on the 131,072-point bumpy-sphere workload (depth 6, Chebyshev order 4,
 eps = 1e-6, sigma = 3).  The tree and coloring (host, built once) and the points
@@ -37,6 +37,18 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32: 128 lanes x 2 flop per clock; FP64: 2 DFMA x 2 flop per clock per SM.
 ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64": 152 * 2 * 2 * 2.070e9 / 1e12}
 METRIC = "IFMM factor+solve s at N=131k, eps=1e-6: mixed/learned vs plain FP64, same GB300"
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest per-rank value (each rank times its own replica; the job takes
+    as long as the slowest).  dist None: a single process."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def parse():
@@ -234,10 +246,7 @@ def main():
     ifmm.ifmm_profile(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     fact, its, rel = last
     stats = ifmm.ifmm_fact_stats(fact)
     # kernels the library launched (every launch is counted as it is issued;
@@ -355,10 +364,7 @@ def run_batch(args, rank, world, dist, ifmm, torch):
     dt = (time.perf_counter() - t0) / args.steps
     launches = ifmm.ifmm_profile_query().get("kernels", (0, 0.0))[0] // args.steps
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dt, dist, "cuda")
     out = {"metric": METRIC + " (64-problem batch)", "value": dt, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
