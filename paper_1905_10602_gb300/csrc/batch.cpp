@@ -43,6 +43,7 @@ ifmm_status run_workers(int nprob, int nworkers, F&& body) {
     for (int w = 0; w < nw; ++w)
       th.emplace_back([&, w] {
         cudaSetDevice(dev);
+        if (nw > 1) ifmm::host_thread_cap() = 1;  // the workers already share the host
         for (;;) {
           const int i = next.fetch_add(1);
           if (i >= nprob) break;

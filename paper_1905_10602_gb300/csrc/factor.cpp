@@ -46,7 +46,9 @@ static int host_threads(int n) {
     const unsigned h = std::thread::hardware_concurrency();
     return (int)std::max(1u, std::min(8u, h / 2));
   }();
-  return n < 64 ? 1 : std::min(hw, n / 32);
+  const int cap = host_thread_cap();
+  const int lim = cap > 0 ? std::min(hw, cap) : hw;
+  return n < 64 ? 1 : std::min(lim, n / 32);
 }
 // f(t) for t in [0, nth) on nth threads (t = 0 on the caller); the first
 // exception any of them threw is rethrown after all have finished

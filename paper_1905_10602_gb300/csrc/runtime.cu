@@ -67,6 +67,10 @@ static const char* kKindNames[KK_COUNT] = {"copy", "gemm_fp64", "gemm_fp32", "ga
                                            "matvec", "permute", "gauss_jordan_big", "solve_graph",
                                            "qr_global_fp64", "qr_global_fp32", "qr_cluster_fp64", "qr_cluster_fp32", "kernels"};
 const char* kernel_kind_name(int k) { return (k >= 0 && k < KK_COUNT) ? kKindNames[k] : nullptr; }
+int& host_thread_cap() {
+  static thread_local int c = 0;
+  return c;
+}
 int& prof_level_tag() {
   static thread_local int t = -1;
   return t;

@@ -193,6 +193,9 @@ struct Profiler {
   void reset();
 };
 Profiler& profiler();
+// per-thread cap on the host threads a factorization may use for its own
+// loops (0: as many as useful; batch workers set 1, as they already share the host)
+int& host_thread_cap();
 // per-thread tags of the per-launch log: level being factored, batch size
 int& prof_level_tag();
 long& prof_batch_tag();
