@@ -583,132 +583,11 @@ __global__ void k_qr(const QrDesc* __restrict__ d, int nd) {
   }
 }
 
-// ---------------------------------------------------------------- one-sided Jacobi SVD
-// Hestenes' method: rotate column pairs of G until all pairs are orthogonal to
-// working precision, accumulating the rotations in V.  Pairs are taken in the
-// round-robin order (n' = n rounded up to even; in round r, position p > 0 holds
-// column 1 + ((p - 1 - r) mod (n'-1)); pair i joins positions i and n'-1-i), so
-// the n'/2 pairs of a round are disjoint and handled by different warps.
-// Dynamic shared memory: n doubles (column norms) + n ints (order).
-template <typename TC>
-__global__ void k_svd(const SvdDesc* __restrict__ d, int nd, int max_sweeps) {
-  if ((int)blockIdx.x >= nd) return;
-  const SvdDesc D = d[blockIdx.x];
-  const int m = D.m, n = D.n;
-  const long ldg = D.ldg;
-  double* G = D.G;
-  double* W = D.Vw;
-  extern __shared__ double sm[];
-  double* nrm = sm;
-  int* ord = (int*)(sm + n);
-  __shared__ int s_rot;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) W[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
-  // scale G to max |G_ij| = 1 so that sums of squares neither overflow nor
-  // underflow in the arithmetic type; singular values are scaled back at the end
-  __shared__ double s_gmax[32];
-  double gmax = 0.0;
-  for (long e = threadIdx.x; e < (long)m * n; e += blockDim.x) {
-    const double v = fabs(G[(e % m) + (e / m) * ldg]);
-    gmax = (v > gmax || v != v) ? v : gmax;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, gmax, o);
-    gmax = (ov > gmax || ov != ov) ? ov : gmax;
-  }
-  if (lane == 0) s_gmax[w] = gmax;
-  __syncthreads();
-  gmax = 0.0;
-  for (int i = 0; i < nw; ++i) gmax = (s_gmax[i] > gmax || s_gmax[i] != s_gmax[i]) ? s_gmax[i] : gmax;
-  const double gscale = (gmax > 0.0 && gmax < 1e300) ? 1.0 / gmax : 1.0;
-  for (long e = threadIdx.x; e < (long)m * n; e += blockDim.x) G[(e % m) + (e / m) * ldg] *= gscale;
-  const int np = n + (n & 1);
-  int sweep = 0;
-  const TC tol = sizeof(TC) == 8 ? (TC)1e-15 : (TC)4e-7;
-  __syncthreads();
-  for (; sweep < max_sweeps && n > 1; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < np - 1; ++r) {
-      for (int pi = w; pi < np / 2; pi += nw) {
-        const int pa = pi, pb = np - 1 - pi;
-        int a = (pa == 0) ? 0 : 1 + ((pa - 1 - r) % (np - 1) + (np - 1)) % (np - 1);
-        int b = (pb == 0) ? 0 : 1 + ((pb - 1 - r) % (np - 1) + (np - 1)) % (np - 1);
-        if (a >= n || b >= n) continue;
-        if (a > b) { const int t = a; a = b; b = t; }
-        double* ga = G + (long)a * ldg;
-        double* gb = G + (long)b * ldg;
-        TC al = 0, be = 0, ga_b = 0;
-        for (int i = lane; i < m; i += 32) {
-          const TC u = (TC)ga[i], v = (TC)gb[i];
-          al += u * u;
-          be += v * v;
-          ga_b += u * v;
-        }
-        al = warp_sum_t<TC>(al);
-        be = warp_sum_t<TC>(be);
-        ga_b = warp_sum_t<TC>(ga_b);
-        const TC tiny = sizeof(TC) == 8 ? (TC)1e-300 : (TC)1e-36;
-        if (al < tiny || be < tiny) continue;
-        if (fabs(ga_b) <= tol * sqrt(al) * sqrt(be)) continue;
-        const TC zeta = (be - al) / ((TC)2 * ga_b);
-        const TC t = (zeta >= (TC)0 ? (TC)1 : (TC)-1) / (fabs(zeta) + hypot((TC)1, zeta));
-        const TC c = (TC)1 / sqrt((TC)1 + t * t), s = c * t;
-        for (int i = lane; i < m; i += 32) {
-          const TC u = (TC)ga[i], v = (TC)gb[i];
-          ga[i] = (double)(c * u - s * v);
-          gb[i] = (double)(s * u + c * v);
-        }
-        double* wa = W + (long)a * n;
-        double* wb = W + (long)b * n;
-        for (int i = lane; i < n; i += 32) {
-          const TC u = (TC)wa[i], v = (TC)wb[i];
-          wa[i] = (double)(c * u - s * v);
-          wb[i] = (double)(s * u + c * v);
-        }
-        if (lane == 0) s_rot = 1;
-      }
-      __syncthreads();
-    }
-    // every thread reads the flag before thread 0 may clear it for the next sweep
-    const int rotated = s_rot;
-    __syncthreads();
-    if (!rotated) break;
-  }
-  // column norms = singular values; order descending (ties: lower index first)
-  for (int j = w; j < n; j += nw) {
-    const double* g = G + (long)j * ldg;
-    double s = 0.0;
-    for (int i = lane; i < m; i += 32) s += g[i] * g[i];
-    s = warp_sum(s);
-    if (lane == 0) nrm[j] = sqrt(s);
-  }
-  __syncthreads();
-  // descending order, ties by index; a NaN norm sorts last (key -1), so the
-  // ranks are a permutation of 0..n-1 whatever the data
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    int rank = 0;
-    const double v = (nrm[j] == nrm[j]) ? nrm[j] : -1.0;
-    for (int k = 0; k < n; ++k) {
-      const double u = (nrm[k] == nrm[k]) ? nrm[k] : -1.0;
-      rank += (u > v) || (u == v && k < j);
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) D.sig[j] = nrm[ord[j]] / gscale;
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    D.V[i + (long)j * D.ldv] = W[i + (long)ord[j] * n];
-  }
-  if (threadIdx.x == 0 && D.sweeps) D.sweeps[0] = sweep;
-}
-
-// ---------------------------------------------------------------- pivoted QR (truncated)
-// One CTA per matrix.  Column norms live in shared memory and are downdated
-// after each step (recomputed when cancellation has eaten two digits).
-// Dynamic shared memory: 2n doubles + n ints.
+// ---------------------------------------------------------------- pivoted QR (truncated), global memory
+// One CTA per matrix, the block in global memory (the fallback for blocks that
+// fit neither one CTA's nor a cluster's shared memory).  Column norms live in
+// shared memory and are downdated after each step (recomputed when
+// cancellation has eaten two digits).  Dynamic shared memory: 2n doubles + n ints.
 template <typename TC>
 __global__ void k_qrcp(const QrcpDesc* __restrict__ d, int nd) {
   if ((int)blockIdx.x >= nd) return;
@@ -864,26 +743,9 @@ __host__ __device__ __forceinline__ size_t qr_slot_bytes(int m, int n, int tc_by
   return (((size_t)m * n + 2 * (size_t)n) * tc_bytes + sizeof(int) * (size_t)n + 15) & ~(size_t)15;
 }
 
-// power of two that maps gmax into [0.5, 1); 1 for zero or non-finite gmax
-__device__ __forceinline__ double pow2_scale(double gmax) {
-  if (!(gmax > 0.0) || !(gmax < 1e300)) return 1.0;
-  int e;
-  frexp(gmax, &e);
-  return ldexp(1.0, -e);
-}
-
 // exponent shift that brings a block whose largest |entry| has biased binary64
 // exponent emax into [0.5, 1) (0 for an all-zero block or one with inf/NaN)
 __device__ __forceinline__ int pow2_shift(int emax) { return (emax <= 0 || emax >= 2047) ? 0 : 1022 - emax; }
-
-__device__ __forceinline__ double warp_max_nan(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    v = (ov > v || ov != ov) ? ov : v;
-  }
-  return v;
-}
 
 // Applies H = I - tau v v^T (v_0 = 1, v_i = sc x_i) to the cnt <= G columns
 // j0.. of the trailing block (rows k..k+len-1, ld m) with one warp: G independent
@@ -1074,7 +936,6 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
   __shared__ unsigned char flag[1024];
   __shared__ TC red_s[32], red_v[32];
   __shared__ int red_i[32];
-  __shared__ double red_g[32];
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   int em = 0;
@@ -1332,7 +1193,6 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   __shared__ unsigned char flag[1024];
   __shared__ TC red_s[32], red_v[32];
   __shared__ int red_i[32];
-  __shared__ double red_g[32];
   __shared__ int xg;
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
@@ -1866,6 +1726,11 @@ __global__ void __launch_bounds__(256) k_schur_scatter(const ScatterDesc* __rest
 }
 
 // ---------------------------------------------------------------- Jacobi on P R_k^T
+// Hestenes' one-sided Jacobi: rotate column pairs of B until all pairs are
+// orthogonal to working precision.  Pairs are taken in the round-robin order
+// (k' = k rounded up to even; in round r, position p > 0 holds column
+// 1 + ((p - 1 - r) mod (k'-1)); pair i joins positions i and k'-1-i), so the k'/2
+// pairs of a round are disjoint and handled by different warps.
 // B (n x k, column-major, ld n) lives in dynamic shared memory when it fits in
 // smem_bytes, else in the descriptor's global work buffer.  Columns are rotated
 // in place (no rotation matrix is accumulated: the rotated columns themselves,

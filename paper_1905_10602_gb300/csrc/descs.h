@@ -41,19 +41,6 @@ struct QrDesc {
   int ld, m, n;
 };
 
-// One-sided Jacobi SVD of the m x n matrix G (destroyed): V (n x n, ldv) gets
-// the right singular vectors ordered by descending singular value, sig (n) the
-// singular values; Vw is an n x n work matrix (ld n).
-struct SvdDesc {
-  double* G;
-  double* V;
-  double* Vw;
-  double* sig;
-  int ldg, ldv, m, n;
-  int* sweeps;
-  int pad;
-};
-
 // y = alpha * op(A) x + beta * y ; A is m x n (op(A) is n x m when trans).
 struct GemvDesc {
   const double* A;

@@ -92,9 +92,7 @@ struct Work {
   std::vector<int> choff;  // offset of this node's y inside its parent's x
   std::vector<int> il_T;   // il_T[e] = position of (b, a) for the IL entry e = (a, b)
   std::vector<int> il_row; // il_row[e] = a for the IL entry e = (a, b)
-  std::vector<char> touched;  // per IL entry, cleared after every use
-  std::vector<int> mark;      // per node, -1 outside a lookup scope
-  std::vector<std::vector<int>> marks;  // one such array per host thread
+  std::vector<std::vector<int>> marks;  // per host thread, per node: -1 outside a lookup scope
   // device copies of the IL structure (phase-B kernel)
   int* d_il_row = nullptr;
   int* d_il = nullptr;
@@ -697,8 +695,6 @@ struct Factorizer {
     event_count.assign(nn, 0);
     W.il_row.assign(LL.il.size(), 0);
     W.il_T.assign(LL.il.size(), -1);
-    W.touched.assign(LL.il.size(), 0);
-    W.mark.assign(nn, -1);
     {
       const int nt = host_threads(nn);
       parallel_ranges(nt, [&](int t) {

@@ -681,36 +681,6 @@ void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec) {
   }
 }
 
-void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec) {
-  if (v.empty()) return;
-  int nmax = 0;
-  for (auto& x : v) nmax = std::max(nmax, x.n);
-  size_t smem = sizeof(double) * nmax + sizeof(int) * nmax + 16;
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    CK(cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CK(cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  });
-  for (size_t i = 0; i < v.size() && registry().on; ++i) {
-    const SvdDesc& x = v[i];
-    req(x.G, span(x.m, x.n, x.ldg), "svd.G", i);
-    req(x.V, span(x.n, x.n, x.ldv), "svd.V", i);
-    req(x.Vw, span(x.n, x.n, x.n), "svd.Vw", i);
-    req(x.sig, span(x.n, 1, x.n), "svd.sig", i);
-    if (x.ldg < x.m || x.ldv < x.n) throw Error(IFMM_EINVAL, "svd ld too small");
-  }
-  const SvdDesc* d = st.push(v);
-  prof_batch_tag() = (long)v.size();
-  const int kk = prec == P32 ? KK_SVD32 : KK_SVD64;
-  cudaEvent_t pe = profiler().begin(kk, st.stream);
-  if (prec == P32)
-    k_svd<float><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
-  else
-    k_svd<double><<<(unsigned)v.size(), 512, smem, st.stream>>>(d, (int)v.size(), 60);
-  check_launch("k_svd");
-  profiler().end(kk, st.stream, pe);
-}
-
 void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec) {
   if (v.empty()) return;
   for (auto& x : v) IFMM_REQUIRE(x.n <= 1024, IFMM_EINVAL, "pivoted QR wider than 1024 columns");
@@ -1035,19 +1005,6 @@ __device__ __forceinline__ df df_quick(float a, float b) {
   const float s = a + b;
   return {s, b - (s - a)};
 }
-__device__ __forceinline__ df df_add(df a, df b) {
-  df s = df_two_sum(a.h, b.h);
-  return df_quick(s.h, s.l + (a.l + b.l));
-}
-__device__ __forceinline__ df df_sub(df a, df b) {
-  df s = df_two_sum(a.h, -b.h);
-  return df_quick(s.h, s.l + (a.l - b.l));
-}
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.h, -p);
-  return df_quick(p, e + (a.h * b.l + a.l * b.h));
-}
 // a - (bh + bl) with a two-sum of the high parts; the low part is left
 // unnormalised (its consumer squares it)
 __device__ __forceinline__ df df_diff(df a, float bh, float bl) {
@@ -1081,13 +1038,6 @@ __device__ __forceinline__ df df_rsqrt_fast(df x) {
 __device__ __forceinline__ df df_acc(df acc, float ph, float pl) {
   const df s = df_two_sum(acc.h, ph);
   return df_quick(s.h, s.l + (acc.l + pl));
-}
-__device__ __forceinline__ df df_rsqrt(df x) {
-  const float y0 = rsqrtf(x.h);
-  const df yy = df_mul({y0, 0.f}, {y0, 0.f});
-  const df t = df_mul(x, yy);
-  const df e = df_sub({1.f, 0.f}, t);
-  return df_add({y0, 0.f}, df_mul({0.5f * y0, 0.f}, e));
 }
 
 __global__ void k_split_df(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo, int n) {

@@ -205,7 +205,6 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec);
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v);
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec);
-void launch_svd(DescStage& st, const std::vector<SvdDesc>& v, int prec);
 void launch_gemv(DescStage& st, const std::vector<GemvDesc>& v);
 void launch_qrcp(DescStage& st, const std::vector<QrcpDesc>& v, int prec);
 void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec);
