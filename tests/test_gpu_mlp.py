@@ -69,7 +69,19 @@ def test_learned_rank_mode_end_to_end():
     f_svd = ifmm.ifmm_factor(t, 4, 1e-6, precision="fp64")
     X, r = ifmm.ifmm_fact_events(f_svd)
     pred = ifmm.ifmm_mlp_forward(w, X) * 64
-    assert np.abs(pred - r).mean() < 3.0
+    err_mlp = float(np.abs(pred - r).mean())
+    assert err_mlp < 3.0
+    # without the network the best one can guess from the level alone is the
+    # level's mean rank (taken here from the test events themselves); the
+    # network's inputs (block size, current rank, fill rows, geometry) must
+    # predict better than that
+    lev = np.rint(X[:, 4] * 10).astype(int)
+    base = np.zeros_like(pred)
+    for L in np.unique(lev):
+        base[lev == L] = r[lev == L].mean()
+    err_base = float(np.abs(base - r).mean())
+    print("mean |rank error|: network", err_mlp, "per-level mean", err_base)
+    assert err_mlp < err_base
     f_lrn = ifmm.ifmm_factor(t, 4, 1e-6, precision="fp64", rank_mode="learned", mlp=w)
     s_svd, s_lrn = ifmm.ifmm_fact_stats(f_svd), ifmm.ifmm_fact_stats(f_lrn)
     print("mean |pred - rank|", float(np.abs(pred - r).mean()), "| factor s: svd", s_svd["time_factor"], "learned",
