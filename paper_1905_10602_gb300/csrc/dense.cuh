@@ -799,11 +799,9 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
   TC* ref = nrm + n;
   int* jp = (int*)(ref + n);
   int em = 0;
-  for (int j = 0; j < n; ++j)
-    for (int i = lane; i < m; i += 32) em = max(em, dexp(D.A[qr_row(D, i) + (long)j * ld]));
+  for (int e = lane; e < mn; e += 32) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
   const int sh = pow2_shift((int)__reduce_max_sync(0xffffffffu, (unsigned)em));
-  for (int j = 0; j < n; ++j)
-    for (int i = lane; i < m; i += 32) A[i + (size_t)j * m] = ld_tc<TC>(D.A[qr_row(D, i) + (long)j * ld], sh);
+  for (int e = lane; e < mn; e += 32) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
   __syncwarp();
   if (PIV) {
     for (int j = 0; j < n; ++j) {
@@ -903,11 +901,11 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
     if (lane == 0) x[0] = alpha;
     __syncwarp();
   }
-  for (int j = 0; j < n; ++j)
-    for (int i = lane; i < m; i += 32) {
-      const TC v = (j < k && i > j) ? (TC)0 : A[i + (size_t)j * m];
-      D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
-    }
+  for (int e = lane; e < mn; e += 32) {
+    const int i = e % m, j = e / m;
+    const TC v = (j < k && i > j) ? (TC)0 : A[e];
+    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
+  }
   if (PIV) {
     for (int j = lane; j < n; j += 32) D.jpvt[j] = jp[j];
     if (lane == 0) {
@@ -941,16 +939,14 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   int em = 0;
-  for (int j = w; j < n; j += nw)
-    for (int i = lane; i < m; i += 32) em = max(em, dexp(D.A[qr_row(D, i) + (long)j * ld]));
+  for (int e = tid; e < mn; e += nt_) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
   if (lane == 0) red_i[w] = em;
   __syncthreads();
   em = 0;
   for (int i = 0; i < nw; ++i) em = max(em, red_i[i]);
   const int sh = pow2_shift(em);
-  for (int j = w; j < n; j += nw)
-    for (int i = lane; i < m; i += 32) A[i + (size_t)j * m] = ld_tc<TC>(D.A[qr_row(D, i) + (long)j * ld], sh);
+  for (int e = tid; e < mn; e += nt_) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
   for (int j = tid; j < n; j += nt_) flag[j] = 0;
   __syncthreads();
   if (PIV) {
@@ -1140,11 +1136,11 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
     if (tid == 0) x[0] = alpha;
   }
   __syncthreads();
-  for (int j = w; j < n; j += nw)
-    for (int i = lane; i < m; i += 32) {
-      const TC v = (j < k && i > j) ? (TC)0 : A[i + (size_t)j * m];
-      D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
-    }
+  for (int e = tid; e < mn; e += nt_) {
+    const int i = e % m, j = e / m;
+    const TC v = (j < k && i > j) ? (TC)0 : A[e];
+    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
+  }
   if (PIV) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
     if (tid == 0) {
@@ -1202,8 +1198,7 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   // power-of-two scale from the cluster-wide largest magnitude
   int em = 0;
-  for (int j = w; j < n; j += nw)
-    for (int li = lane; li < ml; li += 32) em = max(em, dexp(D.A[(r0 + li) + (long)j * ld]));
+  for (int e = tid; e < ml * n; e += nt_) em = max(em, dexp(D.A[(r0 + e % ml) + (long)(e / ml) * ld]));
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
   if (lane == 0) red_i[w] = em;
   __syncthreads();
@@ -1217,8 +1212,10 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   em = 0;
   for (int r = 0; r < R; ++r) em = max(em, *cl.map_shared_rank(&xg, r));
   const int sh = pow2_shift(em);
-  for (int j = w; j < n; j += nw)
-    for (int li = lane; li < ml; li += 32) A[li + (size_t)j * mlp] = ld_tc<TC>(D.A[(r0 + li) + (long)j * ld], sh);
+  for (int e = tid; e < ml * n; e += nt_) {
+    const int li = e % ml, j = e / ml;
+    A[li + (size_t)j * mlp] = ld_tc<TC>(D.A[(r0 + li) + (long)j * ld], sh);
+  }
   __syncthreads();
   if (PIV) {
     for (int j = w; j < n; j += nw) {
@@ -1392,12 +1389,12 @@ __global__ void __launch_bounds__(512) k_qr_cluster(const QrcpDesc* __restrict__
   }
   // no CTA leaves while another may still read its shared memory
   cl.sync();
-  for (int j = w; j < n; j += nw)
-    for (int li = lane; li < ml; li += 32) {
-      const int i = r0 + li;
-      const TC v = (j < k && i > j) ? (TC)0 : A[li + (size_t)j * mlp];
-      D.A[i + (long)j * ld] = st_tc<TC>(v, -sh);
-    }
+  for (int e = tid; e < ml * n; e += nt_) {
+    const int li = e % ml, j = e / ml;
+    const int i = r0 + li;
+    const TC v = (j < k && i > j) ? (TC)0 : A[li + (size_t)j * mlp];
+    D.A[i + (long)j * ld] = st_tc<TC>(v, -sh);
+  }
   if (PIV && rank == 0) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
     if (tid == 0) {
