@@ -115,9 +115,13 @@ ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int
 
 /* Algorithm 1 with the coloring of ifmm_color (Sec. 3.2/3.3): initialise the
  * operators (Sec. 2.2), eliminate levels depth..2 color by color with eps-accurate
- * recompression of far-field fill-ins, and LU-factor the remaining level-2 system.
- * Requires ifmm_color first.  The factor keeps its own reference to device data
- * of the tree: the tree must outlive it. */
+ * recompression of far-field fill-ins, and invert the remaining level-2 system
+ * (explicit Gauss-Jordan inverse, partial pivoting).  Requires ifmm_color first.
+ * The factor keeps its own reference to device data of the tree: the tree must
+ * outlive it.  The call synchronizes the stream once per color (the ranks are
+ * read back) and may use up to 8 host threads for its own descriptor building
+ * (one inside ifmm_factor_batched workers); the result does not depend on the
+ * number of threads. */
 ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opts* o, void* stream,
                         ifmm_fact** out);
 
