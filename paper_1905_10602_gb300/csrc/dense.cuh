@@ -777,6 +777,26 @@ __device__ __forceinline__ void reflect_group(TC* A, int m, int k, int len, cons
   }
 }
 
+// (row, column) of the flat column-major index e = i + j m, advanced by a fixed
+// stride without a division per step
+struct FlatIdx {
+  int i, j, di, dj, m;
+  __device__ __forceinline__ FlatIdx(int e0, int stride, int m_) : m(m_ > 0 ? m_ : 1) {
+    i = e0 % m;
+    j = e0 / m;
+    di = stride % m;
+    dj = stride / m;
+  }
+  __device__ __forceinline__ void next() {
+    i += di;
+    j += dj;
+    if (i >= m) {
+      i -= m;
+      ++j;
+    }
+  }
+};
+
 // physical row of logical row i (QrcpDesc::rb, rs)
 __device__ __forceinline__ long qr_row(const QrcpDesc& D, int i) {
   return D.rb > 0 ? (long)(i / D.rb) * D.rs + i % D.rb : (long)i;
@@ -799,9 +819,15 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
   TC* ref = nrm + n;
   int* jp = (int*)(ref + n);
   int em = 0;
-  for (int e = lane; e < mn; e += 32) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
+  {
+    FlatIdx x(lane, 32, m);
+    for (int e = lane; e < mn; e += 32, x.next()) em = max(em, dexp(D.A[qr_row(D, x.i) + (long)x.j * ld]));
+  }
   const int sh = pow2_shift((int)__reduce_max_sync(0xffffffffu, (unsigned)em));
-  for (int e = lane; e < mn; e += 32) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
+  {
+    FlatIdx x(lane, 32, m);
+    for (int e = lane; e < mn; e += 32, x.next()) A[e] = ld_tc<TC>(D.A[qr_row(D, x.i) + (long)x.j * ld], sh);
+  }
   __syncwarp();
   if (PIV) {
     for (int j = 0; j < n; ++j) {
@@ -901,10 +927,12 @@ __global__ void k_qr_warp(const QrcpDesc* __restrict__ d, int nd, int slot_bytes
     if (lane == 0) x[0] = alpha;
     __syncwarp();
   }
-  for (int e = lane; e < mn; e += 32) {
-    const int i = e % m, j = e / m;
-    const TC v = (j < k && i > j) ? (TC)0 : A[e];
-    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
+  {
+    FlatIdx x(lane, 32, m);
+    for (int e = lane; e < mn; e += 32, x.next()) {
+      const TC v = (x.j < k && x.i > x.j) ? (TC)0 : A[e];
+      D.A[qr_row(D, x.i) + (long)x.j * ld] = st_tc<TC>(v, -sh);
+    }
   }
   if (PIV) {
     for (int j = lane; j < n; j += 32) D.jpvt[j] = jp[j];
@@ -939,14 +967,20 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
   const int tid = threadIdx.x, nt_ = blockDim.x;
   const int lane = tid & 31, w = tid >> 5, nw = nt_ >> 5;
   int em = 0;
-  for (int e = tid; e < mn; e += nt_) em = max(em, dexp(D.A[qr_row(D, e % m) + (long)(e / m) * ld]));
+  {
+    FlatIdx x(tid, nt_, m);
+    for (int e = tid; e < mn; e += nt_, x.next()) em = max(em, dexp(D.A[qr_row(D, x.i) + (long)x.j * ld]));
+  }
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
   if (lane == 0) red_i[w] = em;
   __syncthreads();
   em = 0;
   for (int i = 0; i < nw; ++i) em = max(em, red_i[i]);
   const int sh = pow2_shift(em);
-  for (int e = tid; e < mn; e += nt_) A[e] = ld_tc<TC>(D.A[qr_row(D, e % m) + (long)(e / m) * ld], sh);
+  {
+    FlatIdx x(tid, nt_, m);
+    for (int e = tid; e < mn; e += nt_, x.next()) A[e] = ld_tc<TC>(D.A[qr_row(D, x.i) + (long)x.j * ld], sh);
+  }
   for (int j = tid; j < n; j += nt_) flag[j] = 0;
   __syncthreads();
   if (PIV) {
@@ -1136,10 +1170,12 @@ __global__ void __launch_bounds__(1024) k_qr_cta(const QrcpDesc* __restrict__ d,
     if (tid == 0) x[0] = alpha;
   }
   __syncthreads();
-  for (int e = tid; e < mn; e += nt_) {
-    const int i = e % m, j = e / m;
-    const TC v = (j < k && i > j) ? (TC)0 : A[e];
-    D.A[qr_row(D, i) + (long)j * ld] = st_tc<TC>(v, -sh);
+  {
+    FlatIdx x(tid, nt_, m);
+    for (int e = tid; e < mn; e += nt_, x.next()) {
+      const TC v = (x.j < k && x.i > x.j) ? (TC)0 : A[e];
+      D.A[qr_row(D, x.i) + (long)x.j * ld] = st_tc<TC>(v, -sh);
+    }
   }
   if (PIV) {
     for (int j = tid; j < n; j += nt_) D.jpvt[j] = jp[j];
