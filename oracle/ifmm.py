@@ -107,9 +107,11 @@ class RankPolicy:
     """Rank of each recompression event.  Event key: (level, node, k) with k the
     count of earlier events of that node at that level (k = 0: level start).
 
-    Parity unpinned for the absolute ranks at finite eps: the paper prints none
-    for this kernel; they are checked only through the error's scaling with eps,
-    and the CUDA path is compared with these ranks replayed."""
+    The rule is pinned against the mathematics (strict threshold, the eps = 0
+    numerical-rank threshold, the larger of the two counts, and the weighted
+    re-basing reproducing every far block within eps).  The paper prints no
+    ranks for this kernel, so the absolute ranks of a whole factorization are
+    not pinned beyond that rule; the CUDA path is compared with them replayed."""
 
     def __init__(self, eps: float, replay: dict | None = None):
         self.eps = eps
