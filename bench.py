@@ -9,8 +9,20 @@ eps = 1e-6, sigma = 3).  The tree and coloring (host, built once) and the points
 and right-hand side are resident on the device before timing starts.
 
 The JSON line reports seconds per step in the mixed-precision mode (pivots and
-GMRES in FP64, Schur updates and recompression in FP32, FP64-accurate
-double-float matvec) and, as "fp64", the plain FP64 mode on the same GPU.
+GMRES in FP64; Schur updates on the tensor cores as 3xTF32, recompression in
+FP32; FP64-accurate float-pair matvec and FP32-stored solve) and, as "fp64", the
+plain FP64 mode on the same GPU, with the error of the mixed path against it.
+
+The timed steps run without per-launch events (launch counts only); one further
+profiled step brackets every launch with CUDA events on its stream and gives the
+per-class times behind "kernels" and the per-phase rooflines, whose peaks are
+measured on the same GPU by the library's probes (ifmm_probe_peak) and, for HBM,
+taken from MEASURED_PEAKS.json.
+
+--rank-mode learned first trains the rank predictor on the GPU (SVD-mode ranks
+of the 2,048- and 32,768-point spheres and the 65,536-point torus at eps 1e-4,
+1e-6, 1e-8) and then times the learned mode; the SVD mode of the same workload
+is timed beside it.
 
 --impl reference times the CPU oracle on a bounded sample of the same workload.
 With torchrun (N > 1 ranks) each rank factors and solves its own replica of the
@@ -21,7 +33,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,10 +44,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# ALU peaks from unit counts and the 2070 MHz maximum SM clock (152 SMs):
-# FP32: 128 lanes x 2 flop per clock; FP64: 2 DFMA x 2 flop per clock per SM.
-ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64": 152 * 2 * 2 * 2.070e9 / 1e12}
 METRIC = "IFMM factor+solve s at N=131k, eps=1e-6: mixed/learned vs plain FP64, same GB300"
+# FP32-pipe operations per pair interaction of the float-pair direct sum, counted
+# from its source (three pair differences, squares and their sum, the refined
+# reciprocal square root, the product with the charge and the accumulation)
+MATVEC_DF_OPS_PER_PAIR = 75
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -60,7 +72,8 @@ def parse():
     ap.add_argument("--workload", default="bumpy131k")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--rank-mode", default="svd", choices=["svd", "learned"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (0: min(steps, 4)); one warm-up")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -118,10 +131,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample_seconds(workload_name: str, budget_s: float = 25.0):
-    """The CPU oracle (as it stands) on a bounded sample of the workload: the same
-    surface family and parameters at a smaller N with the same points per leaf,
-    single-threaded BLAS, scaled linearly to the full N (the IFMM is O(N))."""
+def sample_of(workload_name: str, factor: int):
+    """A bounded sample of a workload: the same surface family, seed and
+    parameters at N / factor (a power of 4) with the same mean points per leaf
+    (one level less per factor 4 in N: surface-like trees grow ~4x per level)."""
+    import math
+
+    from paper_1905_10602_gb300.workloads import WORKLOADS
+
+    w = WORKLOADS[workload_name]
+    return w, w.n // factor, max(2, w.depth - int(round(math.log(factor, 4))))
+
+
+def oracle_sample_seconds(workload_name: str, factor: int, repeats: int = 1):
+    """The CPU oracle (as it stands) on a bounded sample of the workload, in a
+    subprocess with every host core available to its BLAS; best of `repeats`."""
     code = r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
@@ -133,28 +157,32 @@ w = WORKLOADS[%r]
 n, depth = %d, %d
 pts = surface(w.shape, n, w.seed)
 b = point_source_rhs(pts)
-t0 = time.perf_counter()
-o = IFMMOracle(pts, depth, w.cheb_order, w.eps, w.sigma).factor()
-x, its, rel = gmres(lambda v: direct_matvec(pts, v), b, precond=o.solve, tol=1e-8)
-t = time.perf_counter() - t0
-print(json.dumps({"t": t, "n": n, "depth": depth, "its": its, "rel": rel}))
+best = None
+for _ in range(%d):
+    t0 = time.perf_counter()
+    o = IFMMOracle(pts, depth, w.cheb_order, w.eps, w.sigma).factor()
+    x, its, rel = gmres(lambda v: direct_matvec(pts, v), b, precond=o.solve, tol=1e-8)
+    t = time.perf_counter() - t0
+    best = t if best is None else min(best, t)
+print(json.dumps({"t": best, "n": n, "depth": depth, "its": its, "rel": rel}))
 """
-    from paper_1905_10602_gb300.workloads import WORKLOADS
-
-    w = WORKLOADS[workload_name]
-    # same mean points per leaf: drop two levels per factor 16 in N
-    n_s, d_s = w.n // 32, max(2, w.depth - 2)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code % (ROOT, workload_name, n_s, d_s)], capture_output=True, text=True,
-                         env=env, timeout=max(120, 10 * budget_s))
+    w, n_s, d_s = sample_of(workload_name, factor)
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
+    out = subprocess.run([sys.executable, "-c", code % (ROOT, workload_name, n_s, d_s, repeats)], capture_output=True,
+                         text=True, env=env, timeout=3600)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     r = json.loads(out.stdout.strip().splitlines()[-1])
-    scaled = r["t"] * w.n / r["n"]
-    return scaled, {"value": scaled, "unit": "s", "cores": 1, "kind": "oracle",
-                    "sample": f"{w.shape} N={r['n']} depth {r['depth']} (same eps, order, sigma, points per leaf), "
-                              f"factor + GMRES(30) to 1e-8 in {r['t']:.1f} s on 1 host core, x{w.n // r['n']} "
-                              f"(work linear in N)"}
+    info = {"kind": "oracle", "cores": cores, "blas_threads": cores,
+            "sample": f"{w.shape} N={r['n']} depth {r['depth']} (same seed, eps, order, sigma and points per leaf), "
+                      f"factor + GMRES(30) to 1e-8 ({r['its']} iterations), best of {repeats}; one Python thread, "
+                      f"BLAS allowed {cores} threads",
+            "measured_sample_s": r["t"], "sample_n": r["n"], "sample_depth": r["depth"],
+            "scaled_by": w.n / r["n"], "scaling": "work linear in N (the IFMM and its GMRES are O(N) at fixed eps "
+                                                  "and points per leaf; the direct-sum matvec is not, and is a small "
+                                                  "part of the oracle's time)"}
+    return r["t"] * w.n / r["n"], info
 
 
 def run_reference(args, rank, world):
@@ -162,24 +190,99 @@ def run_reference(args, rank, world):
         return 0
     from paper_1905_10602_gb300.workloads import WORKLOADS
 
-    times = []
-    info = None
+    times, info = [], None
     for _ in range(args.warmup):
-        oracle_sample_seconds(args.workload)
+        oracle_sample_seconds(args.workload, 64)
     for _ in range(args.steps):
-        t, info = oracle_sample_seconds(args.workload)
+        t, info = oracle_sample_seconds(args.workload, 64)
         times.append(t)
     v = sum(times) / len(times)
     w = WORKLOADS[args.workload]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev {w.cheb_order}, "
-                                   f"eps {w.eps}, sigma {w.sigma}", "global_batch": world},
-            "cpu_baseline": dict(info, value=v),
-            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": config_of(w, args.precision, args.rank_mode, world),
+            "cpu_baseline": dict(info, value=v, unit="s"),
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "each step times the oracle on the stated sample (measured_sample_s) and scales it to the "
+                    "full workload's seconds (value)"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def config_of(w, precision, rank_mode, world):
+    return {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev order {w.cheb_order}, "
+                        f"eps {w.eps}, sigma {w.sigma}, GMRES(30) to 1e-8",
+            "precision": precision, "rank_mode": rank_mode, "matvec": "fp64" if precision == "fp64" else "df",
+            "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"}
+
+
+def measured_peaks(ifmm):
+    """TFLOP/s of the arithmetic units on this GPU (the library's probes) and the
+    HBM copy bandwidth of MEASURED_PEAKS.json."""
+    out = {k: max(ifmm.ifmm_probe_peak(k) for _ in range(2)) for k in ifmm.PEAK_KINDS}
+    try:
+        with open(PEAKS_FILE) as fh:
+            mp = json.load(fh)
+        out["hbm_gbs"] = float(mp["hbm_gbs"])
+        out["hbm_source"] = "MEASURED_PEAKS.json (measured copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        out["hbm_gbs"] = 6800.0
+        out["hbm_source"] = "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+    out["how"] = ("ifmm_probe_peak: register-only FMA / warp-MMA chains on 8 CTAs x 256 threads per SM, best of 2, "
+                  "CUDA events")
+    return out
+
+
+def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1):
+    """One roofline entry per kernel class of the profiled step: counted work /
+    CUDA-event time of the class on its launching stream, against the measured
+    peak of the unit that bounds it."""
+    gemm_peak = {"fp32": (peaks["tf32_mma"] / 3.0, "TF32 warp MMA peak / 3 (three MMAs per 3xTF32 product)"),
+                 "bf16": (peaks["bf16_mma"], "BF16 warp MMA peak"),
+                 "fp64": (peaks["fp64"], "FP64 FMA peak")}[precision]
+    ents = []
+
+    def add(kind, name, work, unit, bound, peak, peak_note):
+        n_, ms = prof.get(kind, (0, 0.0))
+        if not n_ or ms <= 0:
+            return
+        ms /= steps_profiled
+        ach = work / (ms / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        ents.append({"phase": name, "kernel": kind, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                     "frac": ach / peak, "ms_per_step": ms, "launches_per_step": n_ // steps_profiled,
+                     "peak_note": peak_note + " (of measured)"})
+
+    gk = "gemm_fp64" if precision == "fp64" else "gemm_fp32"
+    add(gk, "a5/a7 Schur and transform GEMMs", stats["flops_gemm"], "TFLOP/s", "tensor" if precision != "fp64" else "alu",
+        gemm_peak[0], gemm_peak[1])
+    qk = "qr_fp64" if precision == "fp64" else "qr_fp32"
+    add(qk, "a6 recompression pivoted QR", stats["flops_qr"], "TFLOP/s", "alu",
+        peaks["fp64" if precision == "fp64" else "fp32"], "FP64 FMA peak" if precision == "fp64" else "FP32 FMA peak")
+    sk = "svd_fp64" if precision == "fp64" else "svd_fp32"
+    add(sk, "a6 recompression Jacobi SVD", stats["flops_svd"], "TFLOP/s", "alu",
+        peaks["fp64" if precision == "fp64" else "fp32"], "FP64 FMA peak" if precision == "fp64" else "FP32 FMA peak")
+    add("gauss_jordan", "a4 pivot inverses (FP64)", stats["flops_inv"], "TFLOP/s", "alu", peaks["fp64"], "FP64 FMA peak")
+    add("gauss_jordan_big", "a9 level-1 inverse (FP64)", stats["flops_lu"], "TFLOP/s", "alu", peaks["fp64"],
+        "FP64 FMA peak")
+    apps = its + 1  # preconditioner applications per GMRES solve (one per iteration, one for x)
+    add("solve_graph", "a10 IFMM solve (preconditioner)", stats["solve_matrix_bytes"] * apps, "GB/s", "hbm",
+        peaks["hbm_gbs"], "HBM copy bandwidth")
+    if precision == "fp64":
+        add("matvec", "a11 direct-sum matvec (FP64)", 20.0 * n * n * (its + 1), "TFLOP/s", "alu", peaks["fp64"],
+            "FP64 FMA peak, ~20 flops per pair")
+    else:
+        n_, ms = prof.get("matvec", (0, 0.0))
+        if n_ and ms > 0:
+            pairs = float(n) * n * n_ / steps_profiled
+            ach = pairs / (ms / steps_profiled / 1e3)
+            pk = peaks["fp32"] * 1e12 / 2.0 / MATVEC_DF_OPS_PER_PAIR
+            ents.append({"phase": "a11 direct-sum matvec (float pairs)", "kernel": "matvec", "bound": "alu",
+                         "achieved": ach / 1e9, "peak": pk / 1e9, "unit": "Gpairs/s", "frac": ach / pk,
+                         "ms_per_step": ms / steps_profiled, "launches_per_step": n_ // steps_profiled,
+                         "peak_note": f"measured FP32 FMA issue rate / {MATVEC_DF_OPS_PER_PAIR} FP32 operations "
+                                      "per pair (of measured)"})
+    return ents
 
 
 def main():
@@ -215,6 +318,7 @@ def main():
     b = torch.from_numpy(b_host).cuda()
     stream = torch.cuda.current_stream()
     sptr = __import__("ctypes").c_void_p(stream.cuda_stream)
+    peaks = measured_peaks(ifmm)
 
     def barrier():
         torch.cuda.synchronize()
@@ -222,11 +326,34 @@ def main():
             dist.barrier()
             torch.cuda.synchronize()
 
+    mlp, learned_info = None, None
+    if args.rank_mode == "learned":
+        from paper_1905_10602_gb300.learned import train_rank_model
+
+        t0 = time.perf_counter()
+        mlp, loss, nev = train_rank_model(precision="fp64" if args.precision == "fp64" else "fp32")
+        learned_info = {"training_s": time.perf_counter() - t0, "training_events": nev, "final_loss": loss,
+                        "trained_on": "sphere2k, sphere32k, torus65k at eps 1e-4, 1e-6, 1e-8 (SVD-mode ranks)"}
+
     def step(prec, arith, rank_mode="svd"):
         k = ifmm.default_kernel(w.n, arith)
-        f = ifmm.ifmm_factor(tree, w.cheb_order, w.eps, kernel=k, precision=prec, rank_mode=rank_mode, stream=sptr)
+        f = ifmm.ifmm_factor(tree, w.cheb_order, w.eps, kernel=k, precision=prec, rank_mode=rank_mode,
+                             mlp=mlp if rank_mode == "learned" else None, stream=sptr)
         x, its, rel = ifmm.bem_gmres(tree, b, precond=f, restart=30, tol=1e-8, kernel=k, stream=sptr)
-        return f, its, rel
+        return f, its, rel, x
+
+    def timed(prec, arith, rank_mode, steps, warmup):
+        for _ in range(warmup):
+            step(prec, arith, rank_mode)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = None
+        for _ in range(steps):
+            last = step(prec, arith, rank_mode)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / steps, last
 
     arith = "fp64" if args.precision == "fp64" else "df"
     for _ in range(args.warmup):
@@ -234,7 +361,7 @@ def main():
     barrier()
     clocks = Clocks(local)
     clocks.start()
-    ifmm.ifmm_profile(True)
+    ifmm.ifmm_profile(False)  # launch counts only inside the timed region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     last = None
@@ -242,67 +369,68 @@ def main():
         last = step(args.precision, arith, args.rank_mode)
     e1.record(stream)
     barrier()
-    prof = ifmm.ifmm_profile_query()
-    ifmm.ifmm_profile(False)
     clk = clocks.stop()
+    counts = ifmm.ifmm_profile_query()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, dist, "cuda")
-    fact, its, rel = last
+    fact, its, rel, x_mixed = last
     stats = ifmm.ifmm_fact_stats(fact)
-    # kernels the library launched (every launch is counted as it is issued;
-    # a solve-graph replay counts its kernel nodes)
-    launches = prof.pop("kernels", (0, 0.0))[0] // args.steps
-    # dominant kernel of the step and its roofline (ALU-bound dense kernels)
-    flops_of = {"svd_fp32": stats["flops_svd"], "svd_fp64": stats["flops_svd"], "qr_fp32": stats["flops_qr"],
-                "qr_fp64": stats["flops_qr"], "gemm_fp32": stats["flops_gemm"], "gemm_fp64": stats["flops_gemm"],
-                "gauss_jordan": stats["flops_inv"], "gauss_jordan_big": stats["flops_lu"]}
-    # the shared-memory and global-memory QR kernels share one work counter (the
-    # cluster launches are counted, and timed inside the qr_* regions)
+    launches = counts.get("kernels", (0, 0.0))[0] // args.steps
+    # one profiled step: per-launch CUDA events on the launching stream
+    ifmm.ifmm_profile(True)
+    pf, pits, _, _ = step(args.precision, arith, args.rank_mode)
+    torch.cuda.synchronize()
+    prof = ifmm.ifmm_profile_query()
+    ifmm.ifmm_profile(False)
+    prof.pop("kernels", None)
+    pstats = ifmm.ifmm_fact_stats(pf)
+    # the shared-memory, cluster and global-memory QR kernels share one work counter
     for g in ("fp32", "fp64"):
-        prof.pop(f"qr_cluster_{g}", None)
-        if f"qr_global_{g}" in prof:
-            n1, m1 = prof.get(f"qr_{g}", (0, 0.0))
-            n2, m2 = prof.pop(f"qr_global_{g}")
-            prof[f"qr_{g}"] = (n1 + n2, m1 + m2)
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    kname, (klaunch, kms) = top
-    kms /= args.steps
+        n1, m1 = prof.get(f"qr_{g}", (0, 0.0))
+        for sub in (f"qr_cluster_{g}", f"qr_global_{g}"):
+            if sub in prof:
+                n2, m2 = prof.pop(sub)
+                n1, m1 = n1 + n2, m1 + (m2 if sub.startswith("qr_global") else 0.0)
+        if n1:
+            prof[f"qr_{g}"] = (n1, m1)
+    phases = phase_rooflines(prof, pstats, peaks, args.precision, w.n, pits)
+    top = max(phases, key=lambda e: e["ms_per_step"]) if phases else None
     roof = None
-    if kname in flops_of:
-        kind = "fp64" if (kname.endswith("fp64") or kname.startswith("gauss")) else "fp32"
-        achieved = flops_of[kname] / (kms / 1e3) / 1e12
-        peak = ALU_PEAK_TFLOPS[kind]
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "launches_per_step": klaunch // args.steps,
-                "ms_per_step": kms, "peak_note": f"{kind} FMA units x 2070 MHz (derived)"}
-    elif kname == "matvec":
-        pairs = float(w.n) * w.n
-        roof = {"bound": "alu", "kernel": kname, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "ms_per_step": kms, "pairs_per_s": pairs * (klaunch // args.steps) / (kms / 1e3)}
+    if top is not None:
+        roof = {"bound": top["bound"], "kernel": top["kernel"], "achieved": top["achieved"], "peak": top["peak"],
+                "unit": top["unit"], "frac": top["frac"], "traffic": None, "ms_per_step": top["ms_per_step"],
+                "launches_per_step": top["launches_per_step"], "peak_note": top["peak_note"],
+                "timing": "per-launch CUDA events on the launching stream, one profiled step after the timed region"}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "fp32" else ("bf16" if args.precision == "bf16" else "f64"),
-           "data": "synthetic",
-           "config": {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev order {w.cheb_order}, "
-                                  f"eps {w.eps}, sigma {w.sigma}, GMRES(30) to 1e-8",
-                      "precision": args.precision, "rank_mode": args.rank_mode, "matvec": arith,
-                      "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"},
-           "gmres": {"iterations": its, "relres": rel},
-           "factor_s": stats["time_factor"], "gpu_launches": int(launches),
-           "kernels": {k: {"launches_per_step": n // args.steps, "ms_per_step": m / args.steps}
-                       for k, (n, m) in prof.items() if n},
-           "roofline": roof, "clocks": clk}
-    # plain FP64 on the same GPU (one step, untimed by the events above)
+           "data": "synthetic", "config": config_of(w, args.precision, args.rank_mode, world),
+           "gmres": {"iterations": its, "relres": rel}, "factor_s": stats["time_factor"],
+           "gpu_launches": int(launches),
+           "kernels": {k: {"launches_per_step": n, "ms_per_step": m} for k, (n, m) in prof.items() if n},
+           "roofline": roof, "phases": phases, "peaks": peaks, "clocks": clk}
+    if learned_info is not None:
+        learned_info.update({k: stats.get(k) for k in ("learned_events", "learned_sketched", "learned_fallbacks")})
+        svd_ms, _ = timed(args.precision, arith, "svd", args.steps, 1)
+        learned_info["svd_mode_s"] = svd_ms / 1e3
+        learned_info["learned_vs_svd"] = svd_ms / ms
+        out["learned"] = learned_info
+    # plain FP64 on the same GPU, averaged over its own timed steps
     if not args.no_fp64 and args.precision != "fp64":
-        barrier()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        f64, its64, rel64 = step("fp64", "fp64")
-        s1.record(stream)
-        barrier()
-        out["fp64"] = {"value": s0.elapsed_time(s1) / 1e3, "unit": "s", "gmres_iterations": its64, "relres": rel64,
+        fsteps = args.fp64_steps or min(args.steps, 4)
+        f64_ms, (f64, its64, rel64, x64) = timed("fp64", "fp64", "svd", fsteps, 1)
+        m_mixed = ifmm.ifmm_solve(fact, b).cpu().numpy()
+        m_64 = ifmm.ifmm_solve(f64, b).cpu().numpy()
+        xm, x6 = x_mixed.cpu().numpy(), x64.cpu().numpy()
+        out["fp64"] = {"value": f64_ms / 1e3, "unit": "s", "steps": fsteps, "warmup": 1,
+                       "gmres_iterations": its64, "relres": rel64,
                        "factor_s": ifmm.ifmm_fact_stats(f64)["time_factor"]}
-        out["speedup_vs_fp64"] = out["fp64"]["value"] / out["value"]
+        out["speedup_vs_fp64"] = (f64_ms / 1e3) / out["value"]
+        out["error_vs_fp64"] = {
+            "applied_inverse": float(np.linalg.norm(m_mixed - m_64) / np.linalg.norm(m_64)),
+            "solution": float(np.linalg.norm(xm - x6) / np.linalg.norm(x6)),
+            "note": "||M_mixed b - M_fp64 b|| / ||M_fp64 b|| for the preconditioners of the two modes, and "
+                    "||x_mixed - x_fp64|| / ||x_fp64|| for the GMRES solutions (both at relative residual 1e-8)"}
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         barrier()
@@ -310,7 +438,8 @@ def main():
         tr = ifmm.ifmm_build_tree(pts, w.depth)
         ifmm.ifmm_color(tr, w.sigma)
         k = ifmm.default_kernel(w.n, arith)
-        f = ifmm.ifmm_factor(tr, w.cheb_order, w.eps, kernel=k, precision=args.precision, rank_mode=args.rank_mode)
+        f = ifmm.ifmm_factor(tr, w.cheb_order, w.eps, kernel=k, precision=args.precision, rank_mode=args.rank_mode,
+                             mlp=mlp)
         xh, _, _ = ifmm.bem_gmres(tr, b_host, precond=f, tol=1e-8, kernel=k)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -318,9 +447,30 @@ def main():
         out["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": int(n * (3 * 8 + 6 * 4 + 4 + 8)),
                       "d2h_bytes_per_step": int(n * 8),
                       "note": "tree + coloring + factor + GMRES from host points and host b to host x"}
-    if rank == 0 and not args.no_cpu and world == 1:
+    if rank == 0 and not args.no_cpu and world == 1 and args.workload in WORKLOADS:
         try:
-            _, out["cpu_baseline"] = oracle_sample_seconds(args.workload)
+            factor = 64 if w.n >= 65536 else 16
+            val, info = oracle_sample_seconds(args.workload, factor)
+            # the GPU on the very same sample, for a same-size comparison
+            ws, n_s, d_s = sample_of(args.workload, factor)
+            from paper_1905_10602_gb300.workloads import point_source_rhs, surface
+
+            ps = surface(ws.shape, n_s, ws.seed)
+            ts = ifmm.ifmm_build_tree(ps, d_s)
+            ifmm.ifmm_color(ts, ws.sigma)
+            bs = torch.from_numpy(point_source_rhs(ps)).cuda()
+            ks = ifmm.default_kernel(n_s, arith)
+            best = None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fs = ifmm.ifmm_factor(ts, ws.cheb_order, ws.eps, kernel=ks, precision=args.precision, stream=sptr)
+                ifmm.bem_gmres(ts, bs, precond=fs, tol=1e-8, kernel=ks, stream=sptr)
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                best = t if best is None else min(best, t)
+            out["cpu_baseline"] = dict(info, value=val, unit="s", gpu_same_sample_s=best,
+                                       same_sample_ratio=info["measured_sample_s"] / best)
         except Exception as e:  # the oracle leg must not hide the GPU result
             out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
     if rank == 0:

@@ -84,14 +84,17 @@ typedef struct {
   int rank_mode;         /* IFMM_RANK_*                                                 */
   const int32_t* replay; /* rank_mode REPLAY: host array of (level,node,event,rank)     */
   int64_t replay_len;    /*   quadruples, replay_len quadruples                         */
-  int max_rank;          /* cap on any node rank (0 = library default, 256)             */
+  int max_rank;          /* largest rank any node may need (0 = library default, 256);  */
+                         /*   a recompression that needs more fails with IFMM_ERANK     */
   const float* mlp;      /* rank_mode LEARNED: host weights, IFMM_MLP_NWEIGHTS floats   */
   uint64_t seed;         /* seed of the randomized range finder (LEARNED mode)          */
 } ifmm_opts;
 
 /* Sec. 2.1: uniform octree of the given depth (>= 2, <= 10) over n >= 1 points.
- * xyz: n x 3 row-major doubles, host memory.  The root is the tight bounding cube
- * of the points.  The tree keeps a device copy of the points in tree order. */
+ * xyz: n x 3 row-major doubles, host or device memory (device points are copied
+ * to the host, where the tree and its lists are built).  The root is the tight
+ * bounding cube of the points.  The tree keeps a device copy of the points in
+ * tree order once a device call first needs them. */
 ifmm_status ifmm_build_tree(const double* xyz, int64_t n, int depth, ifmm_tree** out);
 
 /* Sec. 3.4, Algorithm 3: greedy coloring at separation sigma (>= 3) of every level
@@ -121,7 +124,9 @@ ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int
  * outlive it.  The call synchronizes the stream once per color (the ranks are
  * read back) and may use up to 8 host threads for its own descriptor building
  * (one inside ifmm_factor_batched workers); the result does not depend on the
- * number of threads. */
+ * number of threads.  Errors: IFMM_ESINGULAR when a pivot block (or the level-2
+ * system) has an exactly zero pivot in Gauss-Jordan with partial pivoting;
+ * IFMM_ERANK when a recompression keeps more than max_rank directions. */
 ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opts* o, void* stream,
                         ifmm_fact** out);
 
@@ -175,9 +180,12 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
  *   - The tree must already be resident on the current device: any earlier
  *     ifmm_factor, bem_matvec or bem_gmres on it uploads it (this call never
  *     does, since that would allocate).  Otherwise IFMM_EINVAL.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The scratch array's device address is looked up (cudaGetSymbolAddress,
+ *     which also loads the module holding the array and this call's kernels)
+ *     when the tree is first made resident on a device, inside a call that
+ *     allocates anyway.  Only if that look-up failed does the first call here
+ *     repeat it (and may then load the module); make that first call before
+ *     any stream capture.
  *   - All calls share the one scratch array: calls that overlap on the GPU (on
  *     different streams, or from different threads) race and give wrong results.
  *     No part of the scratch needs clearing between calls.
@@ -233,10 +241,7 @@ ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64
 ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count);
 const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
 
-/* Kernel profiling of this process (no counterpart in the paper): ifmm_profile
- * resets the per-kernel counters and, if timing != 0, brackets every later kernel
- * launch (or solve graph launch) with CUDA events on its stream.  Timing adds
- * event records between launches; leave it off for production runs. */
+
 /* Diagnostic: the binary64 -> binary32 conversion the FP32 kernels use on their
  * FP64 storage (integer operations on the IEEE-754 fields, GB300's FP64 pipe
  * being narrow), applied on the device to n host doubles x scaled by 2^shift:
@@ -245,6 +250,26 @@ const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
  * 2^-shift as a double (exact).  |shift| <= 200, n <= 2^26; host arrays. */
 ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, double* back);
 
+/* Diagnostic: one C = alpha op(A) op(B) + beta C through the library's batched
+ * GEMM in the arithmetic of `precision` (IFMM_PREC_*: FP64 FMA; FP32-accurate
+ * 3xTF32 tensor-core MMAs; bfloat16 operands with FP32 accumulation -- the
+ * kernels of the factorization's Schur updates), on host arrays, column-major,
+ * op(X) = X^T when tX != 0.  m, n, k <= 8192.  Synchronous. */
+ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
+                            const double* B, int ldb, double beta, double* C, int ldc);
+
+/* Measured arithmetic peak of the current GPU in TFLOP/s (no counterpart in the
+ * paper: the denominators of the per-phase rooflines).  kind: 0 FP32 FMA, 1 FP64
+ * FMA, 2 TF32 warp MMA (m16n8k8), 3 BF16 warp MMA (m16n8k16, FP32 accumulate),
+ * 4 FP64 warp MMA (m8n8k4).  Runs register-only dependency chains on 8 CTAs of
+ * 256 threads per SM, times the second of two launches with CUDA events on the
+ * legacy default stream, and synchronizes.  Allocates one small device buffer. */
+ifmm_status ifmm_probe_peak(int kind, double* tflops);
+
+/* Kernel profiling of this process (no counterpart in the paper): ifmm_profile
+ * resets the per-kernel counters and, if timing != 0, brackets every later kernel
+ * launch (or solve graph launch) with CUDA events on its stream.  Timing adds
+ * event records between launches; leave it off for production runs. */
 ifmm_status ifmm_profile(int timing);
 
 /* Counter `index` (0..): kernel name, kernels launched so far (a solve graph

@@ -1,9 +1,10 @@
 """Builds libifmm.so in-tree for sm_103a (GB300).
 
-Two CUDA translation units compiled by nvcc (runtime.cu: every kernel of the
-main path; noalloc.cu: the allocation-free matvec) and the host translation
-units compiled by g++, in parallel, then linked against the
-CUDA runtime.  `python -m paper_1905_10602_gb300.build` or build() from Python.
+Four CUDA translation units compiled by nvcc (runtime.cu: every kernel of the
+main path; noalloc.cu: the allocation-free matvec; mlp.cu: the rank
+predictor's training and inference kernels; probe.cu: the arithmetic-peak
+probes) and the host translation units compiled by g++, in parallel, then
+linked against the CUDA runtime.  `python -m paper_1905_10602_gb300.build` or build() from Python.
 """
 
 from __future__ import annotations
@@ -20,7 +21,7 @@ LIB = os.path.join(HERE, "libifmm.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["runtime.cu", "noalloc.cu", "mlp.cu"]
+CU_SOURCES = ["runtime.cu", "noalloc.cu", "mlp.cu", "probe.cu"]
 CPP_SOURCES = ["tree.cpp", "factor.cpp", "solve.cpp", "batch.cpp"]
 
 

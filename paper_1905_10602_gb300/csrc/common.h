@@ -18,6 +18,8 @@ struct Error : std::runtime_error {
 };
 
 void set_last_error(const std::string& msg);
+// loads the allocation-free matvec's module on device `dev` (noalloc.cu)
+void noalloc_prepare_device(int dev);
 
 #define IFMM_REQUIRE(cond, code, msg)                 \
   do {                                                \

@@ -250,6 +250,210 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
   }
 }
 
+// ---------------------------------------------------------------- tensor-core GEMM (reduced precision)
+// C = alpha op(A) op(B) + beta C on the warp-level tensor cores, FP32
+// accumulation, FP64 storage.  MODE 0 (the FP32 mode): each operand x is split
+// into a TF32 head h = rn_tf32(x) and a TF32-rounded tail l = rn_tf32(x - h),
+// and a*b is taken as a_l*b_h + a_h*b_l + a_h*b_h (the l*l term, below
+// 2^-22 |a b|, is dropped; Ootomo and Yokota's 3xTF32 scheme), three
+// m16n8k8 MMAs per product tile.  MODE 1 (the BF16 mode): the operands are
+// rounded to bfloat16 and multiplied by one m16n8k16 MMA.
+//
+// A BM x BN output tile per CTA of WM x WN warps, K in slices of 32.  The next
+// slice is loaded into registers (as FP64) while the current one is multiplied,
+// then converted to FP32 on the integer pipes (d2f_pow2) and stored to the other
+// shared-memory buffer, k-major: As[k][m], Bs[k][n] with 8 floats of padding,
+// so fragment loads are free of bank conflicts.  The epilogue goes through
+// shared memory as a column-major tile, and every warp writes whole column
+// segments of C (coalesced).
+__device__ __forceinline__ unsigned tf32_rn(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// two floats as a bfloat16 pair (round to nearest even), lo in the low half
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+__device__ __forceinline__ void split_tf32(float x, unsigned& h, unsigned& l) {
+  h = tf32_rn(x);
+  l = tf32_rn(x - __uint_as_float(h));
+}
+
+template <int BM, int BN>
+constexpr int gemm_tc_smem_bytes() {
+  return (2 * 32 * (BM + 8) + 2 * 32 * (BN + 8)) * 4 > BN * (BM + 4) * 4 ? (2 * 32 * (BM + 8) + 2 * 32 * (BN + 8)) * 4
+                                                                           : BN * (BM + 4) * 4;
+}
+
+template <int BM, int BN, int WM, int WN, int MODE>
+__global__ void __launch_bounds__(WM * WN * 32) k_gemm_tc(const GemmDesc* __restrict__ d, const int* __restrict__ tile_ptr,
+                                                           int nd) {
+  constexpr int NT = WM * WN * 32, BK = 32;
+  constexpr int PA = BM + 8, PB = BN + 8, PC = BM + 4;
+  constexpr int WTM = BM / WM, WTN = BN / WN;  // warp tile
+  constexpr int MT = WTM / 16, NW = WTN / 8;    // MMA tiles per warp
+  constexpr int EA = BM * BK / NT, EB = BK * BN / NT;
+  static_assert(EA * NT == BM * BK && EB * NT == BK * BN, "tile / thread mismatch");
+  extern __shared__ float smf[];
+  float* As0 = smf;
+  float* Bs0 = smf + 2 * BK * PA;
+  const int di = find_desc(tile_ptr, nd, blockIdx.x);
+  const GemmDesc D = d[di];
+  const int local = blockIdx.x - tile_ptr[di];
+  const int tiles_m = (D.m + BM - 1) / BM;
+  const int row0 = (local % tiles_m) * BM, col0 = (local / tiles_m) * BN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp % WM, wn = warp / WM;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[MT][NW][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+  double ra[EA], rb[EB];
+  // element e of a slice: A tile (BM x BK) walked along the contiguous axis of
+  // A in memory, likewise B (BK x BN)
+  auto a_at = [&](int e, int& i, int& kk) {
+    if (D.ta) { kk = e % BK; i = e / BK; } else { i = e % BM; kk = e / BM; }
+  };
+  auto b_at = [&](int e, int& kk, int& j) {
+    if (D.tb) { j = e % BN; kk = e / BN; } else { kk = e % BK; j = e / BK; }
+  };
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int x = 0; x < EA; ++x) {
+      int i, kk;
+      a_at(tid + x * NT, i, kk);
+      const int r = row0 + i, c = k0 + kk;
+      ra[x] = (r < D.m && c < D.k) ? (D.ta ? D.A[c + (long)r * D.lda] : D.A[r + (long)c * D.lda]) : 0.0;
+    }
+#pragma unroll
+    for (int x = 0; x < EB; ++x) {
+      int kk, j;
+      b_at(tid + x * NT, kk, j);
+      const int r = k0 + kk, c = col0 + j;
+      rb[x] = (r < D.k && c < D.n) ? (D.tb ? D.B[c + (long)r * D.ldb] : D.B[r + (long)c * D.ldb]) : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+    float* As = As0 + buf * BK * PA;
+    float* Bs = Bs0 + buf * BK * PB;
+#pragma unroll
+    for (int x = 0; x < EA; ++x) {
+      int i, kk;
+      a_at(tid + x * NT, i, kk);
+      As[kk * PA + i] = d2f_pow2(ra[x], 0);
+    }
+#pragma unroll
+    for (int x = 0; x < EB; ++x) {
+      int kk, j;
+      b_at(tid + x * NT, kk, j);
+      Bs[kk * PB + j] = d2f_pow2(rb[x], 0);
+    }
+  };
+  const int nk = (D.k + BK - 1) / BK;
+  if (nk > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int ks = 0; ks < nk; ++ks) {
+    const int cur = ks & 1;
+    if (ks + 1 < nk) load((ks + 1) * BK);
+    const float* As = As0 + cur * BK * PA + wm * WTM;
+    const float* Bs = Bs0 + cur * BK * PB + wn * WTN;
+    if constexpr (MODE == 0) {
+#pragma unroll
+      for (int k8 = 0; k8 < BK; k8 += 8) {
+        unsigned bh[NW][2], bl[NW][2];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+          split_tf32(Bs[(k8 + t) * PB + j * 8 + g], bh[j][0], bl[j][0]);
+          split_tf32(Bs[(k8 + t + 4) * PB + j * 8 + g], bh[j][1], bl[j][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+          unsigned ah[4], al[4];
+          split_tf32(As[(k8 + t) * PA + i * 16 + g], ah[0], al[0]);
+          split_tf32(As[(k8 + t) * PA + i * 16 + g + 8], ah[1], al[1]);
+          split_tf32(As[(k8 + t + 4) * PA + i * 16 + g], ah[2], al[2]);
+          split_tf32(As[(k8 + t + 4) * PA + i * 16 + g + 8], ah[3], al[3]);
+#pragma unroll
+          for (int j = 0; j < NW; ++j) {
+            mma_tf32(acc[i][j], al, bh[j]);
+            mma_tf32(acc[i][j], ah, bl[j]);
+            mma_tf32(acc[i][j], ah, bh[j]);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k16 = 0; k16 < BK; k16 += 16) {
+        unsigned b[NW][2];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+          const float* bb = Bs + j * 8 + g;
+          b[j][0] = bf16x2(bb[(k16 + 2 * t) * PB], bb[(k16 + 2 * t + 1) * PB]);
+          b[j][1] = bf16x2(bb[(k16 + 2 * t + 8) * PB], bb[(k16 + 2 * t + 9) * PB]);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+          const float* aa = As + i * 16 + g;
+          unsigned a[4];
+          a[0] = bf16x2(aa[(k16 + 2 * t) * PA], aa[(k16 + 2 * t + 1) * PA]);
+          a[1] = bf16x2(aa[(k16 + 2 * t) * PA + 8], aa[(k16 + 2 * t + 1) * PA + 8]);
+          a[2] = bf16x2(aa[(k16 + 2 * t + 8) * PA], aa[(k16 + 2 * t + 9) * PA]);
+          a[3] = bf16x2(aa[(k16 + 2 * t + 8) * PA + 8], aa[(k16 + 2 * t + 9) * PA + 8]);
+#pragma unroll
+          for (int j = 0; j < NW; ++j) mma_bf16(acc[i][j], a, b[j]);
+        }
+      }
+    }
+    if (ks + 1 < nk) store(cur ^ 1);
+    __syncthreads();
+  }
+  // epilogue: the tile through shared memory (column-major, ld PC), then whole
+  // column segments of C per warp
+  float* Cs = smf;
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const int r = wm * WTM + i * 16 + g, c = wn * WTN + j * 8 + 2 * t;
+      Cs[c * PC + r] = acc[i][j][0];
+      Cs[(c + 1) * PC + r] = acc[i][j][1];
+      Cs[c * PC + r + 8] = acc[i][j][2];
+      Cs[(c + 1) * PC + r + 8] = acc[i][j][3];
+    }
+  __syncthreads();
+  const float al = d2f_pow2(D.alpha, 0);
+  const int bm = D.beta == 0.0 ? 0 : (D.beta == 1.0 ? 1 : 2);
+  const int mr = min(BM, D.m - row0), nc = min(BN, D.n - col0);
+  for (int c = warp; c < nc; c += NT / 32) {
+    double* o = D.C + row0 + (long)(col0 + c) * D.ldc;
+    for (int r = lane; r < mr; r += 32) {
+      const double v = f2d_pow2(al * Cs[c * PC + r], 0);
+      o[r] = bm == 0 ? v : (bm == 1 ? o[r] + v : v + D.beta * o[r]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -1956,33 +2160,6 @@ __global__ void k_gemv(const GemvDesc* __restrict__ d, int nd) {
       const double s = dot_row(D.A + i, D.lda, D.x, D.n);
       D.y[i] = (D.beta == 0.0) ? D.alpha * s : D.alpha * s + D.beta * D.y[i];
     }
-  }
-}
-
-// y = alpha * sum_t A_t x_t + beta * y, one CTA per output vector.  For each
-// block of 32 rows, warp w sums the terms t = w, w + warps, ... (a lane per
-// row); the per-warp sums are then added in warp order (deterministic).
-__global__ void k_gemv_sum(const GemvSumDesc* __restrict__ d, const GemvTerm* __restrict__ terms, int nd) {
-  if ((int)blockIdx.x >= nd) return;
-  const GemvSumDesc D = d[blockIdx.x];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __shared__ double part[32][33];
-  for (int rb = 0; rb < D.m; rb += 32) {
-    const int i = rb + lane;
-    double s = 0.0;
-    if (i < D.m)
-      for (int t = D.first + w; t < D.first + D.count; t += nw) {
-        const GemvTerm T = terms[t];
-        s += dot_row(T.A + D.row0 + i, T.lda, T.x, T.n);
-      }
-    part[w][lane] = s;
-    __syncthreads();
-    if (w == 0 && i < D.m) {
-      double tot = 0.0;
-      for (int q = 0; q < nw; ++q) tot += part[q][lane];
-      D.y[i] = (D.beta == 0.0) ? D.alpha * tot : D.alpha * tot + D.beta * D.y[i];
-    }
-    __syncthreads();
   }
 }
 

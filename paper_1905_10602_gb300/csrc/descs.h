@@ -50,18 +50,30 @@ struct GemvDesc {
   double alpha, beta;
 };
 
-// y = alpha * sum_t A_t x_t + beta * y over the terms [first, first+count) of a
-// term list.
-struct GemvTerm {
-  const double* A;
-  const double* x;
-  int lda, n;
-};
-struct GemvSumDesc {
-  double* y;  // rows [row0, row0 + m) of the output vector start here
-  int m, first, count, row0;
+// One operation of the IFMM solve (Algorithm 2): for r in [0, rows)
+//   out[r] = beta * base[r] + alpha * sum_{c < ncols} M[r * ldm + c] * v(c),
+// v(c) = x[c] (xidx == nullptr) or x[xidx[c]].  M is row-major with ldm a
+// multiple of 4 and 16-byte aligned rows: FP64, or FP32 in the reduced-precision
+// modes.  The vectors are FP64, or float pairs (hi, lo) in the reduced-precision
+// modes, where alpha is +-1 and beta 0 or 1.  lanes (a power of two <= 32) lanes
+// share one row.
+struct SolveOp {
+  const void* M;
+  const void* x;
+  const int* xidx;
+  void* out;
+  const void* base;
   double alpha, beta;
+  int rows, ncols, ldm, lanes;
 };
+
+// dst (row-major, ldd) = src (rows x cols, column-major, lds), as FP64 or FP32.
+struct PackDesc {
+  const double* src;
+  void* dst;
+  int lds, ldd, rows, cols;
+};
+
 // Householder QR with column pivoting of the m x n matrix A, stopped at the
 // first step whose largest remaining column norm is <= tau_rel times the
 // largest initial column norm.  On exit the leading kout rows of A hold R (in

@@ -29,18 +29,21 @@ struct LevelFactor {
   std::vector<NodeFactor> nf;
 };
 
+// The solve as a fixed program of SolveOp launches over one vector buffer V:
+// the top vector, every node vector of levels 2..ell, then per-node scratch.
+// Elements are FP64, or float pairs in the reduced-precision modes (8 bytes
+// either way).  The blocks the solve reads are packed row-major in `mem`.
 struct SolveLaunch {
-  int kind;  // 0 copy, 1 gemv, 2 gemv_sum
-  const void* desc;
-  const void* terms;
-  int count;
+  const SolveOp* ops;
+  const int* warp_ptr;  // prefix sums of the warps of each op
+  int nops, nwarps;
 };
 
 struct SolvePlan {
-  double* X = nullptr;  // all node vectors of all levels + the top
-  int64_t xlen = 0;
-  double* tvec = nullptr;
-  double* stage_in = nullptr;   // tree-ordered input/output vector (alias of level ell's segment)
+  void* V = nullptr;
+  int64_t xlen = 0, vlen = 0;
+  void* stage_in = nullptr;  // tree-ordered input/output vector (level ell's segment of V)
+  bool pairs = false;
   std::vector<SolveLaunch> prog;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;

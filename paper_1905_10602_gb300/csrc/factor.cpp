@@ -209,7 +209,6 @@ struct Factorizer {
   int* d_info = nullptr;
   int info_cap = 0;
   std::vector<double*> pinned_sig;
-  double rank_capped = 0;
   double t_wait = 0;
   float* d_mlp = nullptr;  // rank-predictor weights on the device (learned mode)
   double n_learned = 0, n_capped = 0, n_fallback = 0, qrcp_steps = 0;
@@ -611,10 +610,11 @@ struct Factorizer {
         k = it->second;
         IFMM_REQUIRE(k >= 0 && k <= std::min(ev.avail[0], ev.avail[1]), IFMM_EINVAL, "replayed rank out of range");
       }
-      if (k > W.capr[ev.q]) {
-        rank_capped += 1;
-        k = W.capr[ev.q];
-      }
+      // the blocks of q were sized for at most capr[q] = min(n_q, max_rank)
+      // columns: a larger rank would break the eps guarantee if cut, so it is an error
+      IFMM_REQUIRE(k <= W.capr[ev.q], IFMM_ERANK,
+                   "level " + std::to_string(W.kappa) + " node " + std::to_string(ev.q) + " needs rank " +
+                       std::to_string(k) + " above max_rank " + std::to_string(maxrank));
       ev.k = k;
       F.rank_log.push_back({W.kappa, ev.q, ev.event_no, k});
       F.event_feat.insert(F.event_feat.end(), ev.feat, ev.feat + IFMM_MLP_IN);
@@ -1479,6 +1479,16 @@ struct Factorizer {
     CK(cudaStreamSynchronize(s));
     levelmem.release();
     scratch.release();
+    // the solve reads its own packed copies: the factor's block pool goes
+    F.stat("bytes_factor", (double)F.persist.high);
+    F.persist.release();
+    for (auto& LF : F.lv)
+      for (auto& nf : LF.nf) {
+        nf.piinv = nullptr;
+        nf.lcol.clear();
+        nf.urow.clear();
+      }
+    F.top_inv = nullptr;
     auto t1 = std::chrono::steady_clock::now();
     F.stat("time_factor", std::chrono::duration<double>(t1 - t0).count());
     F.stat("flops_gemm", cnt.gemm);
@@ -1487,13 +1497,11 @@ struct Factorizer {
     F.stat("flops_svd", cnt.svd);
     F.stat("flops_lu", cnt.lu);
     F.stat("flops_total", cnt.total());
-    F.stat("rank_capped", rank_capped);
     F.stat("time_device_wait", t_wait);
     F.stat("learned_events", n_learned);
     F.stat("learned_sketched", n_capped);
     F.stat("learned_fallbacks", n_fallback);
     F.stat("qrcp_steps", qrcp_steps);
-    F.stat("bytes_factor", (double)F.persist.high);
   }
 
   ~Factorizer() {

@@ -46,8 +46,13 @@ void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTab
 // Schur-complement blocks of the eliminated nodes added into their near blocks
 void launch_schur_scatter(DescStage& st, const std::vector<ScatterDesc>& v, const ScatterTables& t, int maxdeg);
 void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n);
-void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n);
-void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n);
+// the solve's row operations (pairs: float-pair vectors and FP32 matrices)
+void launch_solve_ops(cudaStream_t s, const SolveOp* ops, const int* warp_ptr, int nops, int nwarps, bool pairs);
+// column-major FP64 blocks -> row-major FP64 / FP32 copies
+void launch_pack(DescStage& st, const std::vector<PackDesc>& v, bool fp32);
+// FP64 <-> float pairs (hi = nearest float, lo = nearest float of the rest)
+void launch_pair_split(cudaStream_t s, const double* in, void* out, int64_t n);
+void launch_pair_join(cudaStream_t s, const void* in, double* out, int64_t n);
 const char* last_error();
 
 }  // namespace ifmm

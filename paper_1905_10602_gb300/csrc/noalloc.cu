@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "pairs.cuh"
 
 namespace {
 
@@ -26,38 +27,6 @@ static __device__ __align__(256) unsigned char g_matvec_scratch[NOALLOC_MAX_N * 
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[MAX_DEVICES] = {nullptr};
-
-struct fpair {
-  float h, l;
-};
-__device__ __forceinline__ fpair fp_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ fpair fp_quick(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
-  fpair s = fp_two_sum(a.h, b.h);
-  return fp_quick(s.h, s.l + (a.l + b.l));
-}
-__device__ __forceinline__ fpair fp_sub(fpair a, fpair b) {
-  fpair s = fp_two_sum(a.h, -b.h);
-  return fp_quick(s.h, s.l + (a.l - b.l));
-}
-__device__ __forceinline__ fpair fp_mul(fpair a, fpair b) {
-  const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.h, -p);
-  return fp_quick(p, e + (a.h * b.l + a.l * b.h));
-}
-__device__ __forceinline__ fpair fp_rsqrt(fpair x) {
-  const float y0 = rsqrtf(x.h);
-  const fpair t = fp_mul(x, fp_mul({y0, 0.f}, {y0, 0.f}));
-  const fpair e = fp_sub({1.f, 0.f}, t);
-  return fp_add({y0, 0.f}, fp_mul({0.5f * y0, 0.f}, e));
-}
 
 // x (caller order) -> scratch: tree-ordered doubles, then their float pairs
 __global__ void k_na_prepare(const double* __restrict__ x, const int* __restrict__ perm, unsigned char* scratch,
@@ -88,13 +57,13 @@ __global__ void __launch_bounds__(256) k_na_matvec(const double* __restrict__ p6
   __shared__ double d[4][256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (use_pairs) {
-    fpair px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
+    ifmm::df px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
     if (i < n) {
       px = {pdf[i], pdf[n + i]};
       py = {pdf[2 * n + i], pdf[3 * n + i]};
       pz = {pdf[4 * n + i], pdf[5 * n + i]};
     }
-    fpair acc = {0.f, 0.f};
+    ifmm::df acc = {0.f, 0.f};
     for (int j0 = 0; j0 < n; j0 += blockDim.x) {
       const int j = j0 + threadIdx.x;
       if (j < n) {
@@ -110,11 +79,14 @@ __global__ void __launch_bounds__(256) k_na_matvec(const double* __restrict__ p6
       __syncthreads();
       const int cnt = min((int)blockDim.x, n - j0);
       for (int t = 0; t < cnt; ++t) {
-        const fpair dx = fp_sub(px, {s[0][t], s[1][t]});
-        const fpair dy = fp_sub(py, {s[2][t], s[3][t]});
-        const fpair dz = fp_sub(pz, {s[4][t], s[5][t]});
-        const fpair r2 = fp_add(fp_add(fp_mul(dx, dx), fp_mul(dy, dy)), fp_mul(dz, dz));
-        if (j0 + t != i) acc = fp_add(acc, fp_mul({s[6][t], s[7][t]}, fp_rsqrt(r2)));
+        // the pair arithmetic of the main float-pair matvec (pairs.cuh)
+        const ifmm::df dx = ifmm::df_diff(px, s[0][t], s[1][t]);
+        const ifmm::df dy = ifmm::df_diff(py, s[2][t], s[3][t]);
+        const ifmm::df dz = ifmm::df_diff(pz, s[4][t], s[5][t]);
+        const ifmm::df w = ifmm::df_rsqrt_fast(ifmm::df_sum3(ifmm::df_sq(dx), ifmm::df_sq(dy), ifmm::df_sq(dz)));
+        const float ph = s[6][t] * w.h;
+        const float pl = fmaf(s[6][t], w.h, -ph) + fmaf(s[6][t], w.l, s[7][t] * w.h);
+        if (j0 + t != i) acc = ifmm::df_acc(acc, ph, pl);
       }
       __syncthreads();
     }
@@ -156,7 +128,42 @@ bool is_device_pointer(const void* p, int dev) {
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
+// Once per device, with that device current: the scratch array's device
+// address.  Looking it up loads this file's module (the array and the kernel
+// images), which the CUDA runtime otherwise does lazily at first use; the two
+// kernels are loaded here too.  That load is the only allocation tied to this
+// entry point, so it is done where the library allocates anyway.
+cudaError_t setup_device(int dev, void** addr) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_prepare);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_matvec);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *addr = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace
+
+namespace ifmm {
+// Called when a tree is first made resident on a device (ifmm_tree::ensure_device),
+// so that a later bem_matvec_noalloc on that device finds its module loaded.  A
+// failure here is not an error of the caller's call: bem_matvec_noalloc retries
+// and reports it.
+void noalloc_prepare_device(int dev) {
+  if (dev < 0 || dev >= MAX_DEVICES) return;
+  void* p = nullptr;
+  (void)setup_device(dev, &p);
+}
+}  // namespace ifmm
 
 extern "C" ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y,
                                           void* stream) {
@@ -189,20 +196,10 @@ extern "C" ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel*
     return IFMM_EINVAL;
   }
   void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        ifmm::set_last_error(std::string("bem_matvec_noalloc: cudaGetSymbolAddress failed: ") +
-                             cudaGetErrorString(e));
-        return IFMM_ECUDA;
-      }
-      g_scratch_addr[dev] = p;
-    }
-    scratch = g_scratch_addr[dev];
+  const cudaError_t se = setup_device(dev, &scratch);
+  if (se != cudaSuccess) {
+    ifmm::set_last_error(std::string("bem_matvec_noalloc: device set-up failed: ") + cudaGetErrorString(se));
+    return IFMM_ECUDA;
   }
   const int n = (int)t->N;
   cudaStream_t s = (cudaStream_t)stream;

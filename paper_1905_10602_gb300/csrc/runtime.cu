@@ -7,6 +7,7 @@
 #include <thread>
 
 #include "dense.cuh"
+#include "pairs.cuh"
 #include "ifmm_kernels.h"
 #include "runtime.h"
 
@@ -233,6 +234,37 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   profiler().end(KK_COPY, st.stream, pe);
 }
 
+// Reduced-precision GEMMs above 32 x 32 on the tensor cores (k_gemm_tc):
+// 128 x 128 tiles when both sides exceed 64, else 64 x 64 tiles.
+template <int BM, int BN, int WM, int WN>
+static void gemm_tc_one(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
+  if (v.empty()) return;
+  static thread_local std::vector<int> tp;
+  tp.assign(v.size() + 1, 0);
+  for (size_t i = 0; i < v.size(); ++i)
+    tp[i + 1] = tp[i] + (int)((long)((v[i].m + BM - 1) / BM) * ((v[i].n + BN - 1) / BN));
+  const GemmDesc* d = st.push(v);
+  const int* p = st.push(tp);
+  constexpr int smem = gemm_tc_smem_bytes<BM, BN>();
+  static bool attr = false;  // set once per process (the attribute is per function)
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_gemm_tc<BM, BN, WM, WN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_gemm_tc<BM, BN, WM, WN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  prof_batch_tag() = (long)v.size();
+  cudaEvent_t pe = profiler().begin(KK_GEMM32, st.stream);
+  if (prec == P16)
+    k_gemm_tc<BM, BN, WM, WN, 1><<<(unsigned)tp.back(), WM * WN * 32, smem, st.stream>>>(d, p, (int)v.size());
+  else
+    k_gemm_tc<BM, BN, WM, WN, 0><<<(unsigned)tp.back(), WM * WN * 32, smem, st.stream>>>(d, p, (int)v.size());
+  check_launch("k_gemm_tc");
+  profiler().end(KK_GEMM32, st.stream, pe);
+}
+static void launch_gemm_tc(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
+  gemm_tc_one<128, 128, 2, 4>(st, v, prec);
+}
+
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   if (v0.empty()) return;
   check_gemm(v0);
@@ -259,6 +291,16 @@ void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
     profiler().end(kk, st.stream, pe);
   }
   if (v.empty()) return;
+  if (prec != P64) {
+    // large products on the tensor cores; the rest stay on the 64 x 64 FMA tiles
+    static thread_local std::vector<GemmDesc> tc, fma;
+    tc.clear();
+    fma.clear();
+    for (auto& x : v) (x.m > 64 && x.n > 64 && x.k >= 32 ? tc : fma).push_back(x);
+    launch_gemm_tc(st, tc, prec);
+    v.swap(fma);
+    if (v.empty()) return;
+  }
   tp.assign(v.size() + 1, 0);
   for (size_t i = 0; i < v.size(); ++i) {
     long t = (long)((v[i].m + 63) / 64) * ((v[i].n + 63) / 64);
@@ -988,58 +1030,9 @@ __global__ void __launch_bounds__(256) k_matvec(const double* __restrict__ px, c
 }
 
 // ---------------------------------------------------------------- double-float matvec
-// The same sum with every quantity carried as an unevaluated pair of floats
-// (hi + lo, ~48-bit significand) and error-free transformations on FP32 FMAs
-// (Knuth's two-sum, FMA two-product, Dekker's renormalisation); 1/sqrt(r^2)
-// from rsqrtf refined by one Newton step in pair arithmetic.  FP64-level
-// accuracy at FP32 throughput.
-struct df {
-  float h, l;
-};
-__device__ __forceinline__ df df_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ df df_quick(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-// a - (bh + bl) with a two-sum of the high parts; the low part is left
-// unnormalised (its consumer squares it)
-__device__ __forceinline__ df df_diff(df a, float bh, float bl) {
-  const df s = df_two_sum(a.h, -bh);
-  return {s.h, s.l + (a.l - bl)};
-}
-// d^2 for d = h + l: h^2 exactly as a pair (FMA), plus 2 h l (l^2 is below
-// the pair's precision)
-__device__ __forceinline__ df df_sq(df d) {
-  const float p = d.h * d.h;
-  return {p, fmaf(d.h, d.h, -p) + 2.f * d.h * d.l};
-}
-__device__ __forceinline__ df df_sum3(df a, df b, df c) {
-  const df s = df_two_sum(a.h, b.h);
-  const df u = df_two_sum(s.h, c.h);
-  return df_quick(u.h, u.l + (s.l + (a.l + b.l + c.l)));
-}
-// 1/sqrt(x) as a pair: y0 = rsqrtf(x.h), one Newton step y0 + y0 (1 - x y0^2)/2
-// with the residual formed from the exact products (1 - x y0^2 is ~1e-7, so
-// its rounding is far below the pair's precision)
-__device__ __forceinline__ df df_rsqrt_fast(df x) {
-  const float y0 = rsqrtf(x.h);
-  const float th = y0 * y0;
-  const float tl = fmaf(y0, y0, -th);
-  const float uh = x.h * th;
-  const float ul = fmaf(x.h, th, -uh) + fmaf(x.h, tl, x.l * th);
-  const float e = (1.f - uh) - ul;
-  return {y0, 0.5f * y0 * e};
-}
-// acc + (ph + pl): two-sum of the high parts, low parts added
-__device__ __forceinline__ df df_acc(df acc, float ph, float pl) {
-  const df s = df_two_sum(acc.h, ph);
-  return df_quick(s.h, s.l + (acc.l + pl));
-}
-
+// The same sum with every quantity carried as a float pair (pairs.cuh);
+// 1/sqrt(r^2) from rsqrtf refined by one Newton step in pair arithmetic.
+// FP64-level accuracy at FP32 throughput.
 __global__ void k_split_df(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -1102,6 +1095,178 @@ __global__ void __launch_bounds__(BS) k_matvec_df(const float* __restrict__ pts,
     __syncthreads();
   }
   if (i < n) y[i] = diag * x[i] + scale * ((double)acc.h + (double)acc.l);
+}
+
+// ---------------------------------------------------------------- the solve's row operations
+// out[r] = beta base[r] + alpha sum_c M[r][c] v(c) for the rows of every op of a
+// launch.  `lanes` lanes share a row: each reads 16-byte vectors of the row
+// (4 FP32 or 2 FP64 coefficients) at a stride of lanes vectors, two vectors per
+// step, and the partial sums are combined by shuffles in a fixed order.  A warp
+// covers 32 / lanes rows of one op; warp_ptr gives each op's first warp.
+// PAIRS: FP32 coefficients, float-pair vectors and accumulation (the product of
+// an exact float by a pair is formed with FMAs, so the operator applied is the
+// stored FP32 matrix to ~2^-44); otherwise FP64 throughout.
+// s + a v(c) with a exact and v(c) a pair: the FMA two-product of a and the
+// high part plus a times the low part, added with a two-sum
+__device__ __forceinline__ df pair_term(df s, float a, const float2* __restrict__ X, const int* __restrict__ xidx,
+                                        int c) {
+  const float2 xv = xidx ? X[xidx[c]] : X[c];
+  const float p = a * xv.x;
+  return df_acc(s, p, fmaf(a, xv.y, fmaf(a, xv.x, -p)));
+}
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) k_solve_rows(const SolveOp* __restrict__ ops, const int* __restrict__ warp_ptr,
+                                                    int nops) {
+  const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (gw >= warp_ptr[nops]) return;  // whole warps
+  const int oi = find_desc(warp_ptr, nops, gw);
+  const SolveOp& O = ops[oi];
+  const int lane = threadIdx.x & 31;
+  const int G = O.lanes;
+  const int sub = lane & (G - 1);
+  const int r = (gw - warp_ptr[oi]) * (32 / G) + lane / G;
+  const bool live = r < O.rows;
+  const int nc = live ? O.ncols : 0;
+  if constexpr (PAIRS) {
+    const float2* X = (const float2*)O.x;
+    const int* xi = O.xidx;
+    const float* row = (const float*)O.M + (long)r * O.ldm;
+    df s = {0.f, 0.f};
+    int c = sub * 4;
+    for (; c + G * 4 < nc; c += 2 * G * 4) {
+      const float4 u = *(const float4*)(row + c);
+      const float4 w = *(const float4*)(row + c + G * 4);
+      const int c2 = c + G * 4;
+      s = pair_term(s, u.x, X, xi, c);
+      if (c + 1 < nc) s = pair_term(s, u.y, X, xi, c + 1);
+      if (c + 2 < nc) s = pair_term(s, u.z, X, xi, c + 2);
+      if (c + 3 < nc) s = pair_term(s, u.w, X, xi, c + 3);
+      s = pair_term(s, w.x, X, xi, c2);
+      if (c2 + 1 < nc) s = pair_term(s, w.y, X, xi, c2 + 1);
+      if (c2 + 2 < nc) s = pair_term(s, w.z, X, xi, c2 + 2);
+      if (c2 + 3 < nc) s = pair_term(s, w.w, X, xi, c2 + 3);
+    }
+    if (c < nc) {
+      const float4 u = *(const float4*)(row + c);
+      s = pair_term(s, u.x, X, xi, c);
+      if (c + 1 < nc) s = pair_term(s, u.y, X, xi, c + 1);
+      if (c + 2 < nc) s = pair_term(s, u.z, X, xi, c + 2);
+      if (c + 3 < nc) s = pair_term(s, u.w, X, xi, c + 3);
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, s.h, o), ol = __shfl_xor_sync(0xffffffffu, s.l, o);
+      s = df_acc(s, oh, ol);
+    }
+    if (live && sub == 0) {
+      if (O.alpha < 0.0) s = {-s.h, -s.l};
+      if (O.beta != 0.0) {
+        const float2 b = ((const float2*)O.base)[r];
+        s = df_acc(s, b.x, b.y);
+      }
+      ((float2*)O.out)[r] = make_float2(s.h, s.l);
+    }
+  } else {
+    const double* X = (const double*)O.x;
+    const double* row = (const double*)O.M + (long)r * O.ldm;
+    double s0 = 0.0, s1 = 0.0;
+    auto xv = [&](int c) { return O.xidx ? X[O.xidx[c]] : X[c]; };
+    int c = sub * 2;
+    for (; c + G * 2 < nc; c += 2 * G * 2) {
+      const double2 u = *(const double2*)(row + c);
+      const double2 w = *(const double2*)(row + c + G * 2);
+      const int c2 = c + G * 2;
+      s0 = fma(u.x, xv(c), s0);
+      if (c + 1 < nc) s1 = fma(u.y, xv(c + 1), s1);
+      s0 = fma(w.x, xv(c2), s0);
+      if (c2 + 1 < nc) s1 = fma(w.y, xv(c2 + 1), s1);
+    }
+    if (c < nc) {
+      const double2 u = *(const double2*)(row + c);
+      s0 = fma(u.x, xv(c), s0);
+      if (c + 1 < nc) s1 = fma(u.y, xv(c + 1), s1);
+    }
+    double s = s0 + s1;
+    for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (live && sub == 0) {
+      const double v = O.alpha * s;
+      ((double*)O.out)[r] = O.beta == 0.0 ? v : O.beta * ((const double*)O.base)[r] + v;
+    }
+  }
+}
+
+// 32 x 32 tiles of column-major FP64 blocks written row-major (FP64 or FP32),
+// through shared memory so both sides are coalesced
+template <bool F32>
+__global__ void __launch_bounds__(256) k_pack_rows(const PackDesc* __restrict__ d, const int* __restrict__ tile_ptr,
+                                                   int nd) {
+  __shared__ double tile[32][33];
+  const int di = find_desc(tile_ptr, nd, blockIdx.x);
+  const PackDesc D = d[di];
+  const int local = blockIdx.x - tile_ptr[di];
+  const int tr = (D.rows + 31) >> 5;
+  const int r0 = (local % tr) * 32, c0 = (local / tr) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + tx, c = c0 + j;
+    tile[j][tx] = (r < D.rows && c < D.cols) ? D.src[r + (long)c * D.lds] : 0.0;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
+    if (r < D.rows && c < D.cols) {
+      if constexpr (F32)
+        ((float*)D.dst)[(long)r * D.ldd + c] = d2f_pow2(tile[tx][i], 0);
+      else
+        ((double*)D.dst)[(long)r * D.ldd + c] = tile[tx][i];
+    }
+  }
+}
+
+__global__ void k_pair_split(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = in[i];
+    const float h = d2f_pow2(v, 0);
+    out[i] = make_float2(h, d2f_pow2(v - st_tc<float>(h), 0));
+  }
+}
+__global__ void k_pair_join(const float2* __restrict__ in, double* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = in[i];
+    out[i] = st_tc<float>(v.x) + st_tc<float>(v.y);
+  }
+}
+
+void launch_solve_ops(cudaStream_t s, const SolveOp* ops, const int* warp_ptr, int nops, int nwarps, bool pairs) {
+  if (!nops || !nwarps) return;
+  const unsigned blocks = (unsigned)((nwarps + 7) / 8);
+  if (pairs)
+    k_solve_rows<true><<<blocks, 256, 0, s>>>(ops, warp_ptr, nops);
+  else
+    k_solve_rows<false><<<blocks, 256, 0, s>>>(ops, warp_ptr, nops);
+}
+
+void launch_pack(DescStage& st, const std::vector<PackDesc>& v, bool fp32) {
+  if (v.empty()) return;
+  std::vector<int> tp(v.size() + 1, 0);
+  for (size_t i = 0; i < v.size(); ++i)
+    tp[i + 1] = tp[i] + (int)((long)((v[i].rows + 31) / 32) * ((v[i].cols + 31) / 32));
+  if (!tp.back()) return;
+  const PackDesc* d = st.push(v);
+  const int* p = st.push(tp);
+  if (fp32)
+    k_pack_rows<true><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
+  else
+    k_pack_rows<false><<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size());
+  check_launch("k_pack_rows");
+}
+
+void launch_pair_split(cudaStream_t s, const double* in, void* out, int64_t n) {
+  if (n > 0) k_pair_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, (float2*)out, n);
+}
+void launch_pair_join(cudaStream_t s, const void* in, double* out, int64_t n) {
+  if (n > 0) k_pair_join<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)in, out, n);
 }
 
 void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n) {
@@ -1424,17 +1589,51 @@ __global__ void k_conv_check(const double* x, int n, int sh, float* f, double* b
 void launch_copy_dev(cudaStream_t s, const CopyDesc* d, int n) {
   if (n) k_copy<<<n, 256, 0, s>>>(d, n);
 }
-void launch_gemv_dev(cudaStream_t s, const GemvDesc* d, int n) {
-  if (n) k_gemv<<<n, 128, 0, s>>>(d, n);
-}
-void launch_gemv_sum_dev(cudaStream_t s, const GemvSumDesc* d, const GemvTerm* t, int n) {
-  if (n) k_gemv_sum<<<n, 128, 0, s>>>(d, t, n);
-}
 
 }  // namespace ifmm
 
 extern "C" {
 const char* ifmm_last_error(void) { return ifmm::last_error(); }
+
+ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
+                            const double* B, int ldb, double beta, double* C, int ldc) {
+  using namespace ifmm;
+  try {
+    IFMM_REQUIRE(precision >= 0 && precision <= 2 && m >= 0 && n >= 0 && k >= 0 && m <= 8192 && n <= 8192 &&
+                     k <= 8192 && A && B && C,
+                 IFMM_EINVAL, "bad arguments");
+    IFMM_REQUIRE(lda >= std::max(1, ta ? k : m) && ldb >= std::max(1, tb ? n : k) && ldc >= std::max(1, m),
+                 IFMM_EINVAL, "leading dimension too small");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      throw Error(IFMM_ECUDA, "no CUDA device");
+    }
+    const size_t na = (size_t)lda * (ta ? m : k), nb = (size_t)ldb * (tb ? k : n), nc = (size_t)ldc * n;
+    DescStage st;
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    st.stream = s;
+    DeviceArena mem;
+    double* dA = mem.alloc(std::max<size_t>(na, 1));
+    double* dB = mem.alloc(std::max<size_t>(nb, 1));
+    double* dC = mem.alloc(std::max<size_t>(nc, 1));
+    CK(cudaMemcpyAsync(dA, A, sizeof(double) * na, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dB, B, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dC, C, sizeof(double) * nc, cudaMemcpyHostToDevice, s));
+    std::vector<GemmDesc> v{gmm(dA, lda, ta, dB, ldb, tb, dC, ldc, m, n, k, alpha, beta)};
+    launch_gemm(st, v, precision == IFMM_PREC_FP64 ? P64 : (precision == IFMM_PREC_FP32 ? P32 : P16));
+    CK(cudaMemcpyAsync(C, dC, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st.release();
+    mem.release();
+    CK(cudaStreamDestroy(s));
+    return IFMM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
 
 ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, double* back) {
   try {

@@ -8,6 +8,7 @@
 // the matching slice of its parent's x vector: aggregation (Algorithm 2,
 // "aggregate x of the children") and splitting cost nothing.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -18,33 +19,27 @@
 
 namespace ifmm {
 
-// A GEMV over many rows becomes several descriptors of at most 64 rows (one
-// CTA each), so a large pivot block is spread over several SMs.
-static void push_gemv_rows(std::vector<GemvDesc>& out, const GemvDesc& g) {
-  const int chunk = 64;
-  if (g.trans || g.m <= chunk) {
-    out.push_back(g);
-    return;
-  }
-  for (int r = 0; r < g.m; r += chunk) {
-    GemvDesc c = g;
-    c.A = g.A + r;
-    c.y = g.y + r;
-    c.m = std::min(chunk, g.m - r);
-    out.push_back(c);
-  }
+// lanes sharing one row of ncols coefficients, v per 16-byte vector: enough
+// lanes that each takes about two vectors, at most a warp
+static int row_lanes(int ncols, int v) {
+  int g = 1;
+  while (g < 32 && g * v * 2 < ncols) g *= 2;
+  return g;
 }
+static int pad4(int x) { return (x + 3) & ~3; }
 
 void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
   const ifmm_tree& T = *F.t;
   const int ell = T.depth;
   SolvePlan& P = F.plan;
-  // offsets of every node's x segment per level, and of the top vector
+  P.pairs = F.o.precision != IFMM_PREC_FP64;
+  const int esz = P.pairs ? 4 : 8;  // bytes of one packed coefficient
+  const int vw = 16 / esz;          // coefficients per 16-byte vector
+  // offsets (in elements of V) of every node's x segment per level, of the top
+  // vector (level 1), and of the per-node scratch
   std::vector<std::vector<int64_t>> xoff(ell + 1);
   std::vector<int64_t> base(ell + 1, 0);
-  int64_t total = 0;
-  base[1] = 0;
-  total = F.ntop;
+  int64_t total = F.ntop;
   for (int kappa = 2; kappa <= ell; ++kappa) {
     const LevelFactor& LF = F.lv[kappa];
     base[kappa] = total;
@@ -57,7 +52,8 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
     xoff[kappa][LF.nn] = o;
     total += o;
   }
-  // R-vector location (absolute index into X) of node i at level kappa
+  // V index of node i's R-row vector (its y): the matching slice of its
+  // parent's x, or of the top vector at level 2
   auto rloc = [&](int kappa, int i) -> int64_t {
     if (kappa == 2) return base[1] + F.top_off[i];
     const LevelLists& PL = T.lv[kappa - 1];
@@ -70,45 +66,8 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
     }
     return base[kappa - 1] + xoff[kappa - 1][par] + off;
   };
-  int64_t tlen = std::max<int64_t>(F.ntop, 1);
-  for (int kappa = 2; kappa <= ell; ++kappa) {
-    int64_t t = 0;
-    for (int i = 0; i < F.lv[kappa].nn; ++i) t += F.lv[kappa].n[i] + F.lv[kappa].r[i];
-    tlen = std::max(tlen, t);
-  }
-  P.xlen = total;
-  P.X = P.mem.alloc((size_t)std::max<int64_t>(total, 1));
-  P.tvec = P.mem.alloc((size_t)tlen);
-  double* X = P.X;
-  std::vector<CopyDesc> all_copy;
-  std::vector<GemvDesc> all_gemv;
-  std::vector<GemvSumDesc> all_sum;
-  std::vector<GemvTerm> all_terms;
-  struct L {
-    int kind;
-    size_t first, count;
-  };
-  std::vector<L> prog;
-  auto emit_gemv = [&](std::vector<GemvDesc>& v) {
-    if (v.empty()) return;
-    prog.push_back({1, all_gemv.size(), v.size()});
-    all_gemv.insert(all_gemv.end(), v.begin(), v.end());
-    v.clear();
-  };
-  auto emit_copy = [&](std::vector<CopyDesc>& v) {
-    if (v.empty()) return;
-    prog.push_back({0, all_copy.size(), v.size()});
-    all_copy.insert(all_copy.end(), v.begin(), v.end());
-    v.clear();
-  };
-  auto emit_sum = [&](std::vector<GemvSumDesc>& v) {
-    if (v.empty()) return;
-    prog.push_back({2, all_sum.size(), v.size()});
-    all_sum.insert(all_sum.end(), v.begin(), v.end());
-    v.clear();
-  };
-  // per-node t/s scratch offsets (re-used across levels)
   std::vector<std::vector<int64_t>> toff(ell + 1);
+  int64_t tlen = std::max<int64_t>(F.ntop, 1);
   for (int kappa = 2; kappa <= ell; ++kappa) {
     const LevelFactor& LF = F.lv[kappa];
     toff[kappa].resize(LF.nn);
@@ -117,122 +76,201 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
       toff[kappa][i] = o;
       o += LF.n[i] + LF.r[i];
     }
+    tlen = std::max(tlen, o);
   }
+  P.xlen = total;
+  P.vlen = total + tlen;
+  IFMM_REQUIRE(P.vlen < ((int64_t)1 << 31), IFMM_EINVAL, "solve vectors exceed 2^31 elements");
+  P.V = P.mem.alloc_bytes(8 * (size_t)P.vlen);
+  const int64_t TB = total;  // scratch starts here
+  char* V = (char*)P.V;
+  auto vp = [&](int64_t idx) { return (void*)(V + 8 * idx); };
+  // packed row-major copies of every block the solve reads
+  std::vector<PackDesc> pk;
+  auto packed = [&](const double* src, int lds, int rows, int cols, int& ldm) -> void* {
+    ldm = pad4(std::max(cols, 1));
+    void* dst = P.mem.alloc_bytes((size_t)esz * std::max(rows, 1) * ldm);
+    if (rows && cols) pk.push_back(PackDesc{src, dst, lds, ldm, rows, cols});
+    return dst;
+  };
+  std::vector<int32_t> xidx_all;  // gather indices, uploaded once
+  std::vector<std::vector<SolveOp>> launches;
+  auto op = [&](const void* M, int ldm, int rows, int ncols, const void* x, void* out, const void* base_, double alpha,
+                double beta) {
+    SolveOp o;
+    o.M = M;
+    o.x = x;
+    o.xidx = nullptr;
+    o.out = out;
+    o.base = base_;
+    o.alpha = alpha;
+    o.beta = beta;
+    o.rows = rows;
+    o.ncols = ncols;
+    o.ldm = ldm;
+    o.lanes = row_lanes(ncols, vw);
+    return o;
+  };
+  std::vector<std::vector<int64_t>> launch_xidx;  // per launch: xidx offset per op (-1: none)
+  // each pivot inverse is packed once (all m x m), read by both passes
+  std::vector<std::vector<std::pair<const char*, int>>> pip(ell + 1);
+  for (int kappa = 2; kappa <= ell; ++kappa) pip[kappa].assign(F.lv[kappa].nn, {nullptr, 0});
+  auto pivot = [&](int kappa, int i) -> std::pair<const char*, int> {
+    auto& e = pip[kappa][i];
+    if (!e.first) {
+      const NodeFactor& nf = F.lv[kappa].nf[i];
+      const int m = nf.n + nf.r;
+      e.first = (const char*)packed(nf.piinv, m, m, m, e.second);
+    }
+    return e;
+  };
+  auto emit = [&](std::vector<SolveOp>& v, std::vector<int64_t>& xo) {
+    if (v.empty()) return;
+    launches.push_back(std::move(v));
+    launch_xidx.push_back(std::move(xo));
+    v.clear();
+    xo.clear();
+  };
   // ---- forward substitution (upward), colors ascending
   for (int kappa = ell; kappa >= 2; --kappa) {
     const LevelFactor& LF = F.lv[kappa];
-    double* Xk = X + base[kappa];
     for (const auto& grp : LF.order) {
-      std::vector<GemvDesc> g1, g2;
-      std::vector<CopyDesc> c2;
+      std::vector<SolveOp> l1, l2;
+      std::vector<int64_t> x1, x2;
       for (int i : grp) {
         const NodeFactor& nf = LF.nf[i];
         const int n = nf.n, r = nf.r, m = n + r;
-        double* t = P.tvec + toff[kappa][i];
         if (m == 0) continue;
-        if (n) push_gemv_rows(g1, gmv(nf.piinv, m, m, n, 0, Xk + xoff[kappa][i], t, 1.0, 0.0));
-        else c2.push_back(cpy(nullptr, 0, t, m, m, 1));
+        const auto [Pi, ldp] = pivot(kappa, i);
+        const int64_t ti = TB + toff[kappa][i];
+        const int64_t xi = base[kappa] + xoff[kappa][i];
+        // t = Pi^-1 [x_i; 0]: rows [0, n) to scratch, rows [n, m) to the R-row slot
+        if (n) {
+          l1.push_back(op(Pi, ldp, n, n, vp(xi), vp(ti), nullptr, 1.0, 0.0));
+          x1.push_back(-1);
+        }
+        if (r) {
+          l1.push_back(op(Pi + (size_t)esz * n * ldp, ldp, r, n, vp(xi), vp(rloc(kappa, i)), nullptr, 1.0, 0.0));
+          x1.push_back(-1);
+        }
+        if (!n) continue;
+        // neighbours: their current row variable -= L_q t[:n]
         for (size_t a = 0; a < nf.nb.size(); ++a) {
           const int q = nf.nb[a];
           const int mq = nf.lcol_rows[a];
-          if (!mq || !n) continue;
-          double* y = nf.was_elim[a] ? X + rloc(kappa, q) : Xk + xoff[kappa][q];
-          push_gemv_rows(g2, gmv(nf.lcol[a], nf.lcol_ld[a], mq, n, 0, t, y, -1.0, 1.0));
+          if (!mq) continue;
+          int ldl = 0;
+          const void* Lq = packed(nf.lcol[a], nf.lcol_ld[a], mq, n, ldl);
+          const int64_t yq = nf.was_elim[a] ? rloc(kappa, q) : base[kappa] + xoff[kappa][q];
+          l2.push_back(op(Lq, ldl, mq, n, vp(ti), vp(yq), vp(yq), -1.0, 1.0));
+          x2.push_back(-1);
         }
-        if (r) c2.push_back(cpy(t + n, m, X + rloc(kappa, i), r, r, 1));
       }
-      emit_gemv(g1);
-      emit_copy(c2);
-      emit_gemv(g2);
+      emit(l1, x1);
+      emit(l2, x2);
     }
   }
-  // ---- top: y2 = D^{-1} rhs
+  // ---- top: y2 = D^-1 rhs (through the scratch, then back)
   if (F.ntop) {
-    std::vector<GemvDesc> g;
-    std::vector<CopyDesc> c;
-    push_gemv_rows(g, gmv(F.top_inv, F.ntop, F.ntop, F.ntop, 0, X + base[1], P.tvec, 1.0, 0.0));
-    c.push_back(cpy(P.tvec, F.ntop, X + base[1], F.ntop, F.ntop, 1));
-    emit_gemv(g);
-    emit_copy(c);
+    std::vector<SolveOp> l1, l2;
+    std::vector<int64_t> x1, x2;
+    int ldt = 0;
+    const void* Dm = packed(F.top_inv, F.ntop, F.ntop, F.ntop, ldt);
+    l1.push_back(op(Dm, ldt, F.ntop, F.ntop, vp(base[1]), vp(TB), nullptr, 1.0, 0.0));
+    x1.push_back(-1);
+    l2.push_back(op(nullptr, 4, F.ntop, 0, nullptr, vp(base[1]), vp(TB), 1.0, 1.0));
+    x2.push_back(-1);
+    emit(l1, x1);
+    emit(l2, x2);
   }
   // ---- backward substitution (downward), colors descending
   for (int kappa = 2; kappa <= ell; ++kappa) {
     const LevelFactor& LF = F.lv[kappa];
-    double* Xk = X + base[kappa];
     for (auto it = LF.order.rbegin(); it != LF.order.rend(); ++it) {
-      std::vector<CopyDesc> c1;
-      std::vector<GemvSumDesc> s1;
-      std::vector<GemvDesc> g2;
+      std::vector<SolveOp> l1, l2;
+      std::vector<int64_t> x1, x2;
       for (int i : *it) {
         const NodeFactor& nf = LF.nf[i];
         const int n = nf.n, r = nf.r, m = n + r;
         if (!n) continue;
-        double* sv = P.tvec + toff[kappa][i];
-        c1.push_back(cpy(Xk + xoff[kappa][i], n, sv, m, n, 1));
-        if (r) c1.push_back(cpy(X + rloc(kappa, i), r, sv + n, m, r, 1));
-        GemvSumDesc sd;
-        sd.y = sv;
-        sd.m = n;
-        sd.row0 = 0;
-        sd.first = (int)all_terms.size();
-        sd.count = 0;
-        sd.alpha = -1.0;
-        sd.beta = 1.0;
+        const int64_t ti = TB + toff[kappa][i];
+        const int64_t xi = base[kappa] + xoff[kappa][i];
+        // s = x_i - sum_q U_q v_q over the neighbours' current column variables
+        int cols = 0;
+        for (size_t a = 0; a < nf.nb.size(); ++a) cols += nf.urow_cols[a];
+        const int ldu = pad4(std::max(cols, 1));
+        void* U = P.mem.alloc_bytes((size_t)esz * n * ldu);
+        const int64_t xo = (int64_t)xidx_all.size();
+        int c0 = 0;
         for (size_t a = 0; a < nf.nb.size(); ++a) {
           const int q = nf.nb[a];
           const int mq = nf.urow_cols[a];
           if (!mq) continue;
-          const double* val = nf.was_elim[a] ? X + rloc(kappa, q) : Xk + xoff[kappa][q];
-          all_terms.push_back(GemvTerm{nf.urow[a], val, n, mq});
-          sd.count++;
+          pk.push_back(PackDesc{nf.urow[a], (char*)U + (size_t)esz * c0, n, ldu, n, mq});
+          const int64_t vq = nf.was_elim[a] ? rloc(kappa, q) : base[kappa] + xoff[kappa][q];
+          for (int j = 0; j < mq; ++j) xidx_all.push_back((int32_t)(vq + j));
+          c0 += mq;
         }
-        if (sd.count)
-          for (int r0 = 0; r0 < n; r0 += 32) {
-            GemvSumDesc c = sd;
-            c.m = std::min(32, n - r0);
-            c.y = sd.y + r0;
-            c.row0 = r0;
-            s1.push_back(c);
-          }
-        push_gemv_rows(g2, gmv(nf.piinv, m, n, m, 0, sv, Xk + xoff[kappa][i], 1.0, 0.0));
+        l1.push_back(op(U, ldu, n, cols, P.V, vp(ti), vp(xi), -1.0, 1.0));
+        x1.push_back(cols ? xo : -1);
+        // x_i = Pi^-1[:n, :] [s; y_i]
+        const auto [Pi, ldp] = pivot(kappa, i);
+        const int64_t xo2 = (int64_t)xidx_all.size();
+        for (int j = 0; j < n; ++j) xidx_all.push_back((int32_t)(ti + j));
+        const int64_t yi = r ? rloc(kappa, i) : 0;
+        for (int j = 0; j < r; ++j) xidx_all.push_back((int32_t)(yi + j));
+        l2.push_back(op(Pi, ldp, n, m, P.V, vp(xi), nullptr, 1.0, 0.0));
+        x2.push_back(xo2);
       }
-      emit_copy(c1);
-      emit_sum(s1);
-      emit_gemv(g2);
+      emit(l1, x1);
+      emit(l2, x2);
     }
   }
-  // upload
-  CopyDesc* dc = (CopyDesc*)P.mem.alloc_bytes(std::max<size_t>(1, all_copy.size()) * sizeof(CopyDesc));
-  GemvDesc* dg = (GemvDesc*)P.mem.alloc_bytes(std::max<size_t>(1, all_gemv.size()) * sizeof(GemvDesc));
-  GemvSumDesc* ds = (GemvSumDesc*)P.mem.alloc_bytes(std::max<size_t>(1, all_sum.size()) * sizeof(GemvSumDesc));
-  GemvTerm* dt = (GemvTerm*)P.mem.alloc_bytes(std::max<size_t>(1, all_terms.size()) * sizeof(GemvTerm));
-  if (!all_copy.empty()) CK(cudaMemcpy(dc, all_copy.data(), all_copy.size() * sizeof(CopyDesc), cudaMemcpyHostToDevice));
-  if (!all_gemv.empty()) CK(cudaMemcpy(dg, all_gemv.data(), all_gemv.size() * sizeof(GemvDesc), cudaMemcpyHostToDevice));
-  if (!all_sum.empty())
-    CK(cudaMemcpy(ds, all_sum.data(), all_sum.size() * sizeof(GemvSumDesc), cudaMemcpyHostToDevice));
-  if (!all_terms.empty())
-    CK(cudaMemcpy(dt, all_terms.data(), all_terms.size() * sizeof(GemvTerm), cudaMemcpyHostToDevice));
-  P.prog.clear();
-  for (auto& l : prog) {
-    SolveLaunch sl;
-    sl.kind = l.kind;
-    sl.count = (int)l.count;
-    sl.terms = dt;
-    if (l.kind == 0) sl.desc = dc + l.first;
-    else if (l.kind == 1) sl.desc = dg + l.first;
-    else sl.desc = ds + l.first;
-    P.prog.push_back(sl);
+  // ---- pack, upload, capture
+  {
+    DescStage st;
+    st.stream = s;
+    launch_pack(st, pk, P.pairs);
+    CK(cudaStreamSynchronize(s));
   }
-  P.stage_in = X + base[ell];
-  // capture the program into a graph on a private stream
+  int32_t* dx = (int32_t*)P.mem.alloc_bytes(sizeof(int32_t) * std::max<size_t>(1, xidx_all.size()));
+  if (!xidx_all.empty())
+    CK(cudaMemcpy(dx, xidx_all.data(), sizeof(int32_t) * xidx_all.size(), cudaMemcpyHostToDevice));
+  size_t nops_all = 0, nptr_all = 0;
+  for (auto& l : launches) {
+    nops_all += l.size();
+    nptr_all += l.size() + 1;
+  }
+  std::vector<SolveOp> ops_all;
+  std::vector<int> wp_all;
+  ops_all.reserve(nops_all);
+  wp_all.reserve(nptr_all);
+  std::vector<std::array<size_t, 3>> where;  // op offset, warp_ptr offset, warps
+  for (size_t li = 0; li < launches.size(); ++li) {
+    const size_t o0 = ops_all.size(), w0 = wp_all.size();
+    int warps = 0;
+    wp_all.push_back(0);
+    for (size_t k = 0; k < launches[li].size(); ++k) {
+      SolveOp o = launches[li][k];
+      if (launch_xidx[li][k] >= 0) o.xidx = dx + launch_xidx[li][k];
+      warps += (o.rows + 32 / o.lanes - 1) / (32 / o.lanes);
+      ops_all.push_back(o);
+      wp_all.push_back(warps);
+    }
+    where.push_back({o0, w0, (size_t)warps});
+  }
+  SolveOp* dops = (SolveOp*)P.mem.alloc_bytes(sizeof(SolveOp) * std::max<size_t>(1, ops_all.size()));
+  int* dwp = (int*)P.mem.alloc_bytes(sizeof(int) * std::max<size_t>(1, wp_all.size()));
+  if (!ops_all.empty()) CK(cudaMemcpy(dops, ops_all.data(), sizeof(SolveOp) * ops_all.size(), cudaMemcpyHostToDevice));
+  if (!wp_all.empty()) CK(cudaMemcpy(dwp, wp_all.data(), sizeof(int) * wp_all.size(), cudaMemcpyHostToDevice));
+  P.prog.clear();
+  for (size_t li = 0; li < launches.size(); ++li)
+    P.prog.push_back(SolveLaunch{dops + where[li][0], dwp + where[li][1], (int)launches[li].size(), (int)where[li][2]});
+  P.stage_in = vp(base[ell]);
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (auto& l : P.prog) {
-    if (l.kind == 0) launch_copy_dev(cs, (const CopyDesc*)l.desc, l.count);
-    else if (l.kind == 1) launch_gemv_dev(cs, (const GemvDesc*)l.desc, l.count);
-    else launch_gemv_sum_dev(cs, (const GemvSumDesc*)l.desc, (const GemvTerm*)l.terms, l.count);
-  }
+  for (auto& l : P.prog) launch_solve_ops(cs, l.ops, l.warp_ptr, l.nops, l.nwarps, P.pairs);
   cudaGraph_t g;
   CK(cudaStreamEndCapture(cs, &g));
   CK(cudaGraphInstantiate(&P.graph, g, 0));
@@ -240,35 +278,42 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
   CK(cudaStreamDestroy(cs));
   F.stat("solve_launches", (double)P.prog.size());
   F.stat("solve_vector_len", (double)total);
-  (void)s;
+  F.stat("bytes_solve", (double)P.mem.high);
+  double mbytes = 0;  // coefficient bytes one application streams
+  for (auto& o : ops_all) mbytes += (double)esz * o.rows * o.ncols;
+  F.stat("solve_matrix_bytes", mbytes);
 }
 
 // in/out: tree-ordered device vectors of length N (may alias)
 void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStream_t s) {
   const SolvePlan& P = F.plan;
   const int64_t N = F.t->N;
-  CK(cudaMemcpyAsync(P.stage_in, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  if (P.pairs)
+    launch_pair_split(s, in, P.stage_in, N);
+  else
+    CK(cudaMemcpyAsync(P.stage_in, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
   static const bool direct = [] {
     const char* e = getenv("IFMM_SOLVE_NOGRAPH");
     return e && e[0] == '1';
   }();
   if (direct) {  // the same program as individual launches, each timed when profiling
     for (auto& l : P.prog) {
-      const int kind = l.kind == 0 ? KK_COPY : (l.kind == 1 ? KK_GEMV : KK_GEMV_SUM);
-      prof_batch_tag() = l.count;
-      cudaEvent_t pe = profiler().begin(kind, s);
-      if (l.kind == 0) launch_copy_dev(s, (const CopyDesc*)l.desc, l.count);
-      else if (l.kind == 1) launch_gemv_dev(s, (const GemvDesc*)l.desc, l.count);
-      else launch_gemv_sum_dev(s, (const GemvSumDesc*)l.desc, (const GemvTerm*)l.terms, l.count);
-      profiler().end(kind, s, pe);
+      prof_batch_tag() = l.nops;
+      cudaEvent_t pe = profiler().begin(KK_GEMV, s);
+      launch_solve_ops(s, l.ops, l.warp_ptr, l.nops, l.nwarps, P.pairs);
+      profiler().end(KK_GEMV, s, pe);
     }
+    check_launch("k_solve_rows", (long)P.prog.size());
   } else {
     cudaEvent_t pe = profiler().begin(KK_SOLVE_GRAPH, s, (long)P.prog.size());
     CK(cudaGraphLaunch(P.graph, s));
     profiler().end(KK_SOLVE_GRAPH, s, pe);
     profiler().count(KK_ALL, (long)P.prog.size());
   }
-  CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  if (P.pairs)
+    launch_pair_join(s, P.stage_in, out, N);
+  else
+    CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
 
 static std::mutex g_tune_mutex;
@@ -314,6 +359,7 @@ void ifmm_tree::ensure_device() {
   registry().add(d_pts, sizeof(double) * 3 * N);
   registry().add(d_perm, sizeof(int32_t) * N);
   registry().add(d_pts_df, sizeof(float) * 6 * N);
+  noalloc_prepare_device(device);
 }
 
 ifmm_tree::~ifmm_tree() {

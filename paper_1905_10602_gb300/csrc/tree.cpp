@@ -11,6 +11,8 @@
 #include <numeric>
 #include <unordered_map>
 
+#include <cuda_runtime.h>
+
 #include "common.h"
 
 namespace ifmm {
@@ -251,7 +253,21 @@ ifmm_status ifmm_build_tree(const double* xyz, int64_t n, int depth, ifmm_tree**
   if (out) *out = nullptr;
   try {
     IFMM_REQUIRE(out != nullptr, IFMM_EINVAL, "out is NULL");
-    *out = build_tree(xyz, n, depth);
+    IFMM_REQUIRE(xyz != nullptr, IFMM_EINVAL, "xyz is NULL");
+    IFMM_REQUIRE(n >= 1 && n <= ((int64_t)1 << 31) - 1, IFMM_EINVAL, "n out of range");
+    // device points are copied to the host: the octree and lists are built there
+    cudaPointerAttributes a;
+    const bool on_dev = cudaPointerGetAttributes(&a, xyz) == cudaSuccess &&
+                        (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (on_dev) {
+      std::vector<double> h(3 * (size_t)n);
+      const cudaError_t e = cudaMemcpy(h.data(), xyz, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost);
+      IFMM_REQUIRE(e == cudaSuccess, IFMM_ECUDA, std::string("copying device points: ") + cudaGetErrorString(e));
+      *out = build_tree(h.data(), n, depth);
+    } else {
+      *out = build_tree(xyz, n, depth);
+    }
     return IFMM_OK;
   } catch (const Error& e) {
     set_last_error(e.what());

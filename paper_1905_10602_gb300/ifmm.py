@@ -64,6 +64,9 @@ _sig = {
     "ifmm_mlp_train": [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp],
     "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
     "ifmm_convert_check": [_vp, _i64, ctypes.c_int, _vp, _vp],
+    "ifmm_probe_peak": [ctypes.c_int, ctypes.POINTER(_dbl)],
+    "ifmm_gemm_check": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _vp,
+                        ctypes.c_int, _vp, ctypes.c_int, _dbl, _vp, ctypes.c_int],
 }
 for _name, _args in _sig.items():
     getattr(lib, _name).argtypes = _args
@@ -142,9 +145,11 @@ class Fact:
 
 
 def ifmm_build_tree(xyz, depth: int) -> Tree:
-    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
+    """xyz: (N, 3) points, a NumPy array or a float64 CUDA tensor."""
+    if not _is_torch(xyz):
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
     h = ctypes.c_void_p()
-    _check(lib.ifmm_build_tree(xyz.ctypes.data_as(ctypes.c_void_p), xyz.shape[0], depth, ctypes.byref(h)))
+    _check(lib.ifmm_build_tree(_ptr(xyz), xyz.shape[0], depth, ctypes.byref(h)))
     return Tree(h, xyz.shape[0], depth, xyz)
 
 
@@ -273,6 +278,31 @@ def ifmm_convert_check(x: np.ndarray, shift: int = 0):
     _check(lib.ifmm_convert_check(x.ctypes.data_as(ctypes.c_void_p), x.size, int(shift),
                                   f.ctypes.data_as(ctypes.c_void_p), back.ctypes.data_as(ctypes.c_void_p)))
     return f, back
+
+
+def ifmm_gemm_check(precision: str, A, B, C=None, alpha: float = 1.0, beta: float = 0.0, ta=False, tb=False):
+    """alpha op(A) op(B) + beta C through the library's batched GEMM kernels in
+    `precision` ("fp64", "fp32", "bf16"); NumPy arrays (diagnostic)."""
+    A = np.asfortranarray(A, dtype=np.float64)
+    B = np.asfortranarray(B, dtype=np.float64)
+    m = A.shape[1] if ta else A.shape[0]
+    k = A.shape[0] if ta else A.shape[1]
+    n = B.shape[0] if tb else B.shape[1]
+    C = np.asfortranarray(np.zeros((m, n)) if C is None else C, dtype=np.float64).copy(order="F")
+    _check(lib.ifmm_gemm_check(PREC[precision], m, n, k, int(ta), int(tb), alpha, A.ctypes.data_as(_vp),
+                               max(1, A.shape[0]), B.ctypes.data_as(_vp), max(1, B.shape[0]), beta,
+                               C.ctypes.data_as(_vp), max(1, m)))
+    return C
+
+
+PEAK_KINDS = {"fp32": 0, "fp64": 1, "tf32_mma": 2, "bf16_mma": 3, "fp64_mma": 4}
+
+
+def ifmm_probe_peak(kind: str) -> float:
+    """Measured TFLOP/s of one arithmetic unit of the current GPU (PEAK_KINDS)."""
+    v = _dbl()
+    _check(lib.ifmm_probe_peak(PEAK_KINDS[kind], ctypes.byref(v)))
+    return float(v.value)
 
 
 def bem_matvec_noalloc(tree: Tree, x, y, kernel: Kernel | None = None, stream=None) -> None:
