@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--rank-mode", default="svd", choices=["svd", "learned"])
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (0: min(steps, 4)); one warm-up")
+    ap.add_argument("--sigma", type=int, default=0, help="coloring separation (0: the workload's)")
+    ap.add_argument("--tau", type=int, default=2, help="levels below tau one node per color (Table 2's top level)")
+    ap.add_argument("--precond", default="ifmm", choices=["ifmm", "bd"], help="IFMM factor or BD block diagonal")
+    ap.add_argument("--bd-level", type=int, default=0, help="BDbot level (0: the leaf level)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -201,7 +205,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(w, args.precision, args.rank_mode, world),
+            "config": config_of(w, args.precision, args.rank_mode, world, args),
             "cpu_baseline": dict(info, value=v, unit="s"),
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "note": "each step times the oracle on the stated sample (measured_sample_s) and scales it to the "
@@ -210,11 +214,17 @@ def run_reference(args, rank, world):
     return 0
 
 
-def config_of(w, precision, rank_mode, world):
-    return {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev order {w.cheb_order}, "
-                        f"eps {w.eps}, sigma {w.sigma}, GMRES(30) to 1e-8",
-            "precision": precision, "rank_mode": rank_mode, "matvec": "fp64" if precision == "fp64" else "df",
-            "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"}
+def config_of(w, precision, rank_mode, world, args=None):
+    sigma = (args.sigma if args is not None and args.sigma else w.sigma)
+    c = {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev order {w.cheb_order}, "
+                     f"eps {w.eps}, sigma {sigma}, GMRES(30) to 1e-8",
+         "precision": precision, "rank_mode": rank_mode, "matvec": "fp64" if precision == "fp64" else "df",
+         "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"}
+    if args is not None and (args.tau != 2 or args.precond != "ifmm" or args.sigma):
+        c["sigma"] = sigma
+        c["tau"] = args.tau
+        c["precond"] = args.precond if args.precond == "ifmm" else f"BDb{args.bd_level or w.depth}"
+    return c
 
 
 def measured_peaks(ifmm):
@@ -254,19 +264,19 @@ def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1):
                      "peak_note": peak_note + " (of measured)"})
 
     gk = "gemm_fp64" if precision == "fp64" else "gemm_fp32"
-    add(gk, "a5/a7 Schur and transform GEMMs", stats["flops_gemm"], "TFLOP/s", "tensor" if precision != "fp64" else "alu",
+    add(gk, "a5/a7 Schur and transform GEMMs", stats.get("flops_gemm", 0.0), "TFLOP/s", "tensor" if precision != "fp64" else "alu",
         gemm_peak[0], gemm_peak[1])
     qk = "qr_fp64" if precision == "fp64" else "qr_fp32"
-    add(qk, "a6 recompression pivoted QR", stats["flops_qr"], "TFLOP/s", "alu",
+    add(qk, "a6 recompression pivoted QR", stats.get("flops_qr", 0.0), "TFLOP/s", "alu",
         peaks["fp64" if precision == "fp64" else "fp32"], "FP64 FMA peak" if precision == "fp64" else "FP32 FMA peak")
     sk = "svd_fp64" if precision == "fp64" else "svd_fp32"
-    add(sk, "a6 recompression Jacobi SVD", stats["flops_svd"], "TFLOP/s", "alu",
+    add(sk, "a6 recompression Jacobi SVD", stats.get("flops_svd", 0.0), "TFLOP/s", "alu",
         peaks["fp64" if precision == "fp64" else "fp32"], "FP64 FMA peak" if precision == "fp64" else "FP32 FMA peak")
-    add("gauss_jordan", "a4 pivot inverses (FP64)", stats["flops_inv"], "TFLOP/s", "alu", peaks["fp64"], "FP64 FMA peak")
-    add("gauss_jordan_big", "a9 level-1 inverse (FP64)", stats["flops_lu"], "TFLOP/s", "alu", peaks["fp64"],
+    add("gauss_jordan", "a4 pivot inverses (FP64)", stats.get("flops_inv", 0.0), "TFLOP/s", "alu", peaks["fp64"], "FP64 FMA peak")
+    add("gauss_jordan_big", "a9 level-1 inverse (FP64)", stats.get("flops_lu", 0.0), "TFLOP/s", "alu", peaks["fp64"],
         "FP64 FMA peak")
     apps = its + 1  # preconditioner applications per GMRES solve (one per iteration, one for x)
-    add("solve_graph", "a10 IFMM solve (preconditioner)", stats["solve_matrix_bytes"] * apps, "GB/s", "hbm",
+    add("solve_graph", "a10 IFMM solve (preconditioner)", stats.get("solve_matrix_bytes", 0.0) * apps, "GB/s", "hbm",
         peaks["hbm_gbs"], "HBM copy bandwidth")
     if precision == "fp64":
         add("matvec", "a11 direct-sum matvec (FP64)", 20.0 * n * n * (its + 1), "TFLOP/s", "alu", peaks["fp64"],
@@ -314,7 +324,8 @@ def main():
     pts = w.points()
     b_host = w.rhs(pts)
     tree = ifmm.ifmm_build_tree(pts, w.depth)
-    ifmm.ifmm_color(tree, w.sigma)
+    sigma = args.sigma or w.sigma
+    ifmm.ifmm_color_levels(tree, sigma, args.tau)
     b = torch.from_numpy(b_host).cuda()
     stream = torch.cuda.current_stream()
     sptr = __import__("ctypes").c_void_p(stream.cuda_stream)
@@ -335,22 +346,25 @@ def main():
         learned_info = {"training_s": time.perf_counter() - t0, "training_events": nev, "final_loss": loss,
                         "trained_on": "sphere2k, sphere32k, torus65k at eps 1e-4, 1e-6, 1e-8 (SVD-mode ranks)"}
 
-    def step(prec, arith, rank_mode="svd"):
+    def step(prec, arith, rank_mode="svd", precond=args.precond):
         k = ifmm.default_kernel(w.n, arith)
-        f = ifmm.ifmm_factor(tree, w.cheb_order, w.eps, kernel=k, precision=prec, rank_mode=rank_mode,
-                             mlp=mlp if rank_mode == "learned" else None, stream=sptr)
+        if precond == "bd":
+            f = ifmm.ifmm_bd_factor(tree, args.bd_level or w.depth, kernel=k, stream=sptr)
+        else:
+            f = ifmm.ifmm_factor(tree, w.cheb_order, w.eps, kernel=k, precision=prec, rank_mode=rank_mode,
+                                 mlp=mlp if rank_mode == "learned" else None, stream=sptr)
         x, its, rel = ifmm.bem_gmres(tree, b, precond=f, restart=30, tol=1e-8, kernel=k, stream=sptr)
         return f, its, rel, x
 
-    def timed(prec, arith, rank_mode, steps, warmup):
+    def timed(prec, arith, rank_mode, steps, warmup, precond="ifmm"):
         for _ in range(warmup):
-            step(prec, arith, rank_mode)
+            step(prec, arith, rank_mode, precond)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         last = None
         for _ in range(steps):
-            last = step(prec, arith, rank_mode)
+            last = step(prec, arith, rank_mode, precond)
         e1.record(stream)
         barrier()
         return e0.elapsed_time(e1) / steps, last
@@ -393,7 +407,7 @@ def main():
                 n1, m1 = n1 + n2, m1 + (m2 if sub.startswith("qr_global") else 0.0)
         if n1:
             prof[f"qr_{g}"] = (n1, m1)
-    phases = phase_rooflines(prof, pstats, peaks, args.precision, w.n, pits)
+    phases = phase_rooflines(prof, pstats, peaks, args.precision if args.precond == "ifmm" else "fp64", w.n, pits)
     top = max(phases, key=lambda e: e["ms_per_step"]) if phases else None
     roof = None
     if top is not None:
@@ -404,7 +418,7 @@ def main():
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "fp32" else ("bf16" if args.precision == "bf16" else "f64"),
-           "data": "synthetic", "config": config_of(w, args.precision, args.rank_mode, world),
+           "data": "synthetic", "config": config_of(w, args.precision, args.rank_mode, world, args),
            "gmres": {"iterations": its, "relres": rel}, "factor_s": stats["time_factor"],
            "gpu_launches": int(launches),
            "kernels": {k: {"launches_per_step": n, "ms_per_step": m} for k, (n, m) in prof.items() if n},
@@ -416,7 +430,7 @@ def main():
         learned_info["learned_vs_svd"] = svd_ms / ms
         out["learned"] = learned_info
     # plain FP64 on the same GPU, averaged over its own timed steps
-    if not args.no_fp64 and args.precision != "fp64":
+    if not args.no_fp64 and args.precision != "fp64" and args.precond == "ifmm":
         fsteps = args.fp64_steps or min(args.steps, 4)
         f64_ms, (f64, its64, rel64, x64) = timed("fp64", "fp64", "svd", fsteps, 1)
         m_mixed = ifmm.ifmm_solve(fact, b).cpu().numpy()
@@ -436,10 +450,13 @@ def main():
         barrier()
         t0 = time.perf_counter()
         tr = ifmm.ifmm_build_tree(pts, w.depth)
-        ifmm.ifmm_color(tr, w.sigma)
+        ifmm.ifmm_color_levels(tr, sigma, args.tau)
         k = ifmm.default_kernel(w.n, arith)
-        f = ifmm.ifmm_factor(tr, w.cheb_order, w.eps, kernel=k, precision=args.precision, rank_mode=args.rank_mode,
-                             mlp=mlp)
+        if args.precond == "bd":
+            f = ifmm.ifmm_bd_factor(tr, args.bd_level or w.depth, kernel=k)
+        else:
+            f = ifmm.ifmm_factor(tr, w.cheb_order, w.eps, kernel=k, precision=args.precision,
+                                 rank_mode=args.rank_mode, mlp=mlp)
         xh, _, _ = ifmm.bem_gmres(tr, b_host, precond=f, tol=1e-8, kernel=k)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -447,7 +464,7 @@ def main():
         out["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": int(n * (3 * 8 + 6 * 4 + 4 + 8)),
                       "d2h_bytes_per_step": int(n * 8),
                       "note": "tree + coloring + factor + GMRES from host points and host b to host x"}
-    if rank == 0 and not args.no_cpu and world == 1 and args.workload in WORKLOADS:
+    if rank == 0 and not args.no_cpu and world == 1 and args.workload in WORKLOADS and args.precond == "ifmm":
         try:
             factor = 64 if w.n >= 65536 else 16
             val, info = oracle_sample_seconds(args.workload, factor)

@@ -102,6 +102,15 @@ ifmm_status ifmm_build_tree(const double* xyz, int64_t n, int depth, ifmm_tree**
  * NULL, receives depth+1 counts (levels 0 and 1 report 0). */
 ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors_per_level);
 
+/* The per-level strategy switch of Sec. 4.2 (Table 2, nIFMMs{sigma}t{tau}b{l}):
+ * levels tau..depth are colored by Algorithm 3 at separation sigma and
+ * eliminated a color at a time (node-parallel), levels 2..tau-1 get one node
+ * per color, in node order, so their nodes are eliminated one after the other
+ * with each node's large matrix operations spread over the GPU
+ * (matrix-parallel).  tau in [2, depth]; tau = 2 is ifmm_color.  ncolors as
+ * for ifmm_color. */
+ifmm_status ifmm_color_levels(ifmm_tree* t, int sigma, int tau, int32_t* ncolors_per_level);
+
 /* Integer views of the tree, for inspection and tests.  `what` is one of
  *   "cells"  (3 per node: ix iy iz)        "parent"  (per node, level >= 1)
  *   "nbr_ptr" "nbr"   neighbour CSR (Sec. 2.1, excluding the node itself)
@@ -129,6 +138,17 @@ ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int
  * IFMM_ERANK when a recompression keeps more than max_rank directions. */
 ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opts* o, void* stream,
                         ifmm_fact** out);
+
+/* Sec. 4.3, BD / BDbot l_BD: the block-diagonal preconditioner the paper
+ * compares the IFMM with.  For every non-empty cell of `level` (0..depth; the
+ * leaf level is the paper's BD, a coarser level its BDbot l_BD) the self block
+ * of A over the cell's points is inverted on the device (FP64 Gauss-Jordan
+ * with partial pivoting); its application (Algorithm 5) solves each block
+ * independently.  The result is a factor handle: ifmm_solve applies it and
+ * bem_gmres takes it as `precond`, like an IFMM factor; ifmm_fact_stats reports
+ * bd_level, bd_blocks, bd_max_block and time_factor.  Level 0 is a single dense
+ * block: the exact inverse.  Errors: IFMM_ESINGULAR for a singular block. */
+ifmm_status ifmm_bd_factor(const ifmm_tree* t, const ifmm_kernel* k, int level, void* stream, ifmm_fact** out);
 
 /* Algorithm 2 (+ the dense level-2 solve): v = A~^{-1} r approximately, where A~ is
  * the FMM representation of A.  r and v: n x nrhs column-major doubles, host or

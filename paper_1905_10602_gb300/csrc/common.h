@@ -51,6 +51,7 @@ struct ifmm_tree {
   std::vector<int32_t> leaf_ptr; // points of leaf i: [leaf_ptr[i], leaf_ptr[i+1])
   std::vector<ifmm::LevelLists> lv;
   int sigma = 0;
+  int tau = 2;  // levels below tau are colored one node per color
   // device copies
   double* d_pts = nullptr;    // SoA: x[N], y[N], z[N] in tree order
   int32_t* d_perm = nullptr;  // tree order -> caller index

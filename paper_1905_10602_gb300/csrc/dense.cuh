@@ -255,17 +255,18 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
 // accumulation, FP64 storage.  MODE 0 (the FP32 mode): each operand x is split
 // into a TF32 head h = rn_tf32(x) and a TF32-rounded tail l = rn_tf32(x - h),
 // and a*b is taken as a_l*b_h + a_h*b_l + a_h*b_h (the l*l term, below
-// 2^-22 |a b|, is dropped; Ootomo and Yokota's 3xTF32 scheme), three
+// 2^-22 |a b|, is dropped: Ootomo and Yokota's 3xTF32 scheme), three
 // m16n8k8 MMAs per product tile.  MODE 1 (the BF16 mode): the operands are
 // rounded to bfloat16 and multiplied by one m16n8k16 MMA.
 //
-// A BM x BN output tile per CTA of WM x WN warps, K in slices of 32.  The next
-// slice is loaded into registers (as FP64) while the current one is multiplied,
-// then converted to FP32 on the integer pipes (d2f_pow2) and stored to the other
-// shared-memory buffer, k-major: As[k][m], Bs[k][n] with 8 floats of padding,
-// so fragment loads are free of bank conflicts.  The epilogue goes through
-// shared memory as a column-major tile, and every warp writes whole column
-// segments of C (coalesced).
+// A 128 x 128 output tile per CTA of 8 warps (2 x 4, 64 x 32 per warp), K in
+// slices of 16.  The FP64 slices are copied to shared memory with cp.async
+// (8-byte copies, zero-filled outside the matrices) into two stages, so the
+// next slice is in flight while the current one is used; each slice is then
+// converted once to FP32 on the integer pipes (d2f_pow2) and, in MODE 0, split
+// into TF32 head and tail, k-major with 8 words of padding (fragment loads
+// free of bank conflicts).  The epilogue goes through shared memory as a
+// column-major tile and every warp writes whole column segments of C.
 __device__ __forceinline__ unsigned tf32_rn(float x) {
   unsigned r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -288,114 +289,143 @@ __device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const unsigned*>(&v);
 }
-__device__ __forceinline__ void split_tf32(float x, unsigned& h, unsigned& l) {
-  h = tf32_rn(x);
-  l = tf32_rn(x - __uint_as_float(h));
+// 8-byte asynchronous copy global -> shared; nbytes 0 writes zeros
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int nbytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-template <int BM, int BN>
-constexpr int gemm_tc_smem_bytes() {
-  return (2 * 32 * (BM + 8) + 2 * 32 * (BN + 8)) * 4 > BN * (BM + 4) * 4 ? (2 * 32 * (BM + 8) + 2 * 32 * (BN + 8)) * 4
-                                                                           : BN * (BM + 4) * 4;
-}
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 16, kTcPad = 136, kTcPC = 132;
+// shared memory: two FP64 stages (A and B slices), then the converted slice
+// (MODE 0: A head, A tail, B head, B tail; MODE 1: A, B); the epilogue tile
+// (128 x 132 floats) reuses the FP64 stages
+constexpr int kTcStageBytes = 2 * (kTcBM * kTcBK + kTcBK * kTcBN) * 8;
+constexpr int kTcEpiBytes = kTcBN * kTcPC * 4;
+constexpr int kTcLowBytes = kTcStageBytes > kTcEpiBytes ? kTcStageBytes : kTcEpiBytes;
+constexpr int gemm_tc_smem_bytes(int mode) { return kTcLowBytes + (mode == 0 ? 4 : 2) * kTcBK * kTcPad * 4; }
 
-template <int BM, int BN, int WM, int WN, int MODE>
-__global__ void __launch_bounds__(WM * WN * 32) k_gemm_tc(const GemmDesc* __restrict__ d, const int* __restrict__ tile_ptr,
-                                                           int nd) {
-  constexpr int NT = WM * WN * 32, BK = 32;
-  constexpr int PA = BM + 8, PB = BN + 8, PC = BM + 4;
-  constexpr int WTM = BM / WM, WTN = BN / WN;  // warp tile
-  constexpr int MT = WTM / 16, NW = WTN / 8;    // MMA tiles per warp
-  constexpr int EA = BM * BK / NT, EB = BK * BN / NT;
-  static_assert(EA * NT == BM * BK && EB * NT == BK * BN, "tile / thread mismatch");
-  extern __shared__ float smf[];
-  float* As0 = smf;
-  float* Bs0 = smf + 2 * BK * PA;
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) k_gemm_tc(const GemmDesc* __restrict__ d, const int* __restrict__ tile_ptr,
+                                                     int nd) {
+  constexpr int BM = kTcBM, BN = kTcBN, BK = kTcBK, P = kTcPad;
+  extern __shared__ __align__(16) unsigned char tcsm[];
+  double* S64 = (double*)tcsm;                   // [2][BM*BK + BK*BN]
+  unsigned* Cv = (unsigned*)(tcsm + kTcLowBytes);  // converted slice
   const int di = find_desc(tile_ptr, nd, blockIdx.x);
-  const GemmDesc D = d[di];
+  const GemmDesc& D = d[di];
   const int local = blockIdx.x - tile_ptr[di];
   const int tiles_m = (D.m + BM - 1) / BM;
   const int row0 = (local % tiles_m) * BM, col0 = (local / tiles_m) * BN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp % WM, wn = warp / WM;
+  const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, warp tile 64 x 32
   const int g = lane >> 2, t = lane & 3;
-  float acc[MT][NW][4];
+  float acc[4][4][4];
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < NW; ++j)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-  double ra[EA], rb[EB];
-  // element e of a slice: A tile (BM x BK) walked along the contiguous axis of
-  // A in memory, likewise B (BK x BN)
-  auto a_at = [&](int e, int& i, int& kk) {
-    if (D.ta) { kk = e % BK; i = e / BK; } else { i = e % BM; kk = e / BM; }
-  };
-  auto b_at = [&](int e, int& kk, int& j) {
-    if (D.tb) { j = e % BN; kk = e / BN; } else { kk = e % BK; j = e / BK; }
-  };
-  auto load = [&](int k0) {
+  // staging order of a slice: A element (i, kk) at sa(i, kk), B element (kk, j)
+  // at sb(kk, j), along the contiguous axis of each matrix in memory
+  auto issue = [&](int k0, int stage) {
+    double* SA = S64 + stage * (BM * BK + BK * BN);
+    double* SB = SA + BM * BK;
 #pragma unroll
-    for (int x = 0; x < EA; ++x) {
+    for (int x = 0; x < BM * BK / 256; ++x) {
+      const int e = tid + x * 256;
       int i, kk;
-      a_at(tid + x * NT, i, kk);
+      if (D.ta) { kk = e % BK; i = e / BK; } else { i = e % BM; kk = e / BM; }
       const int r = row0 + i, c = k0 + kk;
-      ra[x] = (r < D.m && c < D.k) ? (D.ta ? D.A[c + (long)r * D.lda] : D.A[r + (long)c * D.lda]) : 0.0;
+      const bool in = r < D.m && c < D.k;
+      const double* src = in ? (D.ta ? D.A + c + (long)r * D.lda : D.A + r + (long)c * D.lda) : D.A;
+      cp_async8(SA + e, src, in ? 8 : 0);
     }
 #pragma unroll
-    for (int x = 0; x < EB; ++x) {
+    for (int x = 0; x < BK * BN / 256; ++x) {
+      const int e = tid + x * 256;
       int kk, j;
-      b_at(tid + x * NT, kk, j);
+      if (D.tb) { j = e % BN; kk = e / BN; } else { kk = e % BK; j = e / BK; }
       const int r = k0 + kk, c = col0 + j;
-      rb[x] = (r < D.k && c < D.n) ? (D.tb ? D.B[c + (long)r * D.ldb] : D.B[r + (long)c * D.ldb]) : 0.0;
+      const bool in = r < D.k && c < D.n;
+      const double* src = in ? (D.tb ? D.B + c + (long)r * D.ldb : D.B + r + (long)c * D.ldb) : D.B;
+      cp_async8(SB + e, src, in ? 8 : 0);
     }
+    cp_async_commit();
   };
-  auto store = [&](int buf) {
-    float* As = As0 + buf * BK * PA;
-    float* Bs = Bs0 + buf * BK * PB;
+  // converts stage `stage` into Cv: k-major rows of P words
+  auto convert = [&](int stage) {
+    const double* SA = S64 + stage * (BM * BK + BK * BN);
+    const double* SB = SA + BM * BK;
 #pragma unroll
-    for (int x = 0; x < EA; ++x) {
-      int i, kk;
-      a_at(tid + x * NT, i, kk);
-      As[kk * PA + i] = d2f_pow2(ra[x], 0);
+    for (int x = 0; x < BM * BK / 256; ++x) {
+      const int e = tid + x * 256;
+      const int i = e % BM, kk = e / BM;
+      const float f = d2f_pow2(D.ta ? SA[kk + i * BK] : SA[i + kk * BM], 0);
+      if constexpr (MODE == 0) {
+        const unsigned h = tf32_rn(f);
+        Cv[kk * P + i] = h;
+        Cv[(BK + kk) * P + i] = tf32_rn(f - __uint_as_float(h));
+      } else {
+        Cv[kk * P + i] = __float_as_uint(f);
+      }
     }
+    unsigned* CB = Cv + (MODE == 0 ? 2 : 1) * BK * P;
 #pragma unroll
-    for (int x = 0; x < EB; ++x) {
-      int kk, j;
-      b_at(tid + x * NT, kk, j);
-      Bs[kk * PB + j] = d2f_pow2(rb[x], 0);
+    for (int x = 0; x < BK * BN / 256; ++x) {
+      const int e = tid + x * 256;
+      const int j = e % BN, kk = e / BN;
+      const float f = d2f_pow2(D.tb ? SB[j + kk * BN] : SB[kk + j * BK], 0);
+      if constexpr (MODE == 0) {
+        const unsigned h = tf32_rn(f);
+        CB[kk * P + j] = h;
+        CB[(BK + kk) * P + j] = tf32_rn(f - __uint_as_float(h));
+      } else {
+        CB[kk * P + j] = __float_as_uint(f);
+      }
     }
   };
   const int nk = (D.k + BK - 1) / BK;
-  if (nk > 0) {
-    load(0);
-    store(0);
-  }
-  __syncthreads();
+  if (nk > 0) issue(0, 0);
   for (int ks = 0; ks < nk; ++ks) {
-    const int cur = ks & 1;
-    if (ks + 1 < nk) load((ks + 1) * BK);
-    const float* As = As0 + cur * BK * PA + wm * WTM;
-    const float* Bs = Bs0 + cur * BK * PB + wn * WTN;
+    if (ks + 1 < nk) {
+      issue((ks + 1) * BK, (ks + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // slice ks landed for every thread; the previous MMAs are done with Cv
+    convert(ks & 1);
+    __syncthreads();
+    const unsigned* Ah = Cv + wm * 64;
+    const unsigned* Bh = Cv + (MODE == 0 ? 2 : 1) * BK * P + wn * 32;
     if constexpr (MODE == 0) {
+      const unsigned* Al = Ah + BK * P;
+      const unsigned* Bl = Bh + BK * P;
 #pragma unroll
       for (int k8 = 0; k8 < BK; k8 += 8) {
-        unsigned bh[NW][2], bl[NW][2];
+        unsigned bh[4][2], bl[4][2];
 #pragma unroll
-        for (int j = 0; j < NW; ++j) {
-          split_tf32(Bs[(k8 + t) * PB + j * 8 + g], bh[j][0], bl[j][0]);
-          split_tf32(Bs[(k8 + t + 4) * PB + j * 8 + g], bh[j][1], bl[j][1]);
+        for (int j = 0; j < 4; ++j) {
+          bh[j][0] = Bh[(k8 + t) * P + j * 8 + g];
+          bh[j][1] = Bh[(k8 + t + 4) * P + j * 8 + g];
+          bl[j][0] = Bl[(k8 + t) * P + j * 8 + g];
+          bl[j][1] = Bl[(k8 + t + 4) * P + j * 8 + g];
         }
 #pragma unroll
-        for (int i = 0; i < MT; ++i) {
-          unsigned ah[4], al[4];
-          split_tf32(As[(k8 + t) * PA + i * 16 + g], ah[0], al[0]);
-          split_tf32(As[(k8 + t) * PA + i * 16 + g + 8], ah[1], al[1]);
-          split_tf32(As[(k8 + t + 4) * PA + i * 16 + g], ah[2], al[2]);
-          split_tf32(As[(k8 + t + 4) * PA + i * 16 + g + 8], ah[3], al[3]);
+        for (int i = 0; i < 4; ++i) {
+          const int m0 = i * 16 + g;
+          const unsigned ah[4] = {Ah[(k8 + t) * P + m0], Ah[(k8 + t) * P + m0 + 8], Ah[(k8 + t + 4) * P + m0],
+                                  Ah[(k8 + t + 4) * P + m0 + 8]};
+          const unsigned al[4] = {Al[(k8 + t) * P + m0], Al[(k8 + t) * P + m0 + 8], Al[(k8 + t + 4) * P + m0],
+                                  Al[(k8 + t + 4) * P + m0 + 8]};
 #pragma unroll
-          for (int j = 0; j < NW; ++j) {
+          for (int j = 0; j < 4; ++j) {
             mma_tf32(acc[i][j], al, bh[j]);
             mma_tf32(acc[i][j], ah, bl[j]);
             mma_tf32(acc[i][j], ah, bh[j]);
@@ -403,52 +433,48 @@ __global__ void __launch_bounds__(WM * WN * 32) k_gemm_tc(const GemmDesc* __rest
         }
       }
     } else {
+      const float* As = (const float*)Ah;
+      const float* Bs = (const float*)Bh;
+      unsigned b[4][2];
 #pragma unroll
-      for (int k16 = 0; k16 < BK; k16 += 16) {
-        unsigned b[NW][2];
+      for (int j = 0; j < 4; ++j) {
+        const float* bb = Bs + j * 8 + g;
+        b[j][0] = bf16x2(bb[(2 * t) * P], bb[(2 * t + 1) * P]);
+        b[j][1] = bf16x2(bb[(2 * t + 8) * P], bb[(2 * t + 9) * P]);
+      }
 #pragma unroll
-        for (int j = 0; j < NW; ++j) {
-          const float* bb = Bs + j * 8 + g;
-          b[j][0] = bf16x2(bb[(k16 + 2 * t) * PB], bb[(k16 + 2 * t + 1) * PB]);
-          b[j][1] = bf16x2(bb[(k16 + 2 * t + 8) * PB], bb[(k16 + 2 * t + 9) * PB]);
-        }
+      for (int i = 0; i < 4; ++i) {
+        const float* aa = As + i * 16 + g;
+        unsigned a[4];
+        a[0] = bf16x2(aa[(2 * t) * P], aa[(2 * t + 1) * P]);
+        a[1] = bf16x2(aa[(2 * t) * P + 8], aa[(2 * t + 1) * P + 8]);
+        a[2] = bf16x2(aa[(2 * t + 8) * P], aa[(2 * t + 9) * P]);
+        a[3] = bf16x2(aa[(2 * t + 8) * P + 8], aa[(2 * t + 9) * P + 8]);
 #pragma unroll
-        for (int i = 0; i < MT; ++i) {
-          const float* aa = As + i * 16 + g;
-          unsigned a[4];
-          a[0] = bf16x2(aa[(k16 + 2 * t) * PA], aa[(k16 + 2 * t + 1) * PA]);
-          a[1] = bf16x2(aa[(k16 + 2 * t) * PA + 8], aa[(k16 + 2 * t + 1) * PA + 8]);
-          a[2] = bf16x2(aa[(k16 + 2 * t + 8) * PA], aa[(k16 + 2 * t + 9) * PA]);
-          a[3] = bf16x2(aa[(k16 + 2 * t + 8) * PA + 8], aa[(k16 + 2 * t + 9) * PA + 8]);
-#pragma unroll
-          for (int j = 0; j < NW; ++j) mma_bf16(acc[i][j], a, b[j]);
-        }
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a, b[j]);
       }
     }
-    if (ks + 1 < nk) store(cur ^ 1);
-    __syncthreads();
   }
-  // epilogue: the tile through shared memory (column-major, ld PC), then whole
-  // column segments of C per warp
-  float* Cs = smf;
+  __syncthreads();  // every warp is done with the stages before the epilogue reuses them
+  float* Cs = (float*)tcsm;
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-      const int r = wm * WTM + i * 16 + g, c = wn * WTN + j * 8 + 2 * t;
-      Cs[c * PC + r] = acc[i][j][0];
-      Cs[(c + 1) * PC + r] = acc[i][j][1];
-      Cs[c * PC + r + 8] = acc[i][j][2];
-      Cs[(c + 1) * PC + r + 8] = acc[i][j][3];
+    for (int j = 0; j < 4; ++j) {
+      const int r = wm * 64 + i * 16 + g, c = wn * 32 + j * 8 + 2 * t;
+      Cs[c * kTcPC + r] = acc[i][j][0];
+      Cs[(c + 1) * kTcPC + r] = acc[i][j][1];
+      Cs[c * kTcPC + r + 8] = acc[i][j][2];
+      Cs[(c + 1) * kTcPC + r + 8] = acc[i][j][3];
     }
   __syncthreads();
   const float al = d2f_pow2(D.alpha, 0);
   const int bm = D.beta == 0.0 ? 0 : (D.beta == 1.0 ? 1 : 2);
   const int mr = min(BM, D.m - row0), nc = min(BN, D.n - col0);
-  for (int c = warp; c < nc; c += NT / 32) {
+  for (int c = warp; c < nc; c += 8) {
     double* o = D.C + row0 + (long)(col0 + c) * D.ldc;
     for (int r = lane; r < mr; r += 32) {
-      const double v = f2d_pow2(al * Cs[c * PC + r], 0);
+      const double v = f2d_pow2(al * Cs[c * kTcPC + r], 0);
       o[r] = bm == 0 ? v : (bm == 1 ? o[r] + v : v + D.beta * o[r]);
     }
   }

@@ -51,8 +51,9 @@ struct GemvDesc {
 };
 
 // One operation of the IFMM solve (Algorithm 2): for r in [0, rows)
-//   out[r] = beta * base[r] + alpha * sum_{c < ncols} M[r * ldm + c] * v(c),
-// v(c) = x[c] (xidx == nullptr) or x[xidx[c]].  M is row-major with ldm a
+//   out[o(r)] = beta * base[o(r)] + alpha * sum_{c < ncols} M[r * ldm + c] * v(c),
+// v(c) = x[c] (xidx == nullptr) or x[xidx[c]], o(r) = r (oidx == nullptr) or
+// oidx[r].  M is row-major with ldm a
 // multiple of 4 and 16-byte aligned rows: FP64, or FP32 in the reduced-precision
 // modes.  The vectors are FP64, or float pairs (hi, lo) in the reduced-precision
 // modes, where alpha is +-1 and beta 0 or 1.  lanes (a power of two <= 32) lanes
@@ -61,6 +62,7 @@ struct SolveOp {
   const void* M;
   const void* x;
   const int* xidx;
+  const int* oidx;
   void* out;
   const void* base;
   double alpha, beta;
@@ -124,6 +126,28 @@ struct IlTables {
   const int* newk;
   const double* const* T;
   const double* const* Tp;
+};
+
+// Level start (reading R5): every interaction-list block of the level in the
+// new bases, M2L_ab = T'_a K(c_a - c_b) T_b, with K the translation table
+// (343 offsets of rc x rc, column-major).  The entries (positions in the IL
+// CSR) are grouped by offset; chunk c covers ent[first, first + count), all
+// with offset `off`.  k[x]: new rank of node x; T[x] (rc x k[x], ld rc) and
+// Tp[x] (k[x] x rc, ld k[x]) its transforms.
+struct M2lChunk {
+  int off, first, count, pad;
+};
+struct M2lTables {
+  const int* ent;
+  const int* il_row;
+  const int* il;
+  double* const* far;
+  const int* capr;
+  const int* k;
+  const double* const* T;
+  const double* const* Tp;
+  const double* tab;
+  int rc, pad;
 };
 
 // Weight stack Z of one side of a recompression event of node q (reading R4 of

@@ -42,7 +42,8 @@ struct SolveLaunch {
 struct SolvePlan {
   void* V = nullptr;
   int64_t xlen = 0, vlen = 0;
-  void* stage_in = nullptr;  // tree-ordered input/output vector (level ell's segment of V)
+  void* stage_in = nullptr;   // tree-ordered input vector (level ell's segment of V)
+  void* stage_out = nullptr;  // tree-ordered output vector (nullptr: stage_in)
   bool pairs = false;
   std::vector<SolveLaunch> prog;
   cudaGraphExec_t graph = nullptr;
@@ -87,5 +88,9 @@ struct ifmm_fact {
 
 namespace ifmm {
 void build_solve_plan(ifmm_fact& F, cudaStream_t s);
+void capture_solve_plan(SolvePlan& P, const std::vector<std::vector<SolveOp>>& launches,
+                        const std::vector<std::vector<int64_t>>& xoff, const std::vector<std::vector<int64_t>>& ooff,
+                        const std::vector<int32_t>& idx_all);
+int solve_row_lanes(int ncols, int v);
 void run_solve(const ifmm_fact& F, cudaStream_t s);
 }  // namespace ifmm

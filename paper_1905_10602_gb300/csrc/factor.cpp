@@ -977,16 +977,50 @@ struct Factorizer {
     for (auto& ev : evs) W.r[ev.q] = ev.k;
     // M2L blocks T'_a K T_b; M2M = M2M_tab T; L2L = T' M2M_tab^T
     std::vector<GemmDesc> g1, g2;
-    std::vector<double*> tmp(LL.il.size());
-    for (int a = 0; a < nn; ++a)
-      for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
-        const int b = LL.il[e];
-        const int ka = evs[a].k, kb = evs[b].k;
-        if (!ka || !kb) continue;
-        tmp[e] = scratch.alloc((size_t)ka * rc);
-        g1.push_back(gmm(evs[a].Tp, ka, 0, m2l_tab + off_index(a, b) * rc2, rc, 0, tmp[e], ka, ka, rc, rc, 1.0, 0.0));
-        g2.push_back(gmm(tmp[e], ka, 0, evs[b].T, rc, 0, W.far[e], W.capr[a], ka, kb, rc, 1.0, 0.0));
+    if (rc <= 64) {
+      // on the device (k_m2l_init), the entries grouped by offset so that each
+      // translation block is staged once per chunk
+      std::vector<int> per(344, 0), ent;
+      std::vector<int> offs(LL.il.size(), -1);
+      for (int a = 0; a < nn; ++a)
+        for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+          const int b = LL.il[e];
+          const int ka = evs[a].k, kb = evs[b].k;
+          if (!ka || !kb) continue;
+          offs[e] = off_index(a, b);
+          per[offs[e] + 1]++;
+          cnt.gemm += 2.0 * ka * rc * rc + 2.0 * ka * kb * rc;
+        }
+      for (int o = 0; o < 343; ++o) per[o + 1] += per[o];
+      ent.assign(per[343], 0);
+      std::vector<int> fill(per.begin(), per.end() - 1);
+      for (size_t e = 0; e < offs.size(); ++e)
+        if (offs[e] >= 0) ent[fill[offs[e]]++] = (int)e;
+      std::vector<M2lChunk> chunks;
+      for (int o = 0; o < 343; ++o)
+        for (int f = per[o]; f < per[o + 1]; f += 64) chunks.push_back(M2lChunk{o, f, std::min(64, per[o + 1] - f), 0});
+      std::vector<int> kv(nn);
+      std::vector<const double*> tv(nn), tpv(nn);
+      for (int q = 0; q < nn; ++q) {
+        kv[q] = evs[q].k;
+        tv[q] = evs[q].T;
+        tpv[q] = evs[q].Tp;
       }
+      const M2lTables mt{st.push(ent), W.d_il_row, W.d_il, W.d_far, W.d_capr, st.push(kv), st.push(tv), st.push(tpv),
+                         m2l_tab, rc, 0};
+      launch_m2l_init(st, chunks, mt, prec);
+    } else {
+      std::vector<double*> tmp(LL.il.size());
+      for (int a = 0; a < nn; ++a)
+        for (int e = LL.il_ptr[a]; e < LL.il_ptr[a + 1]; ++e) {
+          const int b = LL.il[e];
+          const int ka = evs[a].k, kb = evs[b].k;
+          if (!ka || !kb) continue;
+          tmp[e] = scratch.alloc((size_t)ka * rc);
+          g1.push_back(gmm(evs[a].Tp, ka, 0, m2l_tab + off_index(a, b) * rc2, rc, 0, tmp[e], ka, ka, rc, rc, 1.0, 0.0));
+          g2.push_back(gmm(tmp[e], ka, 0, evs[b].T, rc, 0, W.far[e], W.capr[a], ka, kb, rc, 1.0, 0.0));
+        }
+    }
     if (kappa > 2)
       for (int q = 0; q < nn; ++q) {
         const int k = evs[q].k;

@@ -24,6 +24,14 @@ struct InterpDesc {
 };
 
 void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag);
+// Self block of A over the points idx[0..n) (tree order), column-major with ld n.
+struct BdBlockDesc {
+  double* dst;
+  const int* idx;
+  int n, pad;
+};
+void launch_bd_fill(DescStage& st, const std::vector<BdBlockDesc>& v, const double* pts, int N, double scale,
+                    double diag);
 void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p);
 void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale);
 void launch_m2m_table(cudaStream_t s, double* out, int p);
@@ -41,6 +49,8 @@ void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, dou
 void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info);
 // phase-B basis changes of the touched IL entries `list` (every rank <= md <= 64)
 void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec);
+// level-start M2L blocks T'_a K T_b of the entries grouped by offset (rc <= 64)
+void launch_m2l_init(DescStage& st, const std::vector<M2lChunk>& chunks, const M2lTables& t, int prec);
 // recompression weight stacks gathered on the device from the IL tables
 void launch_zgather(DescStage& st, const std::vector<ZGatherDesc>& v, const ZTables& t);
 // Schur-complement blocks of the eliminated nodes added into their near blocks

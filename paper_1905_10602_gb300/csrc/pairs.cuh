@@ -28,11 +28,12 @@ __device__ __forceinline__ df df_diff(df a, float bh, float bl) {
   const df s = df_two_sum(a.h, -bh);
   return {s.h, s.l + (a.l - bl)};
 }
-// d^2 for d = h + l: h^2 exactly as a pair (FMA), plus 2 h l (l^2 is below
-// the pair's precision)
+// d^2 for d = h + l: h^2 exactly as a pair (FMA), plus 2 h l + l^2.  The
+// difference of two close points is not renormalised (df_diff), so l can be
+// ~1e-3 of h there and l^2 is not negligible.
 __device__ __forceinline__ df df_sq(df d) {
   const float p = d.h * d.h;
-  return {p, fmaf(d.h, d.h, -p) + 2.f * d.h * d.l};
+  return {p, fmaf(d.h, d.h, -p) + fmaf(d.l, d.l, 2.f * d.h * d.l)};
 }
 __device__ __forceinline__ df df_sum3(df a, df b, df c) {
   const df s = df_two_sum(a.h, b.h);

@@ -234,35 +234,29 @@ void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   profiler().end(KK_COPY, st.stream, pe);
 }
 
-// Reduced-precision GEMMs above 32 x 32 on the tensor cores (k_gemm_tc):
-// 128 x 128 tiles when both sides exceed 64, else 64 x 64 tiles.
-template <int BM, int BN, int WM, int WN>
-static void gemm_tc_one(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
+// Large reduced-precision GEMMs on the tensor cores (k_gemm_tc, 128 x 128 tiles).
+static void launch_gemm_tc(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
   if (v.empty()) return;
   static thread_local std::vector<int> tp;
   tp.assign(v.size() + 1, 0);
   for (size_t i = 0; i < v.size(); ++i)
-    tp[i + 1] = tp[i] + (int)((long)((v[i].m + BM - 1) / BM) * ((v[i].n + BN - 1) / BN));
+    tp[i + 1] = tp[i] + (int)((long)((v[i].m + kTcBM - 1) / kTcBM) * ((v[i].n + kTcBN - 1) / kTcBN));
   const GemmDesc* d = st.push(v);
   const int* p = st.push(tp);
-  constexpr int smem = gemm_tc_smem_bytes<BM, BN>();
   static bool attr = false;  // set once per process (the attribute is per function)
   if (!attr) {
-    CK(cudaFuncSetAttribute(k_gemm_tc<BM, BN, WM, WN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CK(cudaFuncSetAttribute(k_gemm_tc<BM, BN, WM, WN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_tc_smem_bytes(0)));
+    CK(cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_tc_smem_bytes(1)));
     attr = true;
   }
   prof_batch_tag() = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_GEMM32, st.stream);
   if (prec == P16)
-    k_gemm_tc<BM, BN, WM, WN, 1><<<(unsigned)tp.back(), WM * WN * 32, smem, st.stream>>>(d, p, (int)v.size());
+    k_gemm_tc<1><<<(unsigned)tp.back(), 256, gemm_tc_smem_bytes(1), st.stream>>>(d, p, (int)v.size());
   else
-    k_gemm_tc<BM, BN, WM, WN, 0><<<(unsigned)tp.back(), WM * WN * 32, smem, st.stream>>>(d, p, (int)v.size());
+    k_gemm_tc<0><<<(unsigned)tp.back(), 256, gemm_tc_smem_bytes(0), st.stream>>>(d, p, (int)v.size());
   check_launch("k_gemm_tc");
   profiler().end(KK_GEMM32, st.stream, pe);
-}
-static void launch_gemm_tc(DescStage& st, const std::vector<GemmDesc>& v, int prec) {
-  gemm_tc_one<128, 128, 2, 4>(st, v, prec);
 }
 
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
@@ -824,6 +818,73 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
   profiler().end(kk, st.stream, pe);
 }
 
+// Level-start M2L blocks: one CTA per chunk of entries sharing an offset o, the
+// translation block K_o staged once in shared memory (arithmetic type TC); per
+// entry the CTA stages T_b and T'_a, forms W = K_o T_b (rc x kb) and then
+// M2L_ab = T'_a W.  Every rank at a level start is <= rc <= 64.
+template <typename TC>
+__global__ void __launch_bounds__(256) k_m2l_init(const M2lChunk* __restrict__ ch, int nch, M2lTables t) {
+  if ((int)blockIdx.x >= nch) return;
+  const M2lChunk C = ch[blockIdx.x];
+  const int rc = t.rc, tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ __align__(16) unsigned char msm[];
+  TC* K = (TC*)msm;       // rc x rc
+  TC* Tb = K + rc * rc;   // rc x kb, ld rc
+  TC* Tp = Tb + rc * rc;  // ka x rc, ld ka
+  TC* Wm = Tp + rc * rc;  // rc x kb, ld rc
+  const double* Kg = t.tab + (long)C.off * rc * rc;
+  for (int x = tid; x < rc * rc; x += nt) K[x] = ld_tc<TC>(Kg[x]);
+  for (int q = 0; q < C.count; ++q) {
+    const int e = t.ent[C.first + q];
+    const int a = t.il_row[e], b = t.il[e];
+    const int ka = t.k[a], kb = t.k[b];
+    if (!ka || !kb) continue;  // the same for every thread of the CTA
+    __syncthreads();           // K staged; the previous entry is done with Tb, Tp, Wm
+    const double* Tg = t.T[b];
+    const double* Pg = t.Tp[a];
+    for (int x = tid; x < rc * kb; x += nt) Tb[x] = ld_tc<TC>(Tg[x]);
+    for (int x = tid; x < ka * rc; x += nt) Tp[x] = ld_tc<TC>(Pg[x]);
+    __syncthreads();
+    for (int x = tid; x < rc * kb; x += nt) {
+      const int r = x % rc, j = x / rc;
+      TC acc = 0;
+      for (int k = 0; k < rc; ++k) acc += K[r + k * rc] * Tb[k + j * rc];
+      Wm[x] = acc;
+    }
+    __syncthreads();
+    double* M = t.far[e];
+    const long ld = t.capr[a];
+    for (int x = tid; x < ka * kb; x += nt) {
+      const int i = x % ka, j = x / ka;
+      TC acc = 0;
+      for (int r = 0; r < rc; ++r) acc += Tp[i + r * ka] * Wm[r + j * rc];
+      M[i + (long)j * ld] = st_tc<TC>(acc);
+    }
+  }
+}
+
+void launch_m2l_init(DescStage& st, const std::vector<M2lChunk>& chunks, const M2lTables& t, int prec) {
+  if (chunks.empty()) return;
+  IFMM_REQUIRE(t.rc <= 64, IFMM_EINVAL, "internal: level-start M2L kernel needs rc <= 64");
+  const M2lChunk* d = st.push(chunks);
+  const int kk = prec == P64 ? KK_GEMM64 : KK_GEMM32;
+  prof_batch_tag() = (long)chunks.size();
+  cudaEvent_t pe = profiler().begin(kk, st.stream);
+  static bool attr = false;  // once per process: both instantiations may need > 48 KB
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_m2l_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 8));
+    CK(cudaFuncSetAttribute(k_m2l_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 4));
+    attr = true;
+  }
+  const size_t smem = (size_t)4 * t.rc * t.rc * (prec == P64 ? 8 : 4);
+  if (prec == P64)
+    k_m2l_init<double><<<(unsigned)chunks.size(), 256, smem, st.stream>>>(d, (int)chunks.size(), t);
+  else
+    k_m2l_init<float><<<(unsigned)chunks.size(), 256, smem, st.stream>>>(d, (int)chunks.size(), t);
+  check_launch("k_m2l_init");
+  profiler().end(kk, st.stream, pe);
+}
+
 void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec) {
   if (list.empty()) return;
   IFMM_REQUIRE(md >= 1 && md <= 64, IFMM_EINVAL, "IL transform tile out of range");
@@ -932,6 +993,28 @@ __global__ void k_p2p(const P2pDesc* __restrict__ d, int nd, const double* __res
       v = scale / sqrt(dx * dx + dy * dy + dz * dz);
     }
     D.dst[a + (long)b * D.ld] = v;
+  }
+}
+
+// 32 x 32 tiles of the self blocks of the block-diagonal preconditioner
+__global__ void k_bd_fill(const BdBlockDesc* __restrict__ d, const int* __restrict__ tile_ptr, int nd,
+                          const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pz,
+                          double scale, double diag) {
+  const int di = find_desc(tile_ptr, nd, blockIdx.x);
+  const BdBlockDesc D = d[di];
+  const int local = blockIdx.x - tile_ptr[di];
+  const int tr = (D.n + 31) >> 5;
+  const int r0 = (local % tr) * 32, c0 = (local / tr) * 32;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int a = r0 + (e & 31), b = c0 + (e >> 5);
+    if (a >= D.n || b >= D.n) continue;
+    double v = diag;
+    if (a != b) {
+      const int i = D.idx[a], j = D.idx[b];
+      const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
+      v = scale / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    D.dst[a + (long)b * D.n] = v;
   }
 }
 
@@ -1158,12 +1241,13 @@ __global__ void __launch_bounds__(256) k_solve_rows(const SolveOp* __restrict__ 
       s = df_acc(s, oh, ol);
     }
     if (live && sub == 0) {
+      const int orow = O.oidx ? O.oidx[r] : r;
       if (O.alpha < 0.0) s = {-s.h, -s.l};
       if (O.beta != 0.0) {
-        const float2 b = ((const float2*)O.base)[r];
+        const float2 b = ((const float2*)O.base)[orow];
         s = df_acc(s, b.x, b.y);
       }
-      ((float2*)O.out)[r] = make_float2(s.h, s.l);
+      ((float2*)O.out)[orow] = make_float2(s.h, s.l);
     }
   } else {
     const double* X = (const double*)O.x;
@@ -1188,8 +1272,9 @@ __global__ void __launch_bounds__(256) k_solve_rows(const SolveOp* __restrict__ 
     double s = s0 + s1;
     for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (live && sub == 0) {
+      const int orow = O.oidx ? O.oidx[r] : r;
       const double v = O.alpha * s;
-      ((double*)O.out)[r] = O.beta == 0.0 ? v : O.beta * ((const double*)O.base)[r] + v;
+      ((double*)O.out)[orow] = O.beta == 0.0 ? v : O.beta * ((const double*)O.base)[orow] + v;
     }
   }
 }
@@ -1532,6 +1617,25 @@ void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts,
   profiler().count(KK_P2P, 1);
   k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
   check_launch("k_p2p");
+}
+
+void launch_bd_fill(DescStage& st, const std::vector<BdBlockDesc>& v, const double* pts, int N, double scale,
+                    double diag) {
+  if (v.empty()) return;
+  std::vector<int> tp(v.size() + 1, 0);
+  for (size_t i = 0; i < v.size(); ++i) {
+    const long t = (long)((v[i].n + 31) / 32) * ((v[i].n + 31) / 32);
+    IFMM_REQUIRE(tp[i] + t < (1L << 31), IFMM_EINVAL, "block-diagonal blocks too large");
+    tp[i + 1] = tp[i] + (int)t;
+  }
+  if (!tp.back()) return;
+  const BdBlockDesc* d = st.push(v);
+  const int* p = st.push(tp);
+  cudaEvent_t pe = profiler().begin(KK_P2P, st.stream);
+  k_bd_fill<<<(unsigned)tp.back(), 256, 0, st.stream>>>(d, p, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale,
+                                                        diag);
+  check_launch("k_bd_fill");
+  profiler().end(KK_P2P, st.stream, pe);
 }
 
 void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p) {

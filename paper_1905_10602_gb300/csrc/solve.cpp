@@ -21,12 +21,55 @@ namespace ifmm {
 
 // lanes sharing one row of ncols coefficients, v per 16-byte vector: enough
 // lanes that each takes about two vectors, at most a warp
-static int row_lanes(int ncols, int v) {
+int solve_row_lanes(int ncols, int v) {
   int g = 1;
   while (g < 32 && g * v * 2 < ncols) g *= 2;
   return g;
 }
 static int pad4(int x) { return (x + 3) & ~3; }
+
+// Uploads the launches of a solve program (op lists, with gather / scatter
+// index lists given as offsets into idx_all, -1 for none) and captures them
+// into the plan's CUDA graph.
+void capture_solve_plan(SolvePlan& P, const std::vector<std::vector<SolveOp>>& launches,
+                        const std::vector<std::vector<int64_t>>& xoff, const std::vector<std::vector<int64_t>>& ooff,
+                        const std::vector<int32_t>& idx_all) {
+  int32_t* dx = (int32_t*)P.mem.alloc_bytes(sizeof(int32_t) * std::max<size_t>(1, idx_all.size()));
+  if (!idx_all.empty()) CK(cudaMemcpy(dx, idx_all.data(), sizeof(int32_t) * idx_all.size(), cudaMemcpyHostToDevice));
+  std::vector<SolveOp> ops_all;
+  std::vector<int> wp_all;
+  std::vector<std::array<size_t, 3>> where;  // op offset, warp_ptr offset, warps
+  for (size_t li = 0; li < launches.size(); ++li) {
+    const size_t o0 = ops_all.size(), w0 = wp_all.size();
+    int warps = 0;
+    wp_all.push_back(0);
+    for (size_t k = 0; k < launches[li].size(); ++k) {
+      SolveOp o = launches[li][k];
+      if (xoff[li][k] >= 0) o.xidx = dx + xoff[li][k];
+      if (ooff[li][k] >= 0) o.oidx = dx + ooff[li][k];
+      warps += (o.rows + 32 / o.lanes - 1) / (32 / o.lanes);
+      ops_all.push_back(o);
+      wp_all.push_back(warps);
+    }
+    where.push_back({o0, w0, (size_t)warps});
+  }
+  SolveOp* dops = (SolveOp*)P.mem.alloc_bytes(sizeof(SolveOp) * std::max<size_t>(1, ops_all.size()));
+  int* dwp = (int*)P.mem.alloc_bytes(sizeof(int) * std::max<size_t>(1, wp_all.size()));
+  if (!ops_all.empty()) CK(cudaMemcpy(dops, ops_all.data(), sizeof(SolveOp) * ops_all.size(), cudaMemcpyHostToDevice));
+  if (!wp_all.empty()) CK(cudaMemcpy(dwp, wp_all.data(), sizeof(int) * wp_all.size(), cudaMemcpyHostToDevice));
+  P.prog.clear();
+  for (size_t li = 0; li < launches.size(); ++li)
+    P.prog.push_back(SolveLaunch{dops + where[li][0], dwp + where[li][1], (int)launches[li].size(), (int)where[li][2]});
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (auto& l : P.prog) launch_solve_ops(cs, l.ops, l.warp_ptr, l.nops, l.nwarps, P.pairs);
+  cudaGraph_t g;
+  CK(cudaStreamEndCapture(cs, &g));
+  CK(cudaGraphInstantiate(&P.graph, g, 0));
+  P.graph_def = g;
+  CK(cudaStreamDestroy(cs));
+}
 
 void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
   const ifmm_tree& T = *F.t;
@@ -101,6 +144,7 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
     o.M = M;
     o.x = x;
     o.xidx = nullptr;
+    o.oidx = nullptr;
     o.out = out;
     o.base = base_;
     o.alpha = alpha;
@@ -108,7 +152,7 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
     o.rows = rows;
     o.ncols = ncols;
     o.ldm = ldm;
-    o.lanes = row_lanes(ncols, vw);
+    o.lanes = solve_row_lanes(ncols, vw);
     return o;
   };
   std::vector<std::vector<int64_t>> launch_xidx;  // per launch: xidx offset per op (-1: none)
@@ -233,49 +277,12 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
     launch_pack(st, pk, P.pairs);
     CK(cudaStreamSynchronize(s));
   }
-  int32_t* dx = (int32_t*)P.mem.alloc_bytes(sizeof(int32_t) * std::max<size_t>(1, xidx_all.size()));
-  if (!xidx_all.empty())
-    CK(cudaMemcpy(dx, xidx_all.data(), sizeof(int32_t) * xidx_all.size(), cudaMemcpyHostToDevice));
-  size_t nops_all = 0, nptr_all = 0;
-  for (auto& l : launches) {
-    nops_all += l.size();
-    nptr_all += l.size() + 1;
-  }
-  std::vector<SolveOp> ops_all;
-  std::vector<int> wp_all;
-  ops_all.reserve(nops_all);
-  wp_all.reserve(nptr_all);
-  std::vector<std::array<size_t, 3>> where;  // op offset, warp_ptr offset, warps
-  for (size_t li = 0; li < launches.size(); ++li) {
-    const size_t o0 = ops_all.size(), w0 = wp_all.size();
-    int warps = 0;
-    wp_all.push_back(0);
-    for (size_t k = 0; k < launches[li].size(); ++k) {
-      SolveOp o = launches[li][k];
-      if (launch_xidx[li][k] >= 0) o.xidx = dx + launch_xidx[li][k];
-      warps += (o.rows + 32 / o.lanes - 1) / (32 / o.lanes);
-      ops_all.push_back(o);
-      wp_all.push_back(warps);
-    }
-    where.push_back({o0, w0, (size_t)warps});
-  }
-  SolveOp* dops = (SolveOp*)P.mem.alloc_bytes(sizeof(SolveOp) * std::max<size_t>(1, ops_all.size()));
-  int* dwp = (int*)P.mem.alloc_bytes(sizeof(int) * std::max<size_t>(1, wp_all.size()));
-  if (!ops_all.empty()) CK(cudaMemcpy(dops, ops_all.data(), sizeof(SolveOp) * ops_all.size(), cudaMemcpyHostToDevice));
-  if (!wp_all.empty()) CK(cudaMemcpy(dwp, wp_all.data(), sizeof(int) * wp_all.size(), cudaMemcpyHostToDevice));
-  P.prog.clear();
-  for (size_t li = 0; li < launches.size(); ++li)
-    P.prog.push_back(SolveLaunch{dops + where[li][0], dwp + where[li][1], (int)launches[li].size(), (int)where[li][2]});
+  std::vector<std::vector<int64_t>> no_oidx(launches.size());
+  for (size_t li = 0; li < launches.size(); ++li) no_oidx[li].assign(launches[li].size(), -1);
+  capture_solve_plan(P, launches, launch_xidx, no_oidx, xidx_all);
   P.stage_in = vp(base[ell]);
-  cudaStream_t cs;
-  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (auto& l : P.prog) launch_solve_ops(cs, l.ops, l.warp_ptr, l.nops, l.nwarps, P.pairs);
-  cudaGraph_t g;
-  CK(cudaStreamEndCapture(cs, &g));
-  CK(cudaGraphInstantiate(&P.graph, g, 0));
-  P.graph_def = g;
-  CK(cudaStreamDestroy(cs));
+  std::vector<SolveOp> ops_all;
+  for (auto& l : launches) ops_all.insert(ops_all.end(), l.begin(), l.end());
   F.stat("solve_launches", (double)P.prog.size());
   F.stat("solve_vector_len", (double)total);
   F.stat("bytes_solve", (double)P.mem.high);
@@ -310,10 +317,11 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
     profiler().end(KK_SOLVE_GRAPH, s, pe);
     profiler().count(KK_ALL, (long)P.prog.size());
   }
+  const void* res = P.stage_out ? P.stage_out : P.stage_in;
   if (P.pairs)
-    launch_pair_join(s, P.stage_in, out, N);
+    launch_pair_join(s, res, out, N);
   else
-    CK(cudaMemcpyAsync(out, P.stage_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(out, res, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
 }
 
 static std::mutex g_tune_mutex;

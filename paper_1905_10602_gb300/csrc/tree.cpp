@@ -281,14 +281,33 @@ ifmm_status ifmm_build_tree(const double* xyz, int64_t n, int depth, ifmm_tree**
   }
 }
 
-ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors) {
+// Levels below tau: one node per color, in node (scan) order -- the nodes are
+// eliminated one after the other, each with the whole GPU (matrix-parallel).
+static void sequential_coloring(LevelLists& L) {
+  L.color.resize(L.n);
+  L.group_ptr.resize(L.n + 1);
+  L.group.resize(L.n);
+  for (int i = 0; i < L.n; ++i) {
+    L.color[i] = i;
+    L.group_ptr[i] = i;
+    L.group[i] = i;
+  }
+  L.group_ptr[L.n] = L.n;
+}
+
+ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors) { return ifmm_color_levels(t, sigma, 2, ncolors); }
+
+ifmm_status ifmm_color_levels(ifmm_tree* t, int sigma, int tau, int32_t* ncolors) {
   try {
     IFMM_REQUIRE(t != nullptr, IFMM_EINVAL, "tree is NULL");
     IFMM_REQUIRE(sigma >= 3 && sigma <= 64, IFMM_EINVAL, "sigma must be in [3, 64] (sigma >= 3 keeps neighbour sets of a color disjoint)");
+    IFMM_REQUIRE(tau >= 2 && tau <= t->depth, IFMM_EINVAL, "tau must be in [2, depth]");
     for (int kappa = 0; kappa <= t->depth; ++kappa) {
       LevelLists& L = t->lv[kappa];
-      if (kappa >= 2) {
+      if (kappa >= tau) {
         greedy_coloring(L, sigma);
+      } else if (kappa >= 2) {
+        sequential_coloring(L);
       } else {
         L.color.assign(L.n, -1);
         L.group_ptr.assign(1, 0);
@@ -297,6 +316,7 @@ ifmm_status ifmm_color(ifmm_tree* t, int sigma, int32_t* ncolors) {
       if (ncolors) ncolors[kappa] = kappa >= 2 ? (int32_t)(L.group_ptr.size() - 1) : 0;
     }
     t->sigma = sigma;
+    t->tau = tau;
     return IFMM_OK;
   } catch (const Error& e) {
     set_last_error(e.what());

@@ -47,6 +47,7 @@ _vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.
 _sig = {
     "ifmm_build_tree": [_vp, _i64, ctypes.c_int, ctypes.POINTER(_vp)],
     "ifmm_color": [_vp, ctypes.c_int, _vp],
+    "ifmm_color_levels": [_vp, ctypes.c_int, ctypes.c_int, _vp],
     "ifmm_tree_query": [_vp, ctypes.c_int, ctypes.c_char_p, _vp, _i64, ctypes.POINTER(_i64)],
     "ifmm_factor": [_vp, ctypes.POINTER(Kernel), ctypes.POINTER(Opts), _vp, ctypes.POINTER(_vp)],
     "ifmm_solve": [_vp, _vp, _vp, ctypes.c_int, _vp],
@@ -65,6 +66,7 @@ _sig = {
     "ifmm_fact_stats": [_vp, _vp, _i64, ctypes.POINTER(_i64)],
     "ifmm_convert_check": [_vp, _i64, ctypes.c_int, _vp, _vp],
     "ifmm_probe_peak": [ctypes.c_int, ctypes.POINTER(_dbl)],
+    "ifmm_bd_factor": [_vp, ctypes.POINTER(Kernel), ctypes.c_int, _vp, ctypes.POINTER(_vp)],
     "ifmm_gemm_check": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _vp,
                         ctypes.c_int, _vp, ctypes.c_int, _dbl, _vp, ctypes.c_int],
 }
@@ -159,6 +161,13 @@ def ifmm_color(tree: Tree, sigma: int) -> np.ndarray:
     return out
 
 
+def ifmm_color_levels(tree: Tree, sigma: int, tau: int) -> np.ndarray:
+    """Coloring at sigma for levels tau..depth, one node per color below tau."""
+    out = np.zeros(tree.depth + 1, dtype=np.int32)
+    _check(lib.ifmm_color_levels(tree.h, sigma, tau, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
 def ifmm_tree_query(tree: Tree, level: int, what: str) -> np.ndarray:
     cnt = _i64()
     _check(lib.ifmm_tree_query(tree.h, level, what.encode(), None, 0, ctypes.byref(cnt)))
@@ -186,6 +195,14 @@ def ifmm_factor(tree: Tree, cheb_order: int, eps: float, kernel: Kernel | None =
     o.max_rank, o.seed = max_rank, seed
     h = ctypes.c_void_p()
     _check(lib.ifmm_factor(tree.h, ctypes.byref(k), ctypes.byref(o), stream or ctypes.c_void_p(0), ctypes.byref(h)))
+    return Fact(h, tree)
+
+
+def ifmm_bd_factor(tree: Tree, level: int, kernel: Kernel | None = None, stream=None) -> Fact:
+    """Block-diagonal preconditioner (BD / BDbot at `level`) as a factor handle."""
+    k = kernel if kernel is not None else default_kernel(tree.n)
+    h = ctypes.c_void_p()
+    _check(lib.ifmm_bd_factor(tree.h, ctypes.byref(k), level, stream or ctypes.c_void_p(0), ctypes.byref(h)))
     return Fact(h, tree)
 
 

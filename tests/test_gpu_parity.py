@@ -203,3 +203,26 @@ def test_bf16_differs_from_fp32():
     v16 = ifmm.ifmm_solve(ifmm.ifmm_factor(t, 3, 1e-6, precision="bf16"), b)
     d = _rel(v16, v32)
     assert 1e-5 < d < 5e-2, d
+
+
+@pytest.mark.parametrize("tau,sigma", [(3, 3), (4, 6)])
+def test_tau_switch_replay_parity(tau, sigma):
+    """Levels below tau eliminated one node at a time (Table 2's top level tau):
+    the GPU factor equals the oracle's with the same per-level order (singleton
+    groups below tau), ranks replayed, within 1e-9."""
+    pts = bumpy_sphere(3000, 5)
+    depth = 4
+    groups = None
+    from oracle.tree import Tree
+
+    tr = Tree(pts, depth)
+    groups = {k: [[i] for i in range(tr.levels[k].n)] for k in range(2, tau)}
+    o = IFMMOracle(pts, depth, 3, 1e-6, sigma, color_groups=groups).factor()
+    t = ifmm.ifmm_build_tree(pts, depth)
+    ifmm.ifmm_color_levels(t, sigma, tau)
+    rep = [list(k) + [v] for k, v in o.ranks().items()]
+    f = ifmm.ifmm_factor(t, 3, 1e-6, rank_mode="replay", replay=rep)
+    R = np.random.default_rng(3).standard_normal((2, len(pts)))
+    V = ifmm.ifmm_solve(f, R)
+    for k in range(2):
+        assert _rel(V[k], o.solve(R[k])) < 1e-9

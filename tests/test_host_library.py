@@ -80,3 +80,26 @@ def test_invalid_arguments_fail_cleanly():
         ifmm.ifmm_tree_query(t, 9, "cells")
     with pytest.raises(ifmm.IFMMError):
         ifmm.ifmm_factor(t, 3, 1e-6)  # not colored yet
+
+
+@pytest.mark.parametrize("tau", [2, 3, 4])
+def test_color_levels_sequential_below_tau(tau):
+    """Sec. 4.2, Table 2: levels below tau get one node per color in node order
+    (matrix-parallel), levels tau..depth the Algorithm 3 coloring."""
+    pts = bumpy_sphere(5000, 2)
+    a = ifmm.ifmm_build_tree(pts, 4)
+    b = ifmm.ifmm_build_tree(pts, 4)
+    na = ifmm.ifmm_color(a, 3)
+    nb = ifmm.ifmm_color_levels(b, 3, tau)
+    for lvl in range(2, 5):
+        n = len(ifmm.ifmm_tree_query(b, lvl, "parent"))
+        if lvl < tau:
+            assert nb[lvl] == n
+            assert list(ifmm.ifmm_tree_query(b, lvl, "group")) == list(range(n))
+            assert list(ifmm.ifmm_tree_query(b, lvl, "group_ptr")) == list(range(n + 1))
+        else:
+            assert nb[lvl] == na[lvl]
+            for what in ("color", "group", "group_ptr"):
+                assert np.array_equal(ifmm.ifmm_tree_query(a, lvl, what), ifmm.ifmm_tree_query(b, lvl, what))
+    with pytest.raises(ifmm.IFMMError):
+        ifmm.ifmm_color_levels(b, 3, 5)
