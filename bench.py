@@ -77,6 +77,14 @@ def parse():
     ap.add_argument("--tau", type=int, default=2, help="levels below tau one node per color (Table 2's top level)")
     ap.add_argument("--precond", default="ifmm", choices=["ifmm", "bd"], help="IFMM factor or BD block diagonal")
     ap.add_argument("--bd-level", type=int, default=0, help="BDbot level (0: the leaf level)")
+    ap.add_argument("--matvec", default="", choices=["", "df", "fp64", "fmm"],
+                    help="GMRES matvec: direct sum in float pairs (default in the reduced modes) or FP64, or the "
+                         "FMM representation A~ at the factor's Chebyshev order (GMRES then solves A~ x = b)")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="one factor + GMRES through the C ABI without PyTorch (for profilers); --n/--depth override "
+                         "the workload's size")
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -218,7 +226,8 @@ def config_of(w, precision, rank_mode, world, args=None):
     sigma = (args.sigma if args is not None and args.sigma else w.sigma)
     c = {"workload": f"{w.name}: {w.shape} N={w.n}, depth {w.depth}, Chebyshev order {w.cheb_order}, "
                      f"eps {w.eps}, sigma {sigma}, GMRES(30) to 1e-8",
-         "precision": precision, "rank_mode": rank_mode, "matvec": "fp64" if precision == "fp64" else "df",
+         "precision": precision, "rank_mode": rank_mode,
+         "matvec": (args.matvec if args is not None and args.matvec else ("fp64" if precision == "fp64" else "df")),
          "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"}
     if args is not None and (args.tau != 2 or args.precond != "ifmm" or args.sigma):
         c["sigma"] = sigma
@@ -295,6 +304,32 @@ def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1):
     return ents
 
 
+def ncu_case(args):
+    """One factorization + preconditioned GMRES through the C ABI, host arrays,
+    no PyTorch: the command the profiles' ncu captures run."""
+    from paper_1905_10602_gb300 import build as _build
+
+    _build.build()
+    from paper_1905_10602_gb300 import ifmm
+    from paper_1905_10602_gb300.workloads import WORKLOADS, point_source_rhs, surface
+
+    w = WORKLOADS[args.workload]
+    n, depth = args.n or w.n, args.depth or w.depth
+    pts = surface(w.shape, n, w.seed)
+    b = point_source_rhs(pts)
+    t = ifmm.ifmm_build_tree(pts, depth)
+    ifmm.ifmm_color_levels(t, args.sigma or w.sigma, args.tau)
+    arith = "fp64" if args.precision == "fp64" else "df"
+    k = ifmm.default_kernel(n, arith)
+    t0 = time.perf_counter()
+    f = ifmm.ifmm_factor(t, w.cheb_order, w.eps, kernel=k, precision=args.precision)
+    x, its, rel = ifmm.bem_gmres(t, b, precond=f, tol=1e-8, kernel=k)
+    st = ifmm.ifmm_fact_stats(f)
+    print(json.dumps({"case": f"{w.shape} N={n} depth {depth} {args.precision}", "seconds": time.perf_counter() - t0,
+                      "gmres_iterations": its, "relres": rel, "factor_s": st["time_factor"]}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,6 +337,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.ncu_case:
+        return ncu_case(args)
 
     import numpy as np
     import torch
@@ -347,7 +384,7 @@ def main():
                         "trained_on": "sphere2k, sphere32k, torus65k at eps 1e-4, 1e-6, 1e-8 (SVD-mode ranks)"}
 
     def step(prec, arith, rank_mode="svd", precond=args.precond):
-        k = ifmm.default_kernel(w.n, arith)
+        k = ifmm.default_kernel(w.n, arith, w.cheb_order if arith == "fmm" else 0)
         if precond == "bd":
             f = ifmm.ifmm_bd_factor(tree, args.bd_level or w.depth, kernel=k, stream=sptr)
         else:
@@ -369,7 +406,7 @@ def main():
         barrier()
         return e0.elapsed_time(e1) / steps, last
 
-    arith = "fp64" if args.precision == "fp64" else "df"
+    arith = args.matvec or ("fp64" if args.precision == "fp64" else "df")
     for _ in range(args.warmup):
         step(args.precision, arith, args.rank_mode)
     barrier()
@@ -451,7 +488,7 @@ def main():
         t0 = time.perf_counter()
         tr = ifmm.ifmm_build_tree(pts, w.depth)
         ifmm.ifmm_color_levels(tr, sigma, args.tau)
-        k = ifmm.default_kernel(w.n, arith)
+        k = ifmm.default_kernel(w.n, arith, w.cheb_order if arith == "fmm" else 0)
         if args.precond == "bd":
             f = ifmm.ifmm_bd_factor(tr, args.bd_level or w.depth, kernel=k)
         else:

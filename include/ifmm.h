@@ -54,16 +54,27 @@ typedef struct ifmm_fact ifmm_fact; /* opaque, library-owned: the factor's block
 /* Matrix entries: A_ij = scale/|x_i - x_j| for i != j, A_ii = diag.
  * The collocation BEM system of the paper's electrostatic example (Sec. 2) with
  * area weight 4pi/N has scale = 1/N and diag = 0.5 + 1/sqrt(N).
- * arith selects how bem_matvec / bem_gmres sum the direct interactions:
- * IFMM_ARITH_FP64 (plain FP64) or IFMM_ARITH_DF (pairs of floats with
- * error-free transformations: FP64-level accuracy, about 1e-13 relative per
- * interaction on well-separated points, at FP32 throughput). */
-enum { IFMM_ARITH_FP64 = 0, IFMM_ARITH_DF = 1 };
+ * arith selects how bem_matvec / bem_gmres apply the matrix:
+ *   IFMM_ARITH_FP64 - direct summation in plain FP64;
+ *   IFMM_ARITH_DF   - direct summation in pairs of floats with error-free
+ *                     transformations: FP64-level accuracy at FP32 throughput
+ *                     (about 1e-13 relative per interaction; for two points
+ *                     closer than ~1e-3 of the domain the 48-bit pair
+ *                     coordinates bound it at ~2^-46 R / r of the term);
+ *   IFMM_ARITH_FMM  - the FMM representation A~ (Sec. 2.2, Eq. (1); the
+ *                     paper's FMBEM matvec, Algorithm 4): P2M, M2M, M2L over
+ *                     the interaction lists, L2L, L2P and the near field, with
+ *                     the Chebyshev operators of order `order` (0: 4) that
+ *                     ifmm_factor uses, in FP64.  It equals A only to the
+ *                     interpolation error, and GMRES then solves A~ x = b.
+ *                     The operator tables are built on first use and cached
+ *                     on the tree. */
+enum { IFMM_ARITH_FP64 = 0, IFMM_ARITH_DF = 1, IFMM_ARITH_FMM = 2 };
 typedef struct {
   double scale;
   double diag;
   int arith;
-  int reserved;
+  int order; /* Chebyshev order of the FMM matvec (IFMM_ARITH_FMM), 0 = 4 */
 } ifmm_kernel;
 
 /* Arithmetic of the factorization outside the pivots (which are always FP64, as
@@ -209,7 +220,8 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
  *   - All calls share the one scratch array: calls that overlap on the GPU (on
  *     different streams, or from different threads) race and give wrong results.
  *     No part of the scratch needs clearing between calls.
- *   - k->arith selects FP64 or float-pair sums, as for bem_matvec. */
+ *   - k->arith selects FP64 or float-pair sums, as for bem_matvec; the FMM
+ *     matvec (IFMM_ARITH_FMM) needs its own tables and is refused (IFMM_EINVAL). */
 ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream);
 
 /* Rank predictor (the paper's Sec. 5.1 uses a randomized SVD at a prescribed

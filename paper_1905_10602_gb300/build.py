@@ -22,7 +22,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU_SOURCES = ["runtime.cu", "noalloc.cu", "mlp.cu", "probe.cu"]
-CPP_SOURCES = ["tree.cpp", "factor.cpp", "solve.cpp", "batch.cpp", "bd.cpp"]
+CPP_SOURCES = ["tree.cpp", "factor.cpp", "solve.cpp", "batch.cpp", "bd.cpp", "fmm.cpp"]
 
 
 def _run(cmd):

@@ -20,6 +20,8 @@ struct Error : std::runtime_error {
 void set_last_error(const std::string& msg);
 // loads the allocation-free matvec's module on device `dev` (noalloc.cu)
 void noalloc_prepare_device(int dev);
+struct FmmPlan;  // the FMM matvec's device structure of a tree (fmm.cpp)
+void fmm_free(FmmPlan* p);
 
 #define IFMM_REQUIRE(cond, code, msg)                 \
   do {                                                \
@@ -59,6 +61,7 @@ struct ifmm_tree {
   int matvec_block = 0;       // autotuned source tile of the float-pair matvec (0: not yet)
   std::vector<int32_t> matvec_block_v{0};
   int device = -1;
+  ifmm::FmmPlan* fmm = nullptr;  // cached by the first FMM matvec
   void ensure_device();
   ~ifmm_tree();
 };

@@ -112,7 +112,8 @@ struct SvdRtDesc {
 };
 
 // Interaction-list blocks of one level on the device, and the basis changes of
-// one color (phase B of a color, reading R7 of the oracle).  IL entry e is the
+// one color (the interaction-list updates of Algorithm 1 that Sec. 3.3 serializes
+// for sigma = 3, done as one pass after the color's eliminations).  IL entry e is the
 // block M2L_ab, a = il_row[e], b = il[e], stored at far[e] with ld capr[a];
 // rbefore[x] is node x's rank before the color, newk[x] its new rank (-1: not
 // re-based), T[x] (rbefore x newk, ld rbefore) and Tp[x] (newk x rbefore, ld
@@ -128,7 +129,8 @@ struct IlTables {
   const double* const* Tp;
 };
 
-// Level start (reading R5): every interaction-list block of the level in the
+// Level start (every node re-based before its level's eliminations, Sec. 2.3):
+// every interaction-list block of the level in the
 // new bases, M2L_ab = T'_a K(c_a - c_b) T_b, with K the translation table
 // (343 offsets of rc x rc, column-major).  The entries (positions in the IL
 // CSR) are grouped by offset; chunk c covers ent[first, first + count), all
@@ -150,8 +152,8 @@ struct M2lTables {
   int rc, pad;
 };
 
-// Weight stack Z of one side of a recompression event of node q (reading R4 of
-// the oracle): for l in IL_q with a nonzero rank, in IL order, the block M2L_lq
+// Weight stack Z of one side of a recompression event of node q (the far-field
+// operators the basis must keep representing, Sec. 2.3, Algorithm 1): for l in IL_q with a nonzero rank, in IL order, the block M2L_lq
 // (side 0) or M2L_ql^T (side 1), r_l rows each; then, when the level has a
 // parent (tail != 0), M2M_q (side 0) or L2L_q^T (side 1), rc rows.  Z has ld ldz.
 struct ZGatherDesc {
@@ -170,8 +172,8 @@ struct ZTables {
   int rc, tail;
 };
 
-// Schur-complement scatter of one eliminated node i (Algorithm 1, reading R2 of
-// the oracle): F (M x M, ld M) holds -L Pi^-1 U over i's neighbours in CSR
+// Schur-complement scatter of one eliminated node i (Algorithm 1's updates of
+// the neighbours' P2P / M2P / P2L / M2L blocks): F (M x M, ld M) holds -L Pi^-1 U over i's neighbours in CSR
 // order, each neighbour q owning dim(q) rows and columns (dim = r if q is
 // eliminated, else n); every block (q, q2) with q2 = q or q2 a neighbour of q
 // is added to the current near block of stage elim[q] + elim[q2] (ld n[q]).

@@ -92,5 +92,7 @@ void capture_solve_plan(SolvePlan& P, const std::vector<std::vector<SolveOp>>& l
                         const std::vector<std::vector<int64_t>>& xoff, const std::vector<std::vector<int64_t>>& ooff,
                         const std::vector<int32_t>& idx_all);
 int solve_row_lanes(int ncols, int v);
+FmmPlan* fmm_plan(ifmm_tree& T, int order, double scale, double diag, cudaStream_t s);
+void fmm_apply(const ifmm_tree& T, FmmPlan& P, const double* x, double* y, cudaStream_t s);
 void run_solve(const ifmm_fact& F, cudaStream_t s);
 }  // namespace ifmm

@@ -135,7 +135,8 @@ struct Counter {
   double total() const { return gemm + inv + qr + svd + lu; }
 };
 
-// One recompression event (reading R4 of the oracle, Sec. 5.1): new orthonormal
+// One recompression event (Algorithm 1's compression of the fill-ins at relative
+// accuracy eps, Sec. 5.1; weighted as in Sec. 2.3's re-basing): new orthonormal
 // row basis (P2M) and column basis (L2P) of a live node from the SVDs of the
 // weighted old basis stacked with the far fill-ins.
 struct Event {
@@ -878,7 +879,8 @@ struct Factorizer {
     const double h = 0.5 * T.side / (double)((int64_t)1 << kappa);
     m2l_tab = levelmem.alloc((size_t)343 * rc * rc);
     launch_m2l_table(s, m2l_tab, p, h, F.k.scale);
-    // initial recompression of every node (reading R5)
+    // initial recompression of every node (the leaf rank p^3 exceeds the
+    // points of a leaf, Sec. 2.3)
     std::vector<Event> evs;
     std::vector<double*> po, lo;
     std::vector<int> pld, lld;

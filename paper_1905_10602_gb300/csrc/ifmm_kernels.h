@@ -63,6 +63,18 @@ void launch_pack(DescStage& st, const std::vector<PackDesc>& v, bool fp32);
 // FP64 <-> float pairs (hi = nearest float, lo = nearest float of the rest)
 void launch_pair_split(cudaStream_t s, const double* in, void* out, int64_t n);
 void launch_pair_join(cudaStream_t s, const void* in, double* out, int64_t n);
+// FMM matvec stages (runtime.cu)
+void launch_fmm_p2m(cudaStream_t s, const double* S, const long* soff, const int* leaf_ptr, const double* x, double* M,
+                    int nleaf, int rc);
+void launch_fmm_m2m(cudaStream_t s, const int* child_ptr, const int* child, const int* ccells, const double* m2m,
+                    const double* Mc, double* Mp, int nparent, int rc);
+void launch_fmm_m2l(cudaStream_t s, const int* il_ptr, const int* il, const int* cells, const double* tab,
+                    const double* M, double* L, int n, int rc);
+void launch_fmm_l2l(cudaStream_t s, const int* parent, const int* cells, const double* m2m, const double* Lp,
+                    double* Lc, int n, int rc);
+void launch_fmm_l2p(cudaStream_t s, const double* S, const long* soff, const int* leaf_ptr, const int* nbr_ptr,
+                    const int* nbr, const double* L, const double* pts, int N, const double* x, double* y, int nleaf,
+                    int rc, double scale, double diag);
 const char* last_error();
 
 }  // namespace ifmm

@@ -171,6 +171,11 @@ extern "C" ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel*
     ifmm::set_last_error("bem_matvec_noalloc: NULL argument");
     return IFMM_EINVAL;
   }
+  if (k->arith != IFMM_ARITH_FP64 && k->arith != IFMM_ARITH_DF) {
+    ifmm::set_last_error("bem_matvec_noalloc: only the direct sums (IFMM_ARITH_FP64, IFMM_ARITH_DF) run without "
+                         "allocating");
+    return IFMM_EINVAL;
+  }
   if (t->N > NOALLOC_MAX_N) {
     ifmm::set_last_error("bem_matvec_noalloc: the tree has more points than the " +
                          std::to_string(NOALLOC_MAX_N) + " its fixed scratch holds; use bem_matvec");

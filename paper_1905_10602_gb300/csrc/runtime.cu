@@ -367,6 +367,13 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   });
   static int cl_ok[4] = {0, 0, 0, 0};  // per R = 1, 2, 4, 8: 0 unknown, 1 yes, -1 no
   static std::mutex cl_mu;
+  // IFMM_INV_FALLBACK_N=n (read once per process; tests) sends every block of
+  // at least n rows to the batched multi-CTA kernels
+  static const int fallback_n = [] {
+    const char* e = getenv("IFMM_INV_FALLBACK_N");
+    const long n = e ? atol(e) : 0;
+    return n >= 1 ? (int)std::min(n, 1L << 30) : 0;
+  }();
   int nbig = 0;
   for (auto& x : v) nbig += x.n > 32;
   int rwant = 1;
@@ -374,6 +381,10 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   std::vector<InvDesc> cls[3], ccl[4];
   size_t csm[4] = {16, 16, 16, 16};
   for (auto& x : v) {
+    if (fallback_n && x.n >= fallback_n) {
+      cls[2].push_back(x);
+      continue;
+    }
     if (x.n <= 32) {
       cls[0].push_back(x);
       continue;
@@ -1073,6 +1084,124 @@ __global__ void k_m2m_table(double* __restrict__ out, int p) {
     const double ux = sx + 0.5 * cheb_root(ka, p), uy = sy + 0.5 * cheb_root(kb, p), uz = sz + 0.5 * cheb_root(kc, p);
     T[e] = lagrange(ma, p, ux) * lagrange(mb, p, uy) * lagrange(mc, p, uz);
   }
+}
+
+// ---------------------------------------------------------------- FMM matvec
+// y = A~ x through the FMM representation (Sec. 2.2, Eq. (1)) with the
+// Chebyshev operators the factorization uses: P2M at the leaves, M2M up to
+// level 2, M2L over the interaction lists of levels 2..depth, L2L down, then
+// L2P plus the near field (A_ij for i, j in the same or adjacent leaves).  M
+// and L of a level are node-major (rc per node); S (rc x n per leaf, ld rc)
+// at soff[leaf].  FP64 throughout; a CTA per node, threads over the rc
+// coefficients (or the leaf's points).
+__device__ __forceinline__ int octant_of(const int* cells, int c) {
+  return (cells[3 * c] & 1) | ((cells[3 * c + 1] & 1) << 1) | ((cells[3 * c + 2] & 1) << 2);
+}
+__global__ void k_fmm_p2m(const double* __restrict__ S, const long* __restrict__ soff, const int* __restrict__ leaf_ptr,
+                          const double* __restrict__ x, double* __restrict__ M, int rc) {
+  const int leaf = blockIdx.x;
+  const int p0 = leaf_ptr[leaf], n = leaf_ptr[leaf + 1] - p0;
+  const double* Sl = S + soff[leaf];
+  for (int m = threadIdx.x; m < rc; m += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(Sl[m + (long)j * rc], x[p0 + j], acc);
+    M[(long)leaf * rc + m] = acc;
+  }
+}
+__global__ void k_fmm_m2m(const int* __restrict__ child_ptr, const int* __restrict__ child,
+                          const int* __restrict__ ccells, const double* __restrict__ m2m,
+                          const double* __restrict__ Mc, double* __restrict__ Mp, int rc) {
+  const int a = blockIdx.x;
+  const long r2 = (long)rc * rc;
+  for (int m = threadIdx.x; m < rc; m += blockDim.x) {
+    double acc = 0.0;
+    for (int x = child_ptr[a]; x < child_ptr[a + 1]; ++x) {
+      const int c = child[x];
+      const double* T = m2m + octant_of(ccells, c) * r2;
+      const double* v = Mc + (long)c * rc;
+      for (int k = 0; k < rc; ++k) acc = fma(T[m + (long)k * rc], v[k], acc);
+    }
+    Mp[(long)a * rc + m] = acc;
+  }
+}
+__global__ void k_fmm_m2l(const int* __restrict__ il_ptr, const int* __restrict__ il, const int* __restrict__ cells,
+                          const double* __restrict__ tab, const double* __restrict__ M, double* __restrict__ L,
+                          int rc) {
+  const int a = blockIdx.x;
+  const long r2 = (long)rc * rc;
+  const int ax = cells[3 * a], ay = cells[3 * a + 1], az = cells[3 * a + 2];
+  for (int m = threadIdx.x; m < rc; m += blockDim.x) {
+    double acc = 0.0;
+    for (int e = il_ptr[a]; e < il_ptr[a + 1]; ++e) {
+      const int b = il[e];
+      const int o = (az - cells[3 * b + 2] + 3) * 49 + (ay - cells[3 * b + 1] + 3) * 7 + (ax - cells[3 * b] + 3);
+      const double* K = tab + o * r2;
+      const double* v = M + (long)b * rc;
+      for (int k = 0; k < rc; ++k) acc = fma(K[m + (long)k * rc], v[k], acc);
+    }
+    L[(long)a * rc + m] = acc;
+  }
+}
+__global__ void k_fmm_l2l(const int* __restrict__ parent, const int* __restrict__ cells, const double* __restrict__ m2m,
+                          const double* __restrict__ Lp, double* __restrict__ Lc, int rc) {
+  const int c = blockIdx.x;
+  const long r2 = (long)rc * rc;
+  const double* T = m2m + octant_of(cells, c) * r2;  // L2L = M2M^T
+  const double* v = Lp + (long)parent[c] * rc;
+  for (int m = threadIdx.x; m < rc; m += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < rc; ++k) acc = fma(T[k + (long)m * rc], v[k], acc);
+    Lc[(long)c * rc + m] += acc;
+  }
+}
+__global__ void k_fmm_l2p(const double* __restrict__ S, const long* __restrict__ soff, const int* __restrict__ leaf_ptr,
+                          const int* __restrict__ nbr_ptr, const int* __restrict__ nbr, const double* __restrict__ L,
+                          const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pz,
+                          const double* __restrict__ x, double* __restrict__ y, int rc, double scale, double diag) {
+  const int leaf = blockIdx.x;
+  const int p0 = leaf_ptr[leaf], n = leaf_ptr[leaf + 1] - p0;
+  const double* Sl = S + soff[leaf];
+  const double* Ll = L + (long)leaf * rc;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int i = p0 + j;
+    double far = 0.0;
+    for (int m = 0; m < rc; ++m) far = fma(Sl[m + (long)j * rc], Ll[m], far);
+    const double xi = px[i], yi = py[i], zi = pz[i];
+    double near = 0.0;
+    for (int q = -1; q < nbr_ptr[leaf + 1] - nbr_ptr[leaf]; ++q) {
+      const int lq = q < 0 ? leaf : nbr[nbr_ptr[leaf] + q];
+      for (int s = leaf_ptr[lq]; s < leaf_ptr[lq + 1]; ++s) {
+        if (s == i) continue;
+        const double dx = xi - px[s], dy = yi - py[s], dz = zi - pz[s];
+        near = fma(x[s], rsqrt(dx * dx + dy * dy + dz * dz), near);
+      }
+    }
+    y[i] = far + scale * near + diag * x[i];
+  }
+}
+
+void launch_fmm_p2m(cudaStream_t s, const double* S, const long* soff, const int* leaf_ptr, const double* x, double* M,
+                    int nleaf, int rc) {
+  if (nleaf) k_fmm_p2m<<<nleaf, 64, 0, s>>>(S, soff, leaf_ptr, x, M, rc);
+}
+void launch_fmm_m2m(cudaStream_t s, const int* child_ptr, const int* child, const int* ccells, const double* m2m,
+                    const double* Mc, double* Mp, int nparent, int rc) {
+  if (nparent) k_fmm_m2m<<<nparent, 64, 0, s>>>(child_ptr, child, ccells, m2m, Mc, Mp, rc);
+}
+void launch_fmm_m2l(cudaStream_t s, const int* il_ptr, const int* il, const int* cells, const double* tab,
+                    const double* M, double* L, int n, int rc) {
+  if (n) k_fmm_m2l<<<n, 64, 0, s>>>(il_ptr, il, cells, tab, M, L, rc);
+}
+void launch_fmm_l2l(cudaStream_t s, const int* parent, const int* cells, const double* m2m, const double* Lp,
+                    double* Lc, int n, int rc) {
+  if (n) k_fmm_l2l<<<n, 64, 0, s>>>(parent, cells, m2m, Lp, Lc, rc);
+}
+void launch_fmm_l2p(cudaStream_t s, const double* S, const long* soff, const int* leaf_ptr, const int* nbr_ptr,
+                    const int* nbr, const double* L, const double* pts, int N, const double* x, double* y, int nleaf,
+                    int rc, double scale, double diag) {
+  if (nleaf)
+    k_fmm_l2p<<<nleaf, 64, 0, s>>>(S, soff, leaf_ptr, nbr_ptr, nbr, L, pts, pts + N, pts + 2 * (long)N, x, y, rc,
+                                   scale, diag);
 }
 
 // y = diag x + scale * sum_{j != i} x_j / |p_i - p_j|: a thread per target,

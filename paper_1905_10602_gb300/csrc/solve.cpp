@@ -371,6 +371,7 @@ void ifmm_tree::ensure_device() {
 }
 
 ifmm_tree::~ifmm_tree() {
+  fmm_free(fmm);
   if (d_pts) {
     registry().remove_range(d_pts, sizeof(double) * 3 * N);
     cudaFree(d_pts);
@@ -483,7 +484,10 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       src = c;
     }
     launch_gather_perm(s, src, t->d_perm, a, (int)N);
-    if (k->arith == IFMM_ARITH_DF) {
+    if (k->arith == IFMM_ARITH_FMM) {
+      FmmPlan* P = fmm_plan(*const_cast<ifmm_tree*>(t), k->order ? k->order : 4, k->scale, k->diag, s);
+      fmm_apply(*t, *P, a, b, s);
+    } else if (k->arith == IFMM_ARITH_DF) {
       float* q = (float*)V.get(N);
       launch_split_df(s, a, q, q + N, (int)N);
       ifmm_tree* tm = const_cast<ifmm_tree*>(t);
@@ -558,8 +562,13 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
     };
     const bool df_mv = k->arith == IFMM_ARITH_DF;
     float* qdf = df_mv ? (float*)Vm.get(N) : nullptr;
+    FmmPlan* fmm = k->arith == IFMM_ARITH_FMM
+                       ? fmm_plan(*const_cast<ifmm_tree*>(t), k->order ? k->order : 4, k->scale, k->diag, s)
+                       : nullptr;
     auto Amul = [&](const double* in, double* out) {
-      if (df_mv) {
+      if (fmm) {
+        fmm_apply(*t, *fmm, in, out, s);
+      } else if (df_mv) {
         launch_split_df(s, in, qdf, qdf + N, (int)N);
         ifmm_tree* tm = const_cast<ifmm_tree*>(t);
         if (!tm->matvec_block) {

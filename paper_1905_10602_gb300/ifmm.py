@@ -33,7 +33,7 @@ class IFMMError(RuntimeError):
 
 class Kernel(ctypes.Structure):
     _fields_ = [("scale", ctypes.c_double), ("diag", ctypes.c_double), ("arith", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("order", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -117,13 +117,14 @@ def _stream(x=None):
     return ctypes.c_void_p(0)
 
 
-ARITH = {"fp64": 0, "df": 1}
+ARITH = {"fp64": 0, "df": 1, "fmm": 2}
 
 
-def default_kernel(n, arith: str = "fp64"):
-    """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N); arith: matvec sums in
-    plain FP64 or in FP64-accurate float pairs ("df")."""
-    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n), ARITH[arith], 0)
+def default_kernel(n, arith: str = "fp64", order: int = 0):
+    """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N); arith: the matvec as a
+    direct sum in plain FP64 or in FP64-accurate float pairs ("df"), or the FMM
+    representation A~ at Chebyshev order `order` ("fmm", 0 = 4)."""
+    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n), ARITH[arith], order)
 
 
 class Tree:

@@ -3,7 +3,8 @@ the in-place tall reduction, a thread-block cluster per block (rows split over
 2-8 CTAs, exchanging through distributed shared memory), and the global-memory
 kernel.  On the small parity cases nearly every block takes the first two paths,
 so these tests lower the per-CTA shared-memory limit (IFMM_QR_CTA_LIMIT_KB, read
-once per process) in a child process; the factor must still reproduce the
+once per process) in a child process (and, for the pivot inverses, send large
+blocks to the batched multi-CTA Gauss-Jordan with IFMM_INV_FALLBACK_N); the factor must still reproduce the
 oracle's applied inverse to 1e-9 with its ranks replayed (FP64) and keep GMRES
 convergence in FP32.
 """
@@ -44,12 +45,13 @@ f32 = ifmm.ifmm_factor(t, 4, 1e-6, precision="fp32")
 x, its, rel = ifmm.bem_gmres(t, b, precond=f32, tol=1e-8, kernel=ifmm.default_kernel(len(pts), "df"))
 print(json.dumps({"err": err, "its": its, "rel": rel,
                   "cluster": prof.get("qr_cluster_fp64", (0, 0.0))[0],
-                  "global": prof.get("qr_global_fp64", (0, 0.0))[0]}))
+                  "global": prof.get("qr_global_fp64", (0, 0.0))[0],
+                  "gj_batched": prof.get("gauss_jordan_big", (0, 0.0))[0]}))
 """
 
 
-def _run(limit_kb):
-    env = dict(os.environ, IFMM_QR_CTA_LIMIT_KB=str(limit_kb))
+def _run(limit_kb, env_extra=None):
+    env = dict(os.environ, IFMM_QR_CTA_LIMIT_KB=str(limit_kb), **(env_extra or {}))
     out = subprocess.run([sys.executable, "-c", CHILD % {"root": ROOT}], capture_output=True, text=True, env=env,
                          timeout=900)
     assert out.returncode == 0, out.stderr[-3000:]
@@ -63,3 +65,21 @@ def test_qr_paths_replay_parity(limit_kb):
     assert r["rel"] <= 1e-8, r
     # the lowered limit sends blocks to the cluster kernel
     assert r["cluster"] > 0, r
+
+
+def test_qr_global_memory_path_replay_parity():
+    """At a 4 KB per-CTA limit even an 8-CTA cluster holds only 32 KB: the larger
+    blocks take the global-memory pivoted QR (k_qrcp)."""
+    r = _run(4)
+    assert r["err"] < 1e-9 and r["rel"] <= 1e-8, r
+    assert r["global"] > 0, r
+
+
+def test_gauss_jordan_multi_cta_path_replay_parity():
+    """IFMM_INV_FALLBACK_N sends every pivot block of >= 40 rows to the batched
+    multi-CTA Gauss-Jordan (k_gjb_*); the factor still matches the oracle."""
+    base = _run(220)
+    r = _run(220, {"IFMM_INV_FALLBACK_N": "40"})
+    assert r["err"] < 1e-9 and r["rel"] <= 1e-8, r
+    # beyond the level-1 inverse's own launches (the same in both runs)
+    assert r["gj_batched"] > base["gj_batched"], (base, r)
