@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--matvec", default="", choices=["", "df", "fp64", "fmm"],
                     help="GMRES matvec: direct sum in float pairs (default in the reduced modes) or FP64, or the "
                          "FMM representation A~ at the factor's Chebyshev order (GMRES then solves A~ x = b)")
+    ap.add_argument("--wavenumber", type=float, default=0.0,
+                    help="Helmholtz kernel e^{ikr}/(4 pi r) at this k (complex system, FP64 direct-sum matvec)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="one factor + GMRES through the C ABI without PyTorch (for profilers); --n/--depth override "
                          "the workload's size")
@@ -229,6 +231,8 @@ def config_of(w, precision, rank_mode, world, args=None):
          "precision": precision, "rank_mode": rank_mode,
          "matvec": (args.matvec if args is not None and args.matvec else ("fp64" if precision == "fp64" else "df")),
          "global_batch": world, "l2": "working set > L2 (factor of several GB written every step)"}
+    if args is not None and getattr(args, "wavenumber", 0.0):
+        c["kernel"] = f"Helmholtz e^(ikr)/(4 pi r), k = {args.wavenumber}"
     if args is not None and (args.tau != 2 or args.precond != "ifmm" or args.sigma):
         c["sigma"] = sigma
         c["tau"] = args.tau
@@ -253,7 +257,7 @@ def measured_peaks(ifmm):
     return out
 
 
-def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1):
+def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1, matvec=None):
     """One roofline entry per kernel class of the profiled step: counted work /
     CUDA-event time of the class on its launching stream, against the measured
     peak of the unit that bounds it."""
@@ -287,10 +291,11 @@ def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1):
     apps = its + 1  # preconditioner applications per GMRES solve (one per iteration, one for x)
     add("solve_graph", "a10 IFMM solve (preconditioner)", stats.get("solve_matrix_bytes", 0.0) * apps, "GB/s", "hbm",
         peaks["hbm_gbs"], "HBM copy bandwidth")
-    if precision == "fp64":
+    matvec = matvec or ("fp64" if precision == "fp64" else "df")
+    if matvec == "fp64":
         add("matvec", "a11 direct-sum matvec (FP64)", 20.0 * n * n * (its + 1), "TFLOP/s", "alu", peaks["fp64"],
             "FP64 FMA peak, ~20 flops per pair")
-    else:
+    elif matvec == "df":
         n_, ms = prof.get("matvec", (0, 0.0))
         if n_ and ms > 0:
             pairs = float(n) * n * n_ / steps_profiled
@@ -359,7 +364,14 @@ def main():
         return run_batch(args, rank, world, dist, ifmm, torch)
     w = WORKLOADS[args.workload]
     pts = w.points()
-    b_host = w.rhs(pts)
+    if args.wavenumber:
+        from paper_1905_10602_gb300.workloads import helmholtz_source_rhs
+
+        b_host = helmholtz_source_rhs(pts, args.wavenumber)
+        args.matvec = "fp64"
+        args.no_cpu = True
+    else:
+        b_host = w.rhs(pts)
     tree = ifmm.ifmm_build_tree(pts, w.depth)
     sigma = args.sigma or w.sigma
     ifmm.ifmm_color_levels(tree, sigma, args.tau)
@@ -383,8 +395,13 @@ def main():
         learned_info = {"training_s": time.perf_counter() - t0, "training_events": nev, "final_loss": loss,
                         "trained_on": "sphere2k, sphere32k, torus65k at eps 1e-4, 1e-6, 1e-8 (SVD-mode ranks)"}
 
+    def kernel_of(arith):
+        if args.wavenumber:
+            return ifmm.helmholtz_kernel(w.n, args.wavenumber)
+        return ifmm.default_kernel(w.n, arith, w.cheb_order if arith == "fmm" else 0)
+
     def step(prec, arith, rank_mode="svd", precond=args.precond):
-        k = ifmm.default_kernel(w.n, arith, w.cheb_order if arith == "fmm" else 0)
+        k = kernel_of(arith)
         if precond == "bd":
             f = ifmm.ifmm_bd_factor(tree, args.bd_level or w.depth, kernel=k, stream=sptr)
         else:
@@ -444,7 +461,8 @@ def main():
                 n1, m1 = n1 + n2, m1 + (m2 if sub.startswith("qr_global") else 0.0)
         if n1:
             prof[f"qr_{g}"] = (n1, m1)
-    phases = phase_rooflines(prof, pstats, peaks, args.precision if args.precond == "ifmm" else "fp64", w.n, pits)
+    phases = phase_rooflines(prof, pstats, peaks, args.precision if args.precond == "ifmm" else "fp64", w.n, pits,
+                             matvec=None if args.wavenumber else arith)
     top = max(phases, key=lambda e: e["ms_per_step"]) if phases else None
     roof = None
     if top is not None:
@@ -488,7 +506,7 @@ def main():
         t0 = time.perf_counter()
         tr = ifmm.ifmm_build_tree(pts, w.depth)
         ifmm.ifmm_color_levels(tr, sigma, args.tau)
-        k = ifmm.default_kernel(w.n, arith, w.cheb_order if arith == "fmm" else 0)
+        k = kernel_of(arith)
         if args.precond == "bd":
             f = ifmm.ifmm_bd_factor(tr, args.bd_level or w.depth, kernel=k)
         else:

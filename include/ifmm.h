@@ -74,8 +74,23 @@ typedef struct {
   double scale;
   double diag;
   int arith;
-  int order; /* Chebyshev order of the FMM matvec (IFMM_ARITH_FMM), 0 = 4 */
+  int order;         /* Chebyshev order of the FMM matvec (IFMM_ARITH_FMM), 0 = 4 */
+  double wavenumber; /* Helmholtz: k != 0 (see below); 0 = Laplace               */
+  double diag_im;    /* Helmholtz: imaginary part of A_ii                         */
 } ifmm_kernel;
+/* Helmholtz (the paper's acoustic BEM kernel, Sec. 4.1): with wavenumber k != 0
+ * the entries are A_ij = scale e^{ik|x_i - x_j|}/|x_i - x_j| and A_ii = diag +
+ * i diag_im, complex.  Every complex vector (right-hand sides, solutions; host or
+ * device) is then N pairs (real, imaginary) of doubles -- the memory layout of
+ * an array of N complex doubles -- and the factorization works on the real 2 x 2
+ * form [[Re z, -Im z], [Im z, Re z]] of every complex entry: two real unknowns
+ * per point, Chebyshev bases of 2 p^3 real columns, and every kernel of the
+ * real path unchanged (twice the real operations of native complex
+ * arithmetic).  A truncation that keeps k complex directions keeps 2k real ones
+ * (the singular values of the real form come in equal pairs), and the ranks
+ * reported and replayed are those real counts.  The matvec is the FP64 direct
+ * sum (arith IFMM_ARITH_FP64; the float-pair and FMM matvecs, BD and the
+ * allocation-free matvec are Laplace only and refuse k != 0 with IFMM_EINVAL). */
 
 /* Arithmetic of the factorization outside the pivots (which are always FP64, as
  * are the solve, GMRES and its residual):

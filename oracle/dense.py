@@ -24,7 +24,7 @@ from .operators import interp_matrix, kernel_block
 def fmm_matrix(tree, ops) -> np.ndarray:
     """Assemble A~ densely (user point order).  Meant for N <= a few thousand."""
     N, ell, p = tree.N, tree.depth, ops.p
-    At = np.zeros((N, N))
+    At = np.zeros((N, N), dtype=np.complex128 if getattr(ops, "k", 0.0) else np.float64)
     leaf = tree.levels[ell]
     # ancestors of each leaf per level
     anc = {ell: np.arange(leaf.n)}
@@ -45,7 +45,8 @@ def fmm_matrix(tree, ops) -> np.ndarray:
         for Q in range(leaf.n):
             cP, cQ = leaf.cells[P], leaf.cells[Q]
             if np.max(np.abs(cP - cQ)) <= 1:
-                At[np.ix_(idx[P], idx[Q])] = kernel_block(N, tree.pts[idx[P]], tree.pts[idx[Q]], same=(P == Q))
+                At[np.ix_(idx[P], idx[Q])] = kernel_block(N, tree.pts[idx[P]], tree.pts[idx[Q]], same=(P == Q),
+                                                          k=getattr(ops, "k", 0.0))
                 continue
             kappa = ell
             while True:

@@ -95,6 +95,12 @@ def _mm(fl: Flops, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     return A @ B
 
 
+def _h(A: np.ndarray) -> np.ndarray:
+    """Conjugate transpose (the transpose for real data): the adjoint an
+    orthonormal basis is inverted by."""
+    return A.conj().T
+
+
 def kept_count(s: np.ndarray, shape, eps: float) -> int:
     """Number of singular values kept at relative error eps (reading R4)."""
     if len(s) == 0 or s[0] <= 0.0:
@@ -147,11 +153,11 @@ def rebase(fl: Flops, Zrow: list, Zcol: list, P2M_old, L2P_old, Frows: list, Fco
     if Zcol:
         Zc = np.hstack(Zcol)
         fl.qr(*Zc.shape)
-        Rc = np.linalg.qr(Zc.T, mode="r")
+        Rc = np.linalg.qr(_h(Zc), mode="r")
     else:
         Rc = np.zeros((0, r_old))
     Grow = np.vstack([_mm(fl, Rr, P2M_old)] + list(Frows))
-    Gcol = np.hstack([_mm(fl, L2P_old, Rc.T)] + list(Fcols))
+    Gcol = np.hstack([_mm(fl, L2P_old, _h(Rc))] + list(Fcols))
     if Grow.size:
         fl.svd(*Grow.shape)
         _, s_r, Vt = np.linalg.svd(Grow, full_matrices=False)
@@ -165,8 +171,8 @@ def rebase(fl: Flops, Zrow: list, Zcol: list, P2M_old, L2P_old, Frows: list, Fco
     k = policy.choose(key, s_r, Grow.shape, s_c, Gcol.shape)
     P2M_new = np.ascontiguousarray(Vt[:k])
     L2P_new = np.ascontiguousarray(U[:, :k])
-    T = _mm(fl, P2M_old, P2M_new.T)
-    Tp = _mm(fl, L2P_new.T, L2P_old)
+    T = _mm(fl, P2M_old, _h(P2M_new))
+    Tp = _mm(fl, _h(L2P_new), L2P_old)
     return P2M_new, L2P_new, T, Tp
 
 
@@ -185,9 +191,9 @@ class LevelFactor:
 class IFMMOracle:
     """IFMM factorization (Algorithm 1 with colors, Sec. 3) and solve (Algorithm 2)."""
 
-    def __init__(self, pts, depth, cheb_order, eps, sigma=6, rank_replay=None, color_groups=None):
+    def __init__(self, pts, depth, cheb_order, eps, sigma=6, rank_replay=None, color_groups=None, wavenumber=0.0):
         self.tree = Tree(pts, depth)
-        self.ops = Operators(self.tree, cheb_order)
+        self.ops = Operators(self.tree, cheb_order, wavenumber)
         self.eps = eps
         self.sigma = sigma
         self.flops = Flops()
@@ -336,9 +342,9 @@ class IFMMOracle:
         for (a, b, F) in fills_far:
             C = F
             if a not in S["elim"]:
-                C = _mm(fl, S["L2P"][a].T, C)
+                C = _mm(fl, _h(S["L2P"][a]), C)
             if b not in S["elim"]:
-                C = _mm(fl, C, S["P2M"][b].T)
+                C = _mm(fl, C, _h(S["P2M"][b]))
             far[(a, b)] = far[(a, b)] + C
 
     def _block_R_y(self, S, L, a, b):
@@ -379,7 +385,9 @@ class IFMMOracle:
         dense top solve, backward (downward, colors descending)."""
         T = self.tree
         ell = T.depth
-        bt = np.asarray(b, dtype=np.float64)
+        bt = np.asarray(b)
+        if not np.iscomplexobj(bt):
+            bt = bt.astype(np.float64)
         rhs_x = {}
         leaf = T.levels[ell]
         for i in range(leaf.n):
@@ -434,7 +442,7 @@ class IFMMOracle:
                         off += rc
             else:
                 x_leaf = x
-        out = np.empty(T.N)
+        out = np.empty(T.N, dtype=np.result_type(bt, *[v.dtype for v in x_leaf.values()]))
         for i in range(leaf.n):
             out[T.leaf_points(i)] = x_leaf[i]
         return out

@@ -9,6 +9,13 @@ equal area weights 4pi/N,
 the electrostatic example of Sec. 2 (Coulomb interaction, Eq. (1) system Ax=b),
 with a second-kind 0.5 on the diagonal and 1/sqrt(N) for the self panel.
 
+The Helmholtz variant (the paper's acoustic BEM, Sec. 4.1): with wavenumber k
+the kernel is e^{ik|x-y|}/(4pi|x-y|), so
+    A_ij = e^{ik r_ij} / (N r_ij)   (i != j),
+    A_ii = 0.5 + sin(k rho)/(2k) + i (1 - cos(k rho))/(2k),   rho = 2/sqrt(N),
+the self term being the kernel integrated over a disk of area 4pi/N (radius
+rho); k -> 0 gives the Laplace entries above.
+
 The FMM operators (Sec. 2.2 lists P2P, P2M, L2P, M2M, M2L, L2L) come from
 Chebyshev interpolation, the black-box FMM the paper names as an admissible
 choice (Sec. 4.2):
@@ -28,24 +35,31 @@ import math
 import numpy as np
 
 
-def bem_diag(N: int) -> float:
-    return 0.5 + 1.0 / math.sqrt(N)
+def bem_diag(N: int, k: float = 0.0):
+    """The diagonal entry: 0.5 plus the kernel integrated over the point's panel (a
+    disk of area 4pi/N, radius rho = 2/sqrt(N)): rho/2 for Laplace, and
+    (e^{ik rho} - 1)/(2ik) for Helmholtz."""
+    rho = 2.0 / math.sqrt(N)
+    if k == 0.0:
+        return 0.5 + 0.5 * rho
+    return 0.5 + math.sin(k * rho) / (2.0 * k) + 1j * (1.0 - math.cos(k * rho)) / (2.0 * k)
 
 
-def kernel_block(N: int, X: np.ndarray, Y: np.ndarray, same: bool = False) -> np.ndarray:
-    """[1/(N|x_i - y_j|)]; with same=True the diagonal gets 0.5 + 1/sqrt(N)."""
+def kernel_block(N: int, X: np.ndarray, Y: np.ndarray, same: bool = False, k: float = 0.0) -> np.ndarray:
+    """[e^{ik|x_i - y_j|}/(N|x_i - y_j|)] (k = 0: 1/(N|x_i - y_j|)); with same=True the
+    diagonal gets bem_diag(N, k)."""
     d = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(axis=2))
     if same:
         np.fill_diagonal(d, 1.0)
-        K = 1.0 / (N * d)
-        np.fill_diagonal(K, bem_diag(N))
-        return K
-    return 1.0 / (N * d)
+    K = 1.0 / (N * d) if k == 0.0 else np.exp(1j * k * d) / (N * d)
+    if same:
+        np.fill_diagonal(K, bem_diag(N, k))
+    return K
 
 
-def dense_matrix(pts: np.ndarray) -> np.ndarray:
-    """The full N x N BEM matrix A (user point order)."""
-    return kernel_block(len(pts), pts, pts, same=True)
+def dense_matrix(pts: np.ndarray, k: float = 0.0) -> np.ndarray:
+    """The full N x N BEM matrix A (user point order); complex for k != 0."""
+    return kernel_block(len(pts), pts, pts, same=True, k=k)
 
 
 def cheb_roots(p: int) -> np.ndarray:
@@ -85,11 +99,12 @@ def cheb_nodes(center: np.ndarray, halfwidth: float, p: int) -> np.ndarray:
 class Operators:
     """FMM operators of a tree for the BEM matrix, Chebyshev order p."""
 
-    def __init__(self, tree, p: int):
+    def __init__(self, tree, p: int, k: float = 0.0):
         self.tree = tree
         self.p = p
         self.r = p ** 3
         self.N = tree.N
+        self.k = k  # Helmholtz wavenumber (0: Laplace)
 
     def leaf_points(self, i: int) -> np.ndarray:
         return self.tree.pts[self.tree.leaf_points(i)]
@@ -97,7 +112,7 @@ class Operators:
     def p2p(self, i: int, j: int) -> np.ndarray:
         """Near-field block between leaves i (rows) and j (columns)."""
         X, Y = self.leaf_points(i), self.leaf_points(j)
-        return kernel_block(self.N, X, Y, same=(i == j))
+        return kernel_block(self.N, X, Y, same=(i == j), k=self.k)
 
     def p2m_leaf(self, i: int) -> np.ndarray:
         d = self.tree.depth
@@ -108,7 +123,7 @@ class Operators:
         h = self.tree.cell_halfwidth(kappa)
         Xa = cheb_nodes(self.tree.cell_center(kappa, a), h, self.p)
         Xb = cheb_nodes(self.tree.cell_center(kappa, b), h, self.p)
-        return kernel_block(self.N, Xa, Xb)
+        return kernel_block(self.N, Xa, Xb, k=self.k)
 
     def m2m(self, kappa: int, c: int) -> np.ndarray:
         """Child c (level kappa) -> its parent: [S_parent(child node k, parent node m)]."""

@@ -137,6 +137,7 @@ extern "C" ifmm_status ifmm_bd_factor(const ifmm_tree* t, const ifmm_kernel* k, 
   try {
     IFMM_REQUIRE(t && k && out, IFMM_EINVAL, "NULL argument");
     IFMM_REQUIRE(level >= 0 && level <= t->depth, IFMM_EINVAL, "level must be in [0, depth]");
+    IFMM_REQUIRE(k->wavenumber == 0.0, IFMM_EINVAL, "the block-diagonal preconditioner is Laplace only");
     const_cast<ifmm_tree*>(t)->ensure_device();
     F = new ifmm_fact();
     F->t = t;

@@ -232,7 +232,7 @@ struct Factorizer {
     st.stream = s;
     p = F.p;
     rc = F.rc;
-    maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256;
+    maxrank = F.o.max_rank > 0 ? F.o.max_rank : 256 * kernel_dof(F.k);
     prec = F.o.precision == IFMM_PREC_FP64 ? P64 : P32;
     gprec = F.o.precision == IFMM_PREC_BF16 ? P16 : prec;
     if (F.o.rank_mode == IFMM_RANK_LEARNED) {
@@ -676,7 +676,7 @@ struct Factorizer {
     const int nn = LL.n;
     W.n.assign(nn, 0);
     if (!child) {
-      for (int i = 0; i < nn; ++i) W.n[i] = T.leaf_ptr[i + 1] - T.leaf_ptr[i];
+      for (int i = 0; i < nn; ++i) W.n[i] = kernel_dof(F.k) * (T.leaf_ptr[i + 1] - T.leaf_ptr[i]);
     } else {
       child->choff.assign(child->nn, 0);
       for (int a = 0; a < nn; ++a) {
@@ -813,9 +813,9 @@ struct Factorizer {
           P2pDesc d;
           d.dst = W.nb[0][W.slot_ptr[i] + k];
           d.i0 = T.leaf_ptr[i];
-          d.ni = W.n[i];
+          d.ni = T.leaf_ptr[i + 1] - T.leaf_ptr[i];
           d.j0 = T.leaf_ptr[q];
-          d.nj = W.n[q];
+          d.nj = T.leaf_ptr[q + 1] - T.leaf_ptr[q];
           d.ld = W.n[i];
           d.same = (q == i);
           pp.push_back(d);
@@ -827,14 +827,14 @@ struct Factorizer {
         id.cz = T.origin[2] + (LL.cells[3 * i + 2] + 0.5) * 2 * h;
         id.h = h;
         id.p0 = T.leaf_ptr[i];
-        id.n = W.n[i];
+        id.n = T.leaf_ptr[i + 1] - T.leaf_ptr[i];
         id.ld = rc;
         id.pad = 0;
         ip.push_back(id);
         ct.push_back(cpy(P2M0[i], rc, L2P0[i], W.n[i], W.n[i], rc, 1.0, 0.0, 1));
       }
-      launch_p2p(st, pp, T.d_pts, (int)T.N, F.k.scale, F.k.diag);
-      launch_interp(st, ip, T.d_pts, (int)T.N, p);
+      launch_p2p(st, pp, T.d_pts, (int)T.N, F.k);
+      launch_interp(st, ip, T.d_pts, (int)T.N, p, kernel_dof(F.k));
       launch_copy(st, ct);
     } else {
       std::vector<CopyDesc> cc;
@@ -878,7 +878,7 @@ struct Factorizer {
     // M2L translation table of this level
     const double h = 0.5 * T.side / (double)((int64_t)1 << kappa);
     m2l_tab = levelmem.alloc((size_t)343 * rc * rc);
-    launch_m2l_table(s, m2l_tab, p, h, F.k.scale);
+    launch_m2l_table(s, m2l_tab, p, h, F.k);
     // initial recompression of every node (the leaf rank p^3 exceeds the
     // points of a leaf, Sec. 2.3)
     std::vector<Event> evs;
@@ -1472,7 +1472,7 @@ struct Factorizer {
     const int ell = T.depth;
     F.lv.assign(ell + 1, LevelFactor());
     m2m_tab = F.persist.alloc((size_t)8 * rc * rc);
-    launch_m2m_table(s, m2m_tab, p);
+    launch_m2m_table(s, m2m_tab, p, kernel_dof(F.k));
     std::unique_ptr<Work> prev;
     auto t0 = std::chrono::steady_clock::now();
     for (int kappa = ell; kappa >= 2; --kappa) {
@@ -1577,7 +1577,9 @@ ifmm_status ifmm_factor(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_opt
     F->k = *k;
     F->o = *o;
     F->p = o->cheb_order;
-    F->rc = o->cheb_order * o->cheb_order * o->cheb_order;
+    F->rc = kernel_dof(*k) * o->cheb_order * o->cheb_order * o->cheb_order;
+    IFMM_REQUIRE(k->wavenumber == 0.0 || k->arith == IFMM_ARITH_FP64, IFMM_EINVAL,
+                 "the Helmholtz kernel takes the FP64 direct-sum matvec (arith IFMM_ARITH_FP64)");
     {
       Factorizer fz(*F, (cudaStream_t)stream);
       fz.run();

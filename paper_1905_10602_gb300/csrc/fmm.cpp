@@ -79,13 +79,13 @@ FmmPlan* fmm_plan(ifmm_tree& T, int order, double scale, double diag, cudaStream
       d.pad = 0;
       if (d.n) ip.push_back(d);
     }
-    launch_interp(st, ip, T.d_pts, (int)T.N, order);
+    launch_interp(st, ip, T.d_pts, (int)T.N, order, 1);
     P->soff = up(P->mem, soff, s);
     P->leaf_ptr = up(P->mem, T.leaf_ptr, s);
     P->nbr_ptr = up(P->mem, LL.nbr_ptr, s);
     P->nbr = up(P->mem, LL.nbr, s);
     P->m2m = P->mem.alloc((size_t)8 * rc * rc);
-    launch_m2m_table(s, P->m2m, order);
+    launch_m2m_table(s, P->m2m, order, 1);
     P->lv.assign(ell + 1, FmmPlan::Lev());
     for (int kappa = 2; kappa <= ell; ++kappa) {
       const LevelLists& L = T.lv[kappa];
@@ -98,7 +98,10 @@ FmmPlan* fmm_plan(ifmm_tree& T, int order, double scale, double diag, cudaStream
       V.child_ptr = up(P->mem, L.child_ptr, s);
       V.child = up(P->mem, L.child, s);
       V.tab = P->mem.alloc((size_t)343 * rc * rc);
-      launch_m2l_table(s, V.tab, order, 0.5 * T.side / (double)((int64_t)1 << kappa), scale);
+      ifmm_kernel kk{};
+      kk.scale = scale;
+      kk.diag = diag;
+      launch_m2l_table(s, V.tab, order, 0.5 * T.side / (double)((int64_t)1 << kappa), kk);
       V.M = P->mem.alloc((size_t)std::max(1, L.n) * rc);
       V.L = P->mem.alloc((size_t)std::max(1, L.n) * rc);
     }

@@ -23,7 +23,9 @@ struct InterpDesc {
   int p0, n, ld, pad;
 };
 
-void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag);
+// entries per point: 2 (real and imaginary part) for the Helmholtz kernel, else 1
+inline int kernel_dof(const ifmm_kernel& k) { return k.wavenumber != 0.0 ? 2 : 1; }
+void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, const ifmm_kernel& k);
 // Self block of A over the points idx[0..n) (tree order), column-major with ld n.
 struct BdBlockDesc {
   double* dst;
@@ -32,10 +34,10 @@ struct BdBlockDesc {
 };
 void launch_bd_fill(DescStage& st, const std::vector<BdBlockDesc>& v, const double* pts, int N, double scale,
                     double diag);
-void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p);
-void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale);
-void launch_m2m_table(cudaStream_t s, double* out, int p);
-void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag);
+void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p, int dof);
+void launch_m2l_table(cudaStream_t s, double* out, int p, double h, const ifmm_kernel& k);
+void launch_m2m_table(cudaStream_t s, double* out, int p, int dof);
+void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, const ifmm_kernel& k);
 void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n);
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
                       int N, double scale, double diag, int bs);
@@ -44,8 +46,8 @@ int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, con
 void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::vector<const double*>& terms,
                      const std::vector<int>& first, int r);
 void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta);
-void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
-void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n);
+void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n, int dof = 1);
+void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n, int dof = 1);
 void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, double* d_work, int* d_info);
 // phase-B basis changes of the touched IL entries `list` (every rank <= md <= 64)
 void launch_il_transform(DescStage& st, const std::vector<int>& list, const IlTables& t, int md, int prec);

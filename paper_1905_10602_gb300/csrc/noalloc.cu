@@ -171,9 +171,9 @@ extern "C" ifmm_status bem_matvec_noalloc(const ifmm_tree* t, const ifmm_kernel*
     ifmm::set_last_error("bem_matvec_noalloc: NULL argument");
     return IFMM_EINVAL;
   }
-  if (k->arith != IFMM_ARITH_FP64 && k->arith != IFMM_ARITH_DF) {
-    ifmm::set_last_error("bem_matvec_noalloc: only the direct sums (IFMM_ARITH_FP64, IFMM_ARITH_DF) run without "
-                         "allocating");
+  if ((k->arith != IFMM_ARITH_FP64 && k->arith != IFMM_ARITH_DF) || k->wavenumber != 0.0) {
+    ifmm::set_last_error("bem_matvec_noalloc: only the Laplace direct sums (IFMM_ARITH_FP64, IFMM_ARITH_DF) run "
+                         "without allocating");
     return IFMM_EINVAL;
   }
   if (t->N > NOALLOC_MAX_N) {

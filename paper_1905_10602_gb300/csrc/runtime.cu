@@ -987,23 +987,41 @@ __device__ __forceinline__ double lagrange(int a, int p, double u) {
   return v;
 }
 
-// Near-field blocks: A_ij = scale/|x_i - x_j|, A_ii = diag (same leaf).
+// Near-field blocks: A_ij = scale/|x_i - x_j|, A_ii = diag (same leaf).  With
+// dof = 2 (Helmholtz, wavenumber k) the entry is z = scale e^{ik r}/r (A_ii =
+// diag + i diag_im) in the real 2 x 2 form [[Re z, -Im z], [Im z, Re z]] acting
+// on the (real, imaginary) pair of each point: rows and columns 2a, 2a + 1.
 __global__ void k_p2p(const P2pDesc* __restrict__ d, int nd, const double* __restrict__ px,
-                      const double* __restrict__ py, const double* __restrict__ pz, double scale, double diag) {
+                      const double* __restrict__ py, const double* __restrict__ pz, double scale, double diag,
+                      double diag_im, double k, int dof) {
   if ((int)blockIdx.x >= nd) return;
   const P2pDesc D = d[blockIdx.x];
   const int total = D.ni * D.nj;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int a = e % D.ni, b = e / D.ni;
     const int i = D.i0 + a, j = D.j0 + b;
-    double v;
-    if (D.same && a == b) {
-      v = diag;
-    } else {
+    const bool self = D.same && a == b;
+    double r = 1.0;
+    if (!self) {
       const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
-      v = scale / sqrt(dx * dx + dy * dy + dz * dz);
+      r = sqrt(dx * dx + dy * dy + dz * dz);
     }
-    D.dst[a + (long)b * D.ld] = v;
+    if (dof == 1) {
+      D.dst[a + (long)b * D.ld] = self ? diag : scale / r;
+    } else {
+      double zr = diag, zi = diag_im;
+      if (!self) {
+        double sn, cs;
+        sincos(k * r, &sn, &cs);
+        zr = scale * cs / r;
+        zi = scale * sn / r;
+      }
+      double* o = D.dst + 2 * a + (long)(2 * b) * D.ld;
+      o[0] = zr;
+      o[1] = zi;
+      o[D.ld] = -zi;
+      o[D.ld + 1] = zr;
+    }
   }
 }
 
@@ -1031,8 +1049,10 @@ __global__ void k_bd_fill(const BdBlockDesc* __restrict__ d, const int* __restri
 
 // Leaf interpolation matrix S (p^3 x n): S(m, j) = l_a(u_x) l_b(u_y) l_c(u_z),
 // m = (c p + b) p + a, u = (x_j - centre)/halfwidth.
+// With dof = 2 the matrix is S (x) I_2 (each node and point carries a real and
+// an imaginary part).
 __global__ void k_interp(const InterpDesc* __restrict__ d, int nd, const double* __restrict__ px,
-                         const double* __restrict__ py, const double* __restrict__ pz, int p) {
+                         const double* __restrict__ py, const double* __restrict__ pz, int p, int dof) {
   if ((int)blockIdx.x >= nd) return;
   const InterpDesc D = d[blockIdx.x];
   const int r = p * p * p;
@@ -1042,47 +1062,84 @@ __global__ void k_interp(const InterpDesc* __restrict__ d, int nd, const double*
     const int a = m % p, b = (m / p) % p, c = m / (p * p);
     const int pt = D.p0 + j;
     const double ux = (px[pt] - D.cx) / D.h, uy = (py[pt] - D.cy) / D.h, uz = (pz[pt] - D.cz) / D.h;
-    D.dst[m + (long)j * D.ld] = lagrange(a, p, ux) * lagrange(b, p, uy) * lagrange(c, p, uz);
+    const double v = lagrange(a, p, ux) * lagrange(b, p, uy) * lagrange(c, p, uz);
+    if (dof == 1) {
+      D.dst[m + (long)j * D.ld] = v;
+    } else {
+      double* o = D.dst + 2 * m + (long)(2 * j) * D.ld;
+      o[0] = v;
+      o[1] = 0.0;
+      o[D.ld] = 0.0;
+      o[D.ld + 1] = v;
+    }
   }
 }
 
 // M2L translation table of one level: for the 7^3 target-minus-source cell
 // offsets o, K_o(m, k) = scale / |h (2 o + t_m - t_k)| between the Chebyshev
 // nodes of two cells of half-width h (offsets with max |o| <= 1 stay zero).
-__global__ void k_m2l_table(double* __restrict__ out, int p, double h, double scale) {
-  const int r = p * p * p;
+// With dof = 2 (Helmholtz) the entry is scale e^{ik r}/r, r = h |2 o + t_m - t_k|,
+// in the real 2 x 2 form (ld 2 r^3).
+__global__ void k_m2l_table(double* __restrict__ out, int p, double h, double scale, double wk, int dof) {
+  const int r = p * p * p, rd = dof * r;
   const int o = blockIdx.x;  // 0..342
   const int ox = o % 7 - 3, oy = (o / 7) % 7 - 3, oz = o / 49 - 3;
   const bool near = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
-  double* T = out + (long)o * r * r;
+  double* T = out + (long)o * rd * rd;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int m = e % r, k = e / r;
-    if (near) {
-      T[e] = 0.0;
-      continue;
+    double v = 0.0, vi = 0.0;
+    if (!near) {
+      const int ma = m % p, mb = (m / p) % p, mc = m / (p * p);
+      const int ka = k % p, kb = (k / p) % p, kc = k / (p * p);
+      const double dx = 2.0 * ox + cheb_root(ma, p) - cheb_root(ka, p);
+      const double dy = 2.0 * oy + cheb_root(mb, p) - cheb_root(kb, p);
+      const double dz = 2.0 * oz + cheb_root(mc, p) - cheb_root(kc, p);
+      const double dist = h * sqrt(dx * dx + dy * dy + dz * dz);
+      if (dof == 1) {
+        v = scale / dist;
+      } else {
+        double sn, cs;
+        sincos(wk * dist, &sn, &cs);
+        v = scale * cs / dist;
+        vi = scale * sn / dist;
+      }
     }
-    const int ma = m % p, mb = (m / p) % p, mc = m / (p * p);
-    const int ka = k % p, kb = (k / p) % p, kc = k / (p * p);
-    const double dx = 2.0 * ox + cheb_root(ma, p) - cheb_root(ka, p);
-    const double dy = 2.0 * oy + cheb_root(mb, p) - cheb_root(kb, p);
-    const double dz = 2.0 * oz + cheb_root(mc, p) - cheb_root(kc, p);
-    T[e] = scale / (h * sqrt(dx * dx + dy * dy + dz * dz));
+    if (dof == 1) {
+      T[e] = v;
+    } else {
+      double* q = T + 2 * m + (long)(2 * k) * rd;
+      q[0] = v;
+      q[1] = vi;
+      q[rd] = -vi;
+      q[rd + 1] = v;
+    }
   }
 }
 
 // M2M of the 8 child octants: M(m, k) = S_parent(child node k, parent node m),
 // the child node at u = (o - 1/2) + t_k / 2 in parent coordinates.
-__global__ void k_m2m_table(double* __restrict__ out, int p) {
-  const int r = p * p * p;
+// (with dof = 2: M (x) I_2, ld 2 r^3)
+__global__ void k_m2m_table(double* __restrict__ out, int p, int dof) {
+  const int r = p * p * p, rd = dof * r;
   const int oct = blockIdx.x;  // 0..7, bit 0 = x, bit 1 = y, bit 2 = z
   const double sx = (oct & 1) - 0.5, sy = ((oct >> 1) & 1) - 0.5, sz = ((oct >> 2) & 1) - 0.5;
-  double* T = out + (long)oct * r * r;
+  double* T = out + (long)oct * rd * rd;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int m = e % r, k = e / r;
     const int ma = m % p, mb = (m / p) % p, mc = m / (p * p);
     const int ka = k % p, kb = (k / p) % p, kc = k / (p * p);
     const double ux = sx + 0.5 * cheb_root(ka, p), uy = sy + 0.5 * cheb_root(kb, p), uz = sz + 0.5 * cheb_root(kc, p);
-    T[e] = lagrange(ma, p, ux) * lagrange(mb, p, uy) * lagrange(mc, p, uz);
+    const double v = lagrange(ma, p, ux) * lagrange(mb, p, uy) * lagrange(mc, p, uz);
+    if (dof == 1) {
+      T[e] = v;
+    } else {
+      double* q = T + 2 * m + (long)(2 * k) * rd;
+      q[0] = v;
+      q[1] = 0.0;
+      q[rd] = 0.0;
+      q[rd + 1] = v;
+    }
   }
 }
 
@@ -1239,6 +1296,52 @@ __global__ void __launch_bounds__(256) k_matvec(const double* __restrict__ px, c
     __syncthreads();
   }
   if (i < n) y[i] = diag * x[i] + scale * acc;
+}
+
+// Helmholtz: y = A x with A_ij = scale e^{ik r_ij}/r_ij, A_ii = diag + i diag_im,
+// complex vectors interleaved (re, im); FP64, a thread per target, sources
+// staged through shared memory.
+__global__ void __launch_bounds__(256) k_matvec_c(const double* __restrict__ px, const double* __restrict__ py,
+                                                  const double* __restrict__ pz, const double* __restrict__ x,
+                                                  double* __restrict__ y, int n, double scale, double diag,
+                                                  double diag_im, double wk) {
+  __shared__ double sx[256], sy[256], sz[256], sr[256], si[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double xi = 0, yi = 0, zi = 0;
+  if (i < n) {
+    xi = px[i];
+    yi = py[i];
+    zi = pz[i];
+  }
+  double ar = 0.0, ai = 0.0;
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    if (j < n) {
+      sx[threadIdx.x] = px[j];
+      sy[threadIdx.x] = py[j];
+      sz[threadIdx.x] = pz[j];
+      sr[threadIdx.x] = x[2 * j];
+      si[threadIdx.x] = x[2 * j + 1];
+    }
+    __syncthreads();
+    const int cnt = min((int)blockDim.x, n - j0);
+    for (int t = 0; t < cnt; ++t) {
+      if (j0 + t == i) continue;
+      const double dx = xi - sx[t], dy = yi - sy[t], dz = zi - sz[t];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      double sn, cs;
+      sincos(wk * r, &sn, &cs);
+      const double w = 1.0 / r;
+      ar += (cs * sr[t] - sn * si[t]) * w;
+      ai += (sn * sr[t] + cs * si[t]) * w;
+    }
+    __syncthreads();
+  }
+  if (i < n) {
+    const double xr = x[2 * i], xim = x[2 * i + 1];
+    y[2 * i] = diag * xr - diag_im * xim + scale * ar;
+    y[2 * i + 1] = diag * xim + diag_im * xr + scale * ai;
+  }
 }
 
 // ---------------------------------------------------------------- double-float matvec
@@ -1616,15 +1719,22 @@ void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double 
   check_launch("k_chol");
 }
 
+// point permutations of vectors with dof entries per point
 __global__ void k_gather_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
-                              int n) {
+                              int n, int dof) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) dst[k] = src[perm[k]];
+  if (k < n * dof) {
+    const int pt = k / dof, c = k - pt * dof;
+    dst[k] = src[(long)perm[pt] * dof + c];
+  }
 }
 __global__ void k_scatter_perm(const double* __restrict__ src, const int* __restrict__ perm, double* __restrict__ dst,
-                               int n) {
+                               int n, int dof) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) dst[perm[k]] = src[k];
+  if (k < n * dof) {
+    const int pt = k / dof, c = k - pt * dof;
+    dst[(long)perm[pt] * dof + c] = src[k];
+  }
 }
 
 // ---------------------------------------------------------------- big Gauss-Jordan
@@ -1734,17 +1844,19 @@ void big_inverse(cudaStream_t s, double* A, int ld, int n, int* d_work_int, doub
   profiler().end(KK_GJ_BIG, s, pe);
 }
 
-void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, double scale, double diag) {
+void launch_p2p(DescStage& st, const std::vector<P2pDesc>& v, const double* pts, int N, const ifmm_kernel& k) {
   if (v.empty()) return;
+  const int dof = kernel_dof(k);
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
-    req(v[i].dst, span(v[i].ni, v[i].nj, v[i].ld), "p2p.dst", i);
+    req(v[i].dst, span(dof * v[i].ni, dof * v[i].nj, v[i].ld), "p2p.dst", i);
     if (v[i].i0 < 0 || v[i].j0 < 0 || v[i].i0 + v[i].ni > N || v[i].j0 + v[i].nj > N)
       throw Error(IFMM_EINVAL, "p2p point range");
   }
   const P2pDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   profiler().count(KK_P2P, 1);
-  k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, scale, diag);
+  k_p2p<<<(unsigned)v.size(), 128, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, k.scale, k.diag,
+                                                   k.diag_im, k.wavenumber, dof);
   check_launch("k_p2p");
 }
 
@@ -1767,46 +1879,50 @@ void launch_bd_fill(DescStage& st, const std::vector<BdBlockDesc>& v, const doub
   profiler().end(KK_P2P, st.stream, pe);
 }
 
-void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p) {
+void launch_interp(DescStage& st, const std::vector<InterpDesc>& v, const double* pts, int N, int p, int dof) {
   if (v.empty()) return;
   for (size_t i = 0; i < v.size() && registry().on; ++i) {
-    req(v[i].dst, span(p * p * p, v[i].n, v[i].ld), "interp.dst", i);
+    req(v[i].dst, span(dof * p * p * p, dof * v[i].n, v[i].ld), "interp.dst", i);
     if (v[i].p0 < 0 || v[i].p0 + v[i].n > N) throw Error(IFMM_EINVAL, "interp point range");
   }
   const InterpDesc* d = st.push(v);
   prof_batch_tag() = (long)v.size();
   profiler().count(KK_INTERP, 1);
-  k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p);
+  k_interp<<<(unsigned)v.size(), 256, 0, st.stream>>>(d, (int)v.size(), pts, pts + N, pts + 2 * (long)N, p, dof);
   check_launch("k_interp");
 }
 
-void launch_m2l_table(cudaStream_t s, double* out, int p, double h, double scale) {
+void launch_m2l_table(cudaStream_t s, double* out, int p, double h, const ifmm_kernel& k) {
   profiler().count(KK_TABLES, 1);
-  k_m2l_table<<<343, 256, 0, s>>>(out, p, h, scale);
+  k_m2l_table<<<343, 256, 0, s>>>(out, p, h, k.scale, k.wavenumber, kernel_dof(k));
   check_launch("k_m2l_table");
 }
 
-void launch_m2m_table(cudaStream_t s, double* out, int p) {
+void launch_m2m_table(cudaStream_t s, double* out, int p, int dof) {
   profiler().count(KK_TABLES, 1);
-  k_m2m_table<<<8, 256, 0, s>>>(out, p);
+  k_m2m_table<<<8, 256, 0, s>>>(out, p, dof);
   check_launch("k_m2m_table");
 }
 
-void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, double scale, double diag) {
+void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, const ifmm_kernel& k) {
   cudaEvent_t pe = profiler().begin(KK_MATVEC, s);
-  k_matvec<<<(N + 255) / 256, 256, 0, s>>>(pts, pts + N, pts + 2 * (long)N, x, y, N, scale, diag);
+  if (kernel_dof(k) == 2)
+    k_matvec_c<<<(N + 255) / 256, 256, 0, s>>>(pts, pts + N, pts + 2 * (long)N, x, y, N, k.scale, k.diag, k.diag_im,
+                                               k.wavenumber);
+  else
+    k_matvec<<<(N + 255) / 256, 256, 0, s>>>(pts, pts + N, pts + 2 * (long)N, x, y, N, k.scale, k.diag);
   check_launch("k_matvec");
   profiler().end(KK_MATVEC, s, pe);
 }
 
-void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+void launch_gather_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n, int dof) {
   profiler().count(KK_PERM, 1);
-  k_gather_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
+  k_gather_perm<<<(n * dof + 255) / 256, 256, 0, s>>>(src, perm, dst, n, dof);
   check_launch("k_gather_perm");
 }
-void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n) {
+void launch_scatter_perm(cudaStream_t s, const double* src, const int* perm, double* dst, int n, int dof) {
   profiler().count(KK_PERM, 1);
-  k_scatter_perm<<<(n + 255) / 256, 256, 0, s>>>(src, perm, dst, n);
+  k_scatter_perm<<<(n * dof + 255) / 256, 256, 0, s>>>(src, perm, dst, n, dof);
   check_launch("k_scatter_perm");
 }
 

@@ -294,7 +294,7 @@ void build_solve_plan(ifmm_fact& F, cudaStream_t s) {
 // in/out: tree-ordered device vectors of length N (may alias)
 void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStream_t s) {
   const SolvePlan& P = F.plan;
-  const int64_t N = F.t->N;
+  const int64_t N = F.t->N * kernel_dof(F.k);  // doubles per vector
   if (P.pairs)
     launch_pair_split(s, in, P.stage_in, N);
   else
@@ -432,7 +432,8 @@ ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs,
   try {
     IFMM_REQUIRE(f && r && v && nrhs >= 1, IFMM_EINVAL, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = f->t->N;
+    const int dof = kernel_dof(f->k);
+    const int64_t NP = f->t->N, N = NP * dof;  // points, doubles per vector
     const bool dev = is_device_ptr(r);
     IFMM_REQUIRE(dev == is_device_ptr(v), IFMM_EINVAL, "r and v must both be host or both device");
     Vecs V;
@@ -446,12 +447,12 @@ ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs,
         CK(cudaMemcpyAsync(b, rc, sizeof(double) * N, cudaMemcpyHostToDevice, s));
         src = b;
       }
-      launch_gather_perm(s, src, f->t->d_perm, a, (int)N);
+      launch_gather_perm(s, src, f->t->d_perm, a, (int)NP, dof);
       run_solve_tree(*f, a, a, s);
       if (dev) {
-        launch_scatter_perm(s, a, f->t->d_perm, vc, (int)N);
+        launch_scatter_perm(s, a, f->t->d_perm, vc, (int)NP, dof);
       } else {
-        launch_scatter_perm(s, a, f->t->d_perm, b, (int)N);
+        launch_scatter_perm(s, a, f->t->d_perm, b, (int)NP, dof);
         CK(cudaMemcpyAsync(vc, b, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
       }
     }
@@ -469,9 +470,12 @@ ifmm_status ifmm_solve(const ifmm_fact* f, const double* r, double* v, int nrhs,
 ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x, double* y, void* stream) {
   try {
     IFMM_REQUIRE(t && k && x && y, IFMM_EINVAL, "bad argument");
+    IFMM_REQUIRE(k->wavenumber == 0.0 || k->arith == IFMM_ARITH_FP64, IFMM_EINVAL,
+                 "the Helmholtz kernel takes the FP64 direct sum (arith IFMM_ARITH_FP64)");
     const_cast<ifmm_tree*>(t)->ensure_device();
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = t->N;
+    const int dof = kernel_dof(*k);
+    const int64_t NP = t->N, N = NP * dof;
     const bool dev = is_device_ptr(x);
     IFMM_REQUIRE(dev == is_device_ptr(y), IFMM_EINVAL, "x and y must both be host or both device");
     Vecs V;
@@ -483,7 +487,7 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       CK(cudaMemcpyAsync(c, x, sizeof(double) * N, cudaMemcpyHostToDevice, s));
       src = c;
     }
-    launch_gather_perm(s, src, t->d_perm, a, (int)N);
+    launch_gather_perm(s, src, t->d_perm, a, (int)NP, dof);
     if (k->arith == IFMM_ARITH_FMM) {
       FmmPlan* P = fmm_plan(*const_cast<ifmm_tree*>(t), k->order ? k->order : 4, k->scale, k->diag, s);
       fmm_apply(*t, *P, a, b, s);
@@ -497,12 +501,12 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       }
       launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tm->matvec_block);
     } else {
-      launch_matvec(s, t->d_pts, (int)N, a, b, k->scale, k->diag);
+      launch_matvec(s, t->d_pts, (int)NP, a, b, *k);
     }
     if (dev) {
-      launch_scatter_perm(s, b, t->d_perm, y, (int)N);
+      launch_scatter_perm(s, b, t->d_perm, y, (int)NP, dof);
     } else {
-      launch_scatter_perm(s, b, t->d_perm, c, (int)N);
+      launch_scatter_perm(s, b, t->d_perm, c, (int)NP, dof);
       CK(cudaMemcpyAsync(y, c, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -522,9 +526,14 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
     IFMM_REQUIRE(t && k && b && x, IFMM_EINVAL, "bad argument");
     IFMM_REQUIRE(restart >= 1 && restart <= 1000 && maxit >= 1 && tol > 0, IFMM_EINVAL, "bad GMRES parameters");
     IFMM_REQUIRE(!pre || pre->t == t, IFMM_EINVAL, "preconditioner built on another tree");
+    IFMM_REQUIRE(k->wavenumber == 0.0 || k->arith == IFMM_ARITH_FP64, IFMM_EINVAL,
+                 "the Helmholtz kernel takes the FP64 direct sum (arith IFMM_ARITH_FP64)");
+    IFMM_REQUIRE(!pre || kernel_dof(pre->k) == kernel_dof(*k), IFMM_EINVAL,
+                 "preconditioner built for a real (complex) kernel used with a complex (real) one");
     const_cast<ifmm_tree*>(t)->ensure_device();
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = t->N;
+    const int dof = kernel_dof(*k);
+    const int64_t NP = t->N, N = NP * dof;  // points; doubles per vector (real form)
     const int m = restart;
     const bool dev = is_device_ptr(b);
     IFMM_REQUIRE(dev == is_device_ptr(x), IFMM_EINVAL, "b and x must both be host or both device");
@@ -543,7 +552,7 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
       CK(cudaMemcpyAsync(tmp, b, sizeof(double) * N, cudaMemcpyHostToDevice, s));
       src = tmp;
     }
-    launch_gather_perm(s, src, t->d_perm, bt, (int)N);
+    launch_gather_perm(s, src, t->d_perm, bt, (int)NP, dof);
     auto dot = [&](const double* u, const double* v) -> double {
       std::vector<GemvDesc> g{gmv(u, (int)N, (int)N, 1, 1, v, B.d_out, 1.0, 0.0)};
       launch_gemv(B.st, g);
@@ -580,7 +589,7 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
         }
         launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tm->matvec_block);
       } else {
-        launch_matvec(s, t->d_pts, (int)N, in, out, k->scale, k->diag);
+        launch_matvec(s, t->d_pts, (int)NP, in, out, *k);
       }
     };
     CK(cudaMemsetAsync(xt, 0, sizeof(double) * N, s));
@@ -661,9 +670,9 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
       rel = rn / bnorm;
     }
     if (dev) {
-      launch_scatter_perm(s, xt, t->d_perm, x, (int)N);
+      launch_scatter_perm(s, xt, t->d_perm, x, (int)NP, dof);
     } else {
-      launch_scatter_perm(s, xt, t->d_perm, tmp, (int)N);
+      launch_scatter_perm(s, xt, t->d_perm, tmp, (int)NP, dof);
       CK(cudaMemcpyAsync(x, tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));

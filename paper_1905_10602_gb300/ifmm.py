@@ -33,7 +33,7 @@ class IFMMError(RuntimeError):
 
 class Kernel(ctypes.Structure):
     _fields_ = [("scale", ctypes.c_double), ("diag", ctypes.c_double), ("arith", ctypes.c_int),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("wavenumber", ctypes.c_double), ("diag_im", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -100,8 +100,21 @@ def _is_torch(x):
     return type(x).__module__.startswith("torch")
 
 
+def _as_real(x):
+    """A complex array as its interleaved (real, imaginary) float64 view, sharing
+    memory (the layout the C ABI takes for the Helmholtz kernel); real arrays as
+    they are."""
+    if _is_torch(x):
+        import torch
+
+        return torch.view_as_real(x) if x.is_complex() else x
+    return x.view(np.float64) if np.iscomplexobj(x) else x
+
+
 def _ptr(x):
-    """Pointer of a C-contiguous float64 NumPy array or torch tensor."""
+    """Pointer of a C-contiguous float64 NumPy array or torch tensor (complex:
+    its interleaved float64 view)."""
+    x = _as_real(x)
     if _is_torch(x):
         assert x.is_contiguous() and str(x.dtype) == "torch.float64"
         return ctypes.c_void_p(x.data_ptr())
@@ -124,7 +137,16 @@ def default_kernel(n, arith: str = "fp64", order: int = 0):
     """A_ij = 1/(N |x_i - x_j|), A_ii = 0.5 + 1/sqrt(N); arith: the matvec as a
     direct sum in plain FP64 or in FP64-accurate float pairs ("df"), or the FMM
     representation A~ at Chebyshev order `order` ("fmm", 0 = 4)."""
-    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n), ARITH[arith], order)
+    return Kernel(1.0 / n, 0.5 + 1.0 / np.sqrt(n), ARITH[arith], order, 0.0, 0.0)
+
+
+def helmholtz_kernel(n, wavenumber: float):
+    """A_ij = e^{ik|x_i - x_j|}/(N |x_i - x_j|), A_ii = 0.5 plus the kernel
+    integrated over a disk panel of area 4 pi / N (radius rho = 2/sqrt(N)):
+    (e^{ik rho} - 1)/(2ik).  Complex; FP64 direct-sum matvec."""
+    k = float(wavenumber)
+    rho = 2.0 / np.sqrt(n)
+    return Kernel(1.0 / n, 0.5 + np.sin(k * rho) / (2.0 * k), 0, 0, k, (1.0 - np.cos(k * rho)) / (2.0 * k))
 
 
 class Tree:
@@ -214,7 +236,8 @@ def ifmm_solve(fact: Fact, r, stream=None):
 
         v = torch.empty_like(r)
     else:
-        r = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+        r = np.asarray(r)
+        r = np.ascontiguousarray(r if np.iscomplexobj(r) else r.astype(np.float64))
         v = np.empty_like(r)
     nrhs = 1 if r.ndim == 1 else r.shape[0]
     _check(lib.ifmm_solve(fact.h, _ptr(r), _ptr(v), nrhs, stream or _stream(r)))
@@ -228,7 +251,8 @@ def bem_matvec(tree: Tree, x, kernel: Kernel | None = None, stream=None):
 
         y = torch.empty_like(x)
     else:
-        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        x = np.asarray(x)
+        x = np.ascontiguousarray(x if np.iscomplexobj(x) else x.astype(np.float64))
         y = np.empty_like(x)
     _check(lib.bem_matvec(tree.h, ctypes.byref(k), _ptr(x), _ptr(y), stream or _stream(x)))
     return y
@@ -243,7 +267,8 @@ def bem_gmres(tree: Tree, b, precond: Fact | None = None, restart: int = 30, tol
 
         x = torch.empty_like(b)
     else:
-        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+        b = np.asarray(b)
+        b = np.ascontiguousarray(b if np.iscomplexobj(b) else b.astype(np.float64))
         x = np.empty_like(b)
     its, rel = ctypes.c_int(), ctypes.c_double()
     code = lib.bem_gmres(tree.h, ctypes.byref(k), precond.h if precond else None, _ptr(b), _ptr(x), restart, tol,

@@ -100,6 +100,12 @@ def point_source_rhs(pts: np.ndarray, src=SOURCE_POINT) -> np.ndarray:
     return 1.0 / (4.0 * math.pi * d)
 
 
+def helmholtz_source_rhs(pts: np.ndarray, k: float, src=SOURCE_POINT) -> np.ndarray:
+    """Right-hand side b_i = e^{ik|x_i - s|}/(4 pi |x_i - s|): a unit acoustic source at s."""
+    d = np.linalg.norm(pts - np.asarray(src, dtype=np.float64)[None, :], axis=1)
+    return np.exp(1j * k * d) / (4.0 * math.pi * d)
+
+
 def surface(shape: str, n: int, seed: int) -> np.ndarray:
     if shape == "sphere":
         return fibonacci_sphere(n, seed)

@@ -27,7 +27,7 @@ def test_exactly_singular_pivot_is_esingular():
     (Algorithm 1's 'factorize P2P_ii' cannot proceed)."""
     t = _tree()
     with pytest.raises(ifmm.IFMMError) as e:
-        ifmm.ifmm_factor(t, 3, 1e-6, kernel=ifmm.Kernel(0.0, 0.0, 0, 0))
+        ifmm.ifmm_factor(t, 3, 1e-6, kernel=ifmm.Kernel(0.0, 0.0, 0, 0, 0.0, 0.0))
     assert e.value.code == 4 and "singular" in str(e.value)
     # the library stays usable afterwards
     f = ifmm.ifmm_factor(t, 3, 1e-6)
