@@ -177,7 +177,12 @@ struct Factorizer {
   const ifmm_tree& T;
   cudaStream_t s;
   DescStage st;
-  DeviceArena scratch;
+  // Per-color scratch, two arenas used by alternate colors: a color's phase B/C
+  // is issued after the next color's phase A (see run), so its buffers must
+  // outlive that color's reset.
+  DeviceArena scratch_buf[2];
+  int scratch_sel = 0;
+  DeviceArena& scratch() { return scratch_buf[scratch_sel]; }
   DeviceArena levelmem;
   int p, rc, maxrank;
   int prec = P64;  // arithmetic of Schur GEMMs and recompression (pivots stay FP64)
@@ -302,8 +307,8 @@ struct Factorizer {
       std::vector<float> feat(evs.size() * IFMM_MLP_IN);
       for (size_t e = 0; e < evs.size(); ++e)
         memcpy(&feat[e * IFMM_MLP_IN], evs[e].feat, sizeof(float) * IFMM_MLP_IN);
-      float* dx = (float*)scratch.alloc(feat.size() / 2 + 1);
-      float* dy = (float*)scratch.alloc(evs.size() / 2 + 1);
+      float* dx = (float*)scratch().alloc(feat.size() / 2 + 1);
+      float* dy = (float*)scratch().alloc(evs.size() / 2 + 1);
       CK(cudaMemcpyAsync(dx, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, s));
       mlp_predict_device(d_mlp, dx, dy, (int)evs.size(), s);
       std::vector<float> pred(evs.size());
@@ -318,9 +323,9 @@ struct Factorizer {
     // contiguous readback buffers: singular values, truncation counts, tails
     size_t sig_total = 0;
     for (auto& ev : evs) sig_total += 2 * (size_t)ev.n;
-    double* sig_all = scratch.alloc(std::max<size_t>(sig_total, 1));
-    int* kall = (int*)scratch.alloc(evs.size() + 1);
-    double* tail_all = scratch.alloc(2 * evs.size() + 1);
+    double* sig_all = scratch().alloc(std::max<size_t>(sig_total, 1));
+    int* kall = (int*)scratch().alloc(evs.size() + 1);
+    double* tail_all = scratch().alloc(2 * evs.size() + 1);
     size_t sig_off = 0;
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
@@ -351,7 +356,7 @@ struct Factorizer {
         }
         double* Z = nullptr;
         if (mw > 0) {
-          Z = scratch.alloc((size_t)mz * r0);
+          Z = scratch().alloc((size_t)mz * r0);
           if (ev.zq >= 0) {
             IFMM_REQUIRE(zt, IFMM_EINVAL, "internal: device weight stack without tables");
             zg.push_back(ZGatherDesc{Z, mz, ev.zq, side, 0});
@@ -367,7 +372,7 @@ struct Factorizer {
             cnt.qr += 2.0 * mz * r0 * (double)r0 - 2.0 * std::pow((double)std::min(mz, r0), 3) / 3.0;
           }
         }
-        double* Y = scratch.alloc((size_t)my * n);
+        double* Y = scratch().alloc((size_t)my * n);
         if (mw > 0) {
           const Blk& B = ev.b[side];
           // W = Z * B (path A) or R_Z * B (path B); B logical r0 x n
@@ -381,9 +386,9 @@ struct Factorizer {
           off += f.rows;
         }
         ev.cf_count[side] = (int)cf.size() - ev.cf_first[side];
-        ev.V[side] = scratch.alloc((size_t)n * n);
-        double* work = scratch.alloc((size_t)n * n);
-        int* jp = (int*)scratch.alloc((size_t)n / 2 + 1);
+        ev.V[side] = scratch().alloc((size_t)n * n);
+        double* work = scratch().alloc((size_t)n * n);
+        int* jp = (int*)scratch().alloc((size_t)n / 2 + 1);
         QrcpDesc qd;
         qd.A = Y;
         qd.ld = my;
@@ -437,8 +442,8 @@ struct Factorizer {
     // randomized range finder (Halko, Martinsson, Tropp) at the predicted rank s:
     // Z = Y^T Omega, Q = orth(Z), B = Y Q, SVD of B -> V = Q V_B; residual
     // E = Y - B Q^T, whose Frobenius norm bounds what the sketch missed
-    double* enorm_all = scratch.alloc(2 * evs.size() + 1);
-    double* ynorm_all = scratch.alloc(2 * evs.size() + 1);
+    double* enorm_all = scratch().alloc(2 * evs.size() + 1);
+    double* ynorm_all = scratch().alloc(2 * evs.size() + 1);
     {
       std::vector<SketchDesc> sk;
       std::vector<GemmDesc> g1, g2, g3, g4;
@@ -448,22 +453,22 @@ struct Factorizer {
       std::vector<FrobDesc> fr;
       std::vector<int> widths;
       std::vector<int*> wdev;
-      int* sarr = (int*)scratch.alloc(evs.size() + 1);
+      int* sarr = (int*)scratch().alloc(evs.size() + 1);
       for (size_t e = 0; e < evs.size(); ++e)
         for (int side = 0; side < 2; ++side) {
           Event& ev = evs[e];
           if (!ev.rnd[side]) continue;
           const int n = ev.n, my = ev.my[side], sw = std::min(ev.kcap, n);
-          double* Om = scratch.alloc((size_t)my * sw);
-          double* Zs = scratch.alloc((size_t)n * sw);
-          double* Q = scratch.alloc((size_t)n * n);
-          double* qs = scratch.alloc(n);
-          double* qw = scratch.alloc((size_t)n * n);
-          double* Bm = scratch.alloc((size_t)my * sw);
-          double* VB = scratch.alloc((size_t)sw * sw);
-          double* bw = scratch.alloc((size_t)sw * sw);
-          double* E = scratch.alloc((size_t)my * n);
-          int* jpb = (int*)scratch.alloc((size_t)sw / 2 + 1);
+          double* Om = scratch().alloc((size_t)my * sw);
+          double* Zs = scratch().alloc((size_t)n * sw);
+          double* Q = scratch().alloc((size_t)n * n);
+          double* qs = scratch().alloc(n);
+          double* qw = scratch().alloc((size_t)n * n);
+          double* Bm = scratch().alloc((size_t)my * sw);
+          double* VB = scratch().alloc((size_t)sw * sw);
+          double* bw = scratch().alloc((size_t)sw * sw);
+          double* E = scratch().alloc((size_t)my * n);
+          int* jpb = (int*)scratch().alloc((size_t)sw / 2 + 1);
           int* sdev = sarr + widths.size();
           widths.push_back(sw);
           sk.push_back(SketchDesc{Om, my, sw, (unsigned long long)(F.o.seed * 0x100000001B3ull + (uint64_t)ev.key * 2 + side)});
@@ -626,8 +631,8 @@ struct Factorizer {
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
       const int k = ev.k, n = ev.n, r0 = ev.r_old;
-      ev.T = scratch.alloc((size_t)std::max(1, r0 * k));
-      ev.Tp = scratch.alloc((size_t)std::max(1, r0 * k));
+      ev.T = scratch().alloc((size_t)std::max(1, r0 * k));
+      ev.Tp = scratch().alloc((size_t)std::max(1, r0 * k));
       if (k == 0) continue;
       // side 0: B = P2M_old (r0 x n); side 1: B = L2P_old^T
       if (r0 > 0) {
@@ -796,11 +801,12 @@ struct Factorizer {
       }
     }
     // stage-0 near blocks and the initial bases (r_cheb columns / rows)
-    scratch.reset();
+    scratch_sel = 0;
+    scratch().reset();
     std::vector<double*> P2M0(nn), L2P0(nn);
     for (int i = 0; i < nn; ++i) {
-      P2M0[i] = scratch.alloc((size_t)rc * std::max(1, W.n[i]));
-      L2P0[i] = scratch.alloc((size_t)rc * std::max(1, W.n[i]));
+      P2M0[i] = scratch().alloc((size_t)rc * std::max(1, W.n[i]));
+      L2P0[i] = scratch().alloc((size_t)rc * std::max(1, W.n[i]));
     }
     if (!child) {
       std::vector<P2pDesc> pp;
@@ -918,7 +924,7 @@ struct Factorizer {
       std::vector<int> first(2 * (size_t)nn + 1, 0);
       rz_row.resize(nn);
       rz_col.resize(nn);
-      double* Rall = scratch.alloc(std::max<size_t>(1, 2 * (size_t)nn * ((rc2 + 31) & ~(size_t)31)));
+      double* Rall = scratch().alloc(std::max<size_t>(1, 2 * (size_t)nn * ((rc2 + 31) & ~(size_t)31)));
       for (int q = 0; q < nn; ++q)
         for (int side = 0; side < 2; ++side) {
           const size_t x = 2 * (size_t)q + side;
@@ -1018,7 +1024,7 @@ struct Factorizer {
           const int b = LL.il[e];
           const int ka = evs[a].k, kb = evs[b].k;
           if (!ka || !kb) continue;
-          tmp[e] = scratch.alloc((size_t)ka * rc);
+          tmp[e] = scratch().alloc((size_t)ka * rc);
           g1.push_back(gmm(evs[a].Tp, ka, 0, m2l_tab + off_index(a, b) * rc2, rc, 0, tmp[e], ka, ka, rc, rc, 1.0, 0.0));
           g2.push_back(gmm(tmp[e], ka, 0, evs[b].T, rc, 0, W.far[e], W.capr[a], ka, kb, rc, 1.0, 0.0));
         }
@@ -1037,10 +1043,39 @@ struct Factorizer {
   }
 
   // ------------------------------------------------------------------ one color
-  void eliminate_color(Work& W, const std::vector<int>& grp, LevelFactor& LF) {
+  // A color is done in three stages (Algorithm 1 over the color's nodes):
+  //   phase A     pivots and Schur complements (launched);
+  //   events      recompression of the live neighbours that received far
+  //               fill-ins, the ranks read back (the stream is synchronized),
+  //               the new bases and transforms (launched);
+  //   phase B/C   interaction-list blocks re-expressed in the new bases, fill-in
+  //               coefficients added (launched).
+  // run() issues them as A(c), B/C(c-1), events(c): the next color's pivots
+  // and Schur updates read only near blocks and the just re-based P2M/L2P, never
+  // the far blocks that B/C(c-1) rewrite, so the GPU executes them while the
+  // host builds B/C(c-1); events(c) read far blocks and come after.
+  struct FarFill {
+    int a, b;
+    const double* Fp;
+    int ld, rows, cols;
+    int fx;  // position of (a, b) in the IL CSR
+  };
+  struct ColorState {
+    std::vector<int> grp;
+    int sel = 0;  // scratch arena
+    std::vector<FarFill> fills;
+    std::vector<int> slot_of, rebase_order, trigger_of;
+    std::vector<std::vector<Blk>> rowfill_v, colfill_v;
+    std::vector<Event> evs;
+    std::vector<int> r_before;
+  };
+
+  void color_phase_a(Work& W, ColorState& cs, LevelFactor& LF) {
     const LevelLists& LL = *W.LL;
     auto tp = std::chrono::steady_clock::now();
-    scratch.reset();
+    scratch_sel = cs.sel;
+    scratch().reset();
+    const std::vector<int>& grp = cs.grp;
     const int ng = (int)grp.size();
     if (info_cap < ng) {
       if (d_info) {
@@ -1084,19 +1119,15 @@ struct Factorizer {
     el8.assign(W.elim.begin(), W.elim.end());
     auto& gx = fresh(L.gx);
     auto& gf = fresh(L.gf);
-    struct FarFill {
-      int a, b;
-      const double* Fp;
-      int ld, rows, cols;
-      int fx;  // position of (a, b) in the IL CSR
-    };
-    std::vector<FarFill> fills;
+    auto& fills = cs.fills;
     // per-node fill lists, indexed through the order in which nodes first
     // receive a far fill (the re-base order)
-    std::vector<int> slot_of(W.nn, -1);
-    std::vector<int> rebase_order;
-    std::vector<std::vector<Blk>> rowfill_v, colfill_v;
-    std::vector<int> trigger_of;
+    auto& slot_of = cs.slot_of;
+    slot_of.assign(W.nn, -1);
+    auto& rebase_order = cs.rebase_order;
+    auto& rowfill_v = cs.rowfill_v;
+    auto& colfill_v = cs.colfill_v;
+    auto& trigger_of = cs.trigger_of;
     int cur_i = -1;
     auto rebase_slot = [&](int q) {
       if (slot_of[q] < 0) {
@@ -1132,7 +1163,7 @@ struct Factorizer {
           tot += rup((size_t)M * std::max(1, ni)) + rup((size_t)std::max(1, ni) * M) + rup((size_t)M * m) +
                  rup((size_t)M * M) + rup((size_t)std::max(1, ri) * M);
       }
-      double* blk = tot ? scratch.alloc(tot) : nullptr;
+      double* blk = tot ? scratch().alloc(tot) : nullptr;
       for (int g = 0; g < ng; ++g) nbase[g] = blk ? blk + offs[g] : nullptr;
     }
     const int nth = host_threads(ng);
@@ -1258,12 +1289,23 @@ struct Factorizer {
       launch_schur_scatter(st, scat, tt, maxdeg);
     }
     phase("host_schur", tp);
+  }
+
+  void color_events(Work& W, ColorState& cs) {
+    const LevelLists& LL = *W.LL;
+    auto tp = std::chrono::steady_clock::now();
+    scratch_sel = cs.sel;
+    const int ng = (int)cs.grp.size();
+    auto& slot_of = cs.slot_of;
+    auto& rowfill_v = cs.rowfill_v;
+    auto& colfill_v = cs.colfill_v;
+    auto& trigger_of = cs.trigger_of;
     // ---- recompression events (snapshots: nothing below reads what phase A changes)
-    std::vector<Event> evs;
+    auto& evs = cs.evs;
     std::vector<double*> po, lo;
     std::vector<int> pld, lld;
-    std::vector<int> r_before(W.r);
-    for (int q : rebase_order) {
+    cs.r_before = W.r;
+    for (int q : cs.rebase_order) {
       Event ev = make_event(W, q, trigger_of[slot_of[q]]);
       ev.r_old = W.r[q];
       ev.n = W.n[q];
@@ -1294,6 +1336,16 @@ struct Factorizer {
     run_events(evs, W, po, lo, pld, lld, nullptr, ng, &zt);
     F.stat_add("host_run_events_wait", t_wait - w0);
     phase("host_run_events", tp);
+    for (auto& ev : evs) W.r[ev.q] = ev.k;
+  }
+
+  void color_phase_bc(Work& W, ColorState& cs) {
+    const LevelLists& LL = *W.LL;
+    auto tp = std::chrono::steady_clock::now();
+    scratch_sel = cs.sel;
+    auto& evs = cs.evs;
+    auto& fills = cs.fills;
+    const std::vector<int>& r_before = cs.r_before;
     // ---- phase B: re-express blocks that touch a re-based node
     std::vector<int> newk(W.nn, -1);
     std::vector<const Event*> evof(W.nn, nullptr);
@@ -1308,8 +1360,8 @@ struct Factorizer {
     for (auto& ev : evs) {
       const int q = ev.q;
       if (W.kappa > 2 && ev.k && ev.r_old) {
-        double* t1 = scratch.alloc((size_t)rc * ev.k);
-        double* t2 = scratch.alloc((size_t)rc * ev.k);
+        double* t1 = scratch().alloc((size_t)rc * ev.k);
+        double* t2 = scratch().alloc((size_t)rc * ev.k);
         b1.push_back(gmm(W.M2M[q], rc, 0, ev.T, ev.r_old, 0, t1, rc, rc, ev.k, ev.r_old, 1.0, 0.0));
         b1.push_back(gmm(ev.Tp, ev.k, 0, W.L2L[q], W.capr[q], 0, t2, ev.k, ev.k, rc, ev.r_old, 1.0, 0.0));
         bc1.push_back(cpy(t1, rc, W.M2M[q], rc, rc, ev.k));
@@ -1366,7 +1418,7 @@ struct Factorizer {
         const int b = LL.il[e];
         const int ra = r_before[a], rb = r_before[b];
         const int ka = newk[a] >= 0 ? newk[a] : ra, kb = newk[b] >= 0 ? newk[b] : rb;
-        double* t1 = scratch.alloc((size_t)ka * std::max(1, rb));
+        double* t1 = scratch().alloc((size_t)ka * std::max(1, rb));
         if (!ra || !rb) {
           bc2.push_back(cpy(nullptr, 0, W.far[e], W.capr[a], ka, kb));
           continue;
@@ -1399,7 +1451,6 @@ struct Factorizer {
       launch_il_transform(st, fast, t, md, prec);
     }
     phase("host_phase_b", tp);
-    for (auto& ev : evs) W.r[ev.q] = ev.k;
     // ---- phase C: fill-in coefficients in the new bases
     auto& c1 = fresh(L.c1);
     auto& c2 = fresh(L.c2);
@@ -1412,7 +1463,7 @@ struct Factorizer {
       const int ldd = W.capr[a];
       if (!ka || !kb) continue;
       if (la && lb) {
-        double* t = scratch.alloc((size_t)ka * f.cols);
+        double* t = scratch().alloc((size_t)ka * f.cols);
         c1.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, t, ka, ka, f.cols, f.rows, 1.0, 0.0));
         c2.push_back(gmm(t, ka, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
       } else if (la) {
@@ -1456,9 +1507,9 @@ struct Factorizer {
       }
     (void)LL;
     launch_copy(st, cc);
-    double* wk = scratch.alloc(2 * (size_t)nt);
-    int* wi = (int*)scratch.alloc((size_t)nt);
-    int* info = (int*)scratch.alloc(1);
+    double* wk = scratch().alloc(2 * (size_t)nt);
+    int* wi = (int*)scratch().alloc((size_t)nt);
+    int* info = (int*)scratch().alloc(1);
     big_inverse(s, F.top_inv, nt, nt, wi, wk, info);
     cnt.lu += 2.0 * std::pow((double)nt, 3);
     int hinfo = 0;
@@ -1497,11 +1548,19 @@ struct Factorizer {
       LF.nf.assign(W->nn, NodeFactor());
       LF.n = W->n;
       const LevelLists& LL = T.lv[kappa];
+      std::unique_ptr<ColorState> pend;  // the previous color, its phase B/C not yet issued
       for (size_t c = 0; c + 1 < LL.group_ptr.size(); ++c) {
-        std::vector<int> grp(LL.group.begin() + LL.group_ptr[c], LL.group.begin() + LL.group_ptr[c + 1]);
-        eliminate_color(*W, grp, LF);
-        LF.order.push_back(grp);
+        std::unique_ptr<ColorState> cs(new ColorState());
+        cs->grp.assign(LL.group.begin() + LL.group_ptr[c], LL.group.begin() + LL.group_ptr[c + 1]);
+        cs->sel = (int)(c & 1);
+        color_phase_a(*W, *cs, LF);
+        if (pend) color_phase_bc(*W, *pend);
+        color_events(*W, *cs);
+        LF.order.push_back(cs->grp);
+        pend = std::move(cs);
       }
+      if (pend) color_phase_bc(*W, *pend);
+      pend.reset();
       LF.r = W->r;
       if (kappa == 2) top(*W);
       wait();
@@ -1514,7 +1573,8 @@ struct Factorizer {
     build_solve_plan(F, s);
     CK(cudaStreamSynchronize(s));
     levelmem.release();
-    scratch.release();
+    scratch_buf[0].release();
+    scratch_buf[1].release();
     // the solve reads its own packed copies: the factor's block pool goes
     F.stat("bytes_factor", (double)F.persist.high);
     F.persist.release();
