@@ -305,6 +305,16 @@ ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, 
 ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
                             const double* B, int ldb, double beta, double* C, int ldc);
 
+/* The FP64 Gauss-Jordan inverse with partial pivoting of the pivot blocks
+ * (Algorithm 1's inverses of Pi_i), on host arrays, through the same size
+ * classes as the factorization (one CTA in shared memory, a thread-block
+ * cluster, or the batched multi-CTA kernels).  A holds nmat column-major
+ * matrices back to back, matrix i of order n[i] (1..4096) with leading
+ * dimension n[i]; each is replaced by its inverse.  info[i] = 0, or k + 1 when
+ * step k found no nonzero pivot (that matrix is then left partly eliminated).
+ * At most 2^28 doubles in all.  Synchronous; IFMM_ECUDA without a device. */
+ifmm_status ifmm_inv_check(int nmat, const int* n, double* A, int* info);
+
 /* Measured arithmetic peak of the current GPU in TFLOP/s (no counterpart in the
  * paper: the denominators of the per-phase rooflines).  kind: 0 FP32 FMA, 1 FP64
  * FMA, 2 TF32 warp MMA (m16n8k8), 3 BF16 warp MMA (m16n8k16, FP32 accumulate),

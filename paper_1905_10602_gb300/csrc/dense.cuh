@@ -67,15 +67,21 @@ __global__ void k_copy_small(const CopyDesc* __restrict__ d, int nd) {
 // FP64 pipe (about 2 operations per clock per SM).  The FP32 kernels read and
 // write FP64 storage, so they convert with integer operations on the IEEE-754
 // fields instead, folding an optional power-of-two scale 2^sh into the
-// exponent.  d2f_pow2 rounds to nearest with ties away from zero (IEEE binary64
+// exponent.  No path of either function uses a floating-point instruction (the
+// compiler would evaluate a rare-path hardware conversion on every call and
+// select).  d2f_pow2 rounds to nearest with ties away from zero (IEEE binary64
 // -> binary32 keeps the top 23 of 52 fraction bits; the first dropped bit
-// decides); results below the binary32 normal range become signed zero, above it
-// infinity; NaN and infinity inputs and non-normal outputs of f2d_pow2 take the
-// hardware conversion (rare).
+// decides); results below the binary32 normal range become signed zero, above
+// it infinity; infinity and NaN stay infinity and (quiet) NaN.  f2d_pow2 widens
+// exactly (binary32 subnormals included); results below the binary64 normal
+// range become signed zero, above it infinity.
 __device__ __forceinline__ float d2f_pow2(double d, int sh) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned ah = hi & 0x7fffffffu, sg = hi & 0x80000000u;
-  if (ah >= 0x7ff00000u) return (float)d;
+  if (ah >= 0x7ff00000u) {
+    const bool nan = ah > 0x7ff00000u || lo != 0u;
+    return __uint_as_float(sg | 0x7f800000u | (nan ? 0x400000u | ((ah & 0x000fffffu) << 3) : 0u));
+  }
   const int e = (int)(ah >> 20) + sh;  // biased binary64 exponent after scaling
   if (ah < 0x00100000u || e <= 896) return __uint_as_float(sg);
   if (e >= 1151) return __uint_as_float(sg | 0x7f800000u);
@@ -87,9 +93,23 @@ __device__ __forceinline__ double f2d_pow2(float f, int sh) {
   const unsigned u = __float_as_uint(f);
   const unsigned a = u & 0x7fffffffu, sg = u & 0x80000000u;
   if (a == 0) return __hiloint2double((int)sg, 0);
-  const int e = (int)(a >> 23) + 896 + sh;  // biased binary64 exponent
-  if (a < 0x00800000u || a >= 0x7f800000u || e <= 0 || e >= 2047) return ldexp((double)f, sh);
-  return __hiloint2double((int)(sg | ((unsigned)e << 20) | ((a & 0x007fffffu) >> 3)), (int)(a << 29));
+  if (a >= 0x7f800000u) {
+    const unsigned m = a & 0x007fffffu;  // NaN payload (0: infinity)
+    return __hiloint2double((int)(sg | 0x7ff00000u | (m ? 0x80000u | (m >> 3) : 0u)), (int)(m << 29));
+  }
+  unsigned mant;
+  int e;  // biased binary64 exponent
+  if (a < 0x00800000u) {  // subnormal: a 2^-149, normalised
+    const int lz = __clz((int)a) - 8;
+    mant = (a << lz) & 0x007fffffu;
+    e = 897 - lz + sh;
+  } else {
+    mant = a & 0x007fffffu;
+    e = (int)(a >> 23) + 896 + sh;
+  }
+  if (e <= 0) return __hiloint2double((int)sg, 0);
+  if (e >= 2047) return __hiloint2double((int)(sg | 0x7ff00000u), 0);
+  return __hiloint2double((int)(sg | ((unsigned)e << 20) | (mant >> 3)), (int)(mant << 29));
 }
 // biased binary64 exponent of |d| (0 for zero and subnormals, 2047 for inf/NaN)
 __device__ __forceinline__ int dexp(double d) { return (int)(((unsigned)__double2hiint(d) & 0x7fffffffu) >> 20); }
@@ -267,10 +287,16 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ d, co
 // into TF32 head and tail, k-major with 8 words of padding (fragment loads
 // free of bank conflicts).  The epilogue goes through shared memory as a
 // column-major tile and every warp writes whole column segments of C.
+// x rounded to TF32 (10 fraction bits), to nearest with ties away from zero,
+// by integer operations on its bits: adding half a TF32 unit to the magnitude
+// and clearing the 13 dropped bits (a carry into the exponent is the correct
+// rounding).  Infinity stays infinity and NaN stays NaN (its quiet bit, which
+// survives the truncation, is set).  The conversion instruction would run on
+// the narrow FP64 pipe.
 __device__ __forceinline__ unsigned tf32_rn(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+  const unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (u & 0x7fffffu) ? ((u | 0x400000u) & 0xffffe000u) : u;
+  return (u + 0x1000u) & 0xffffe000u;
 }
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
   asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -555,12 +581,14 @@ __global__ void k_inv(const InvDesc* __restrict__ d, int nd, int smem_mat) {
     __syncthreads();
     if (s_bad) break;
     const int p = s_p;
-    if (p != k)
+    if (p != k) {
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double t = A[k + j * ld];
         A[k + j * ld] = A[p + j * ld];
         A[p + j * ld] = t;
       }
+      __syncthreads();  // p is the same in every thread: row k complete before it is read below
+    }
     // the reciprocal of the pivot once (an FP64 divide is a long FP64 sequence)
     if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];
     __syncthreads();
@@ -654,12 +682,14 @@ __global__ void k_gjb_pivot(const InvDesc* __restrict__ d, int nd, int k, double
   __syncthreads();
   if (D.info[0] != 0) return;
   const int p = s_p;
-  if (p != k)
+  if (p != k) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const double t = A[k + j * ld];
       A[k + j * ld] = A[p + j * ld];
       A[p + j * ld] = t;
     }
+    __syncthreads();  // p is the same in every thread: rows k and p swapped before they are read below
+  }
   __shared__ double s_inv;
   if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];  // once: an FP64 divide is a long FP64 sequence
   __syncthreads();

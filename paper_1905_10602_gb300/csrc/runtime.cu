@@ -28,6 +28,20 @@ Registry& registry() {
   return r;
 }
 
+bool poison_on() {
+  static const bool on = [] {
+    const char* e = getenv("IFMM_POISON");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+void poison_fill(void* p, size_t bytes) {
+  // earlier work on any stream may still use the memory being handed out again
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemset(p, 0x7e, bytes) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    (void)cudaGetLastError();  // e.g. during a stream capture: left unpoisoned
+}
+
 // bytes spanned by an m x n column-major block with leading dimension ld
 static size_t span(int m, int n, long ld) {
   if (m <= 0 || n <= 0) return 0;
@@ -1776,12 +1790,14 @@ __global__ void k_gj_pivot(double* A, long ld, int n, int k, int* piv, double* r
   __syncthreads();
   if (info[0] != 0) return;
   const int p = s_p;
-  if (p != k)
+  if (p != k) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const double t = A[k + j * ld];
       A[k + j * ld] = A[p + j * ld];
       A[p + j * ld] = t;
     }
+    __syncthreads();  // p is the same in every thread: rows k and p swapped before they are read below
+  }
   __shared__ double s_inv;
   if (threadIdx.x == 0) s_inv = 1.0 / A[k + k * ld];  // once: an FP64 divide is a long FP64 sequence
   __syncthreads();
@@ -1973,6 +1989,51 @@ ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, 
     std::vector<GemmDesc> v{gmm(dA, lda, ta, dB, ldb, tb, dC, ldc, m, n, k, alpha, beta)};
     launch_gemm(st, v, precision == IFMM_PREC_FP64 ? P64 : (precision == IFMM_PREC_FP32 ? P32 : P16));
     CK(cudaMemcpyAsync(C, dC, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st.release();
+    mem.release();
+    CK(cudaStreamDestroy(s));
+    return IFMM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+ifmm_status ifmm_inv_check(int nmat, const int* n, double* A, int* info) {
+  using namespace ifmm;
+  try {
+    IFMM_REQUIRE(nmat >= 0 && nmat <= 4096 && (nmat == 0 || (n && A && info)), IFMM_EINVAL, "bad arguments");
+    size_t tot = 0;
+    for (int i = 0; i < nmat; ++i) {
+      IFMM_REQUIRE(n[i] >= 1 && n[i] <= 4096, IFMM_EINVAL, "matrix order must be in [1, 4096]");
+      tot += (size_t)n[i] * n[i];
+    }
+    IFMM_REQUIRE(tot <= ((size_t)1 << 28), IFMM_EINVAL, "batch too large");
+    if (nmat == 0) return IFMM_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      throw Error(IFMM_ECUDA, "no CUDA device");
+    }
+    DescStage st;
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    st.stream = s;
+    DeviceArena mem;
+    double* dA = mem.alloc(tot);
+    int* dinfo = (int*)mem.alloc_bytes(sizeof(int) * (size_t)nmat);
+    CK(cudaMemcpyAsync(dA, A, sizeof(double) * tot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dinfo, 0, sizeof(int) * (size_t)nmat, s));
+    std::vector<InvDesc> v;
+    size_t off = 0;
+    for (int i = 0; i < nmat; ++i) {
+      v.push_back(InvDesc{dA + off, n[i], n[i], dinfo + i, 0});
+      off += (size_t)n[i] * n[i];
+    }
+    launch_inv(st, v);
+    CK(cudaMemcpyAsync(A, dA, sizeof(double) * tot, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(info, dinfo, sizeof(int) * (size_t)nmat, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     st.release();
     mem.release();

@@ -55,6 +55,13 @@ struct Registry {
 };
 Registry& registry();
 
+// Optional poisoning of new arena memory (IFMM_POISON=1): every allocation is
+// filled with the byte 0x7e (about 1e301 as a double, 2e38 as a float), so that
+// a kernel reading memory nothing wrote turns its results into overflow.
+// Debugging aid; it synchronizes the device on every allocation.
+bool poison_on();
+void poison_fill(void* p, size_t bytes);
+
 // Bump allocator over cudaMalloc'd chunks.  reset() makes the memory reusable;
 // callers only reset at points where all earlier work on the stream that uses
 // the memory has been ordered before later work (one stream) .
@@ -75,6 +82,7 @@ struct DeviceArena {
         void* r = chunks[ci].p + off;
         off += bytes;
         registry().add(r, bytes);
+        if (poison_on()) poison_fill(r, bytes);
         return r;
       }
       ++ci;
@@ -88,6 +96,7 @@ struct DeviceArena {
     off = bytes;
     high += sz;
     registry().add(p, bytes);
+    if (poison_on()) poison_fill(p, bytes);
     return p;
   }
   double* alloc(size_t n) { return (double*)alloc_bytes(n * sizeof(double)); }

@@ -69,6 +69,7 @@ _sig = {
     "ifmm_bd_factor": [_vp, ctypes.POINTER(Kernel), ctypes.c_int, _vp, ctypes.POINTER(_vp)],
     "ifmm_gemm_check": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _vp,
                         ctypes.c_int, _vp, ctypes.c_int, _dbl, _vp, ctypes.c_int],
+    "ifmm_inv_check": [ctypes.c_int, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
     getattr(lib, _name).argtypes = _args
@@ -336,6 +337,24 @@ def ifmm_gemm_check(precision: str, A, B, C=None, alpha: float = 1.0, beta: floa
                                max(1, A.shape[0]), B.ctypes.data_as(_vp), max(1, B.shape[0]), beta,
                                C.ctypes.data_as(_vp), max(1, m)))
     return C
+
+
+def ifmm_inv_check(mats):
+    """Inverses of a list of square NumPy matrices through the library's FP64
+    Gauss-Jordan pivot-block kernels (diagnostic); returns (inverses, info), info[i]
+    = 0 or the 1-based step with no nonzero pivot."""
+    ns = np.array([np.shape(a)[0] for a in mats], dtype=np.int32)
+    for a, n in zip(mats, ns):
+        assert np.shape(a) == (n, n)
+    flat = np.concatenate([np.asarray(a, dtype=np.float64).ravel(order="F") for a in mats]) if len(mats) else \
+        np.zeros(0)
+    info = np.zeros(len(mats), dtype=np.int32)
+    _check(lib.ifmm_inv_check(len(mats), ns.ctypes.data_as(_vp), flat.ctypes.data_as(_vp), info.ctypes.data_as(_vp)))
+    out, off = [], 0
+    for n in ns:
+        out.append(flat[off:off + n * n].reshape((n, n), order="F").copy())
+        off += n * n
+    return out, info
 
 
 PEAK_KINDS = {"fp32": 0, "fp64": 1, "tf32_mma": 2, "bf16_mma": 3, "fp64_mma": 4}

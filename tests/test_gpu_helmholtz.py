@@ -40,7 +40,8 @@ def test_helmholtz_matvec_matches_dense(k):
     assert _rel(y, dense_matrix(pts, k) @ x) < 1e-13
 
 
-@pytest.mark.parametrize("N,depth,p,sigma,k", [(900, 3, 3, 3, 2.0), (1200, 3, 3, 6, 8.0), (600, 2, 2, 3, 4.0)])
+@pytest.mark.parametrize("N,depth,p,sigma,k", [(900, 3, 3, 3, 2.0), (1200, 3, 3, 6, 8.0), (600, 2, 2, 3, 4.0),
+                                               (200, 2, 2, 3, 2.0), (60, 2, 2, 3, 2.0)])
 def test_helmholtz_exact_at_eps0(N, depth, p, sigma, k):
     pts = fibonacci_sphere(N, 2)
     b = helmholtz_source_rhs(pts, k)
@@ -112,3 +113,16 @@ def test_helmholtz_refusals():
         ifmm.bem_matvec(t, np.zeros(500, dtype=np.complex128), kernel=k)
     with pytest.raises(ifmm.IFMMError):
         ifmm.ifmm_bd_factor(t, 3, kernel=ifmm.helmholtz_kernel(500, 2.0))
+
+
+def test_factor_is_repeatable():
+    """The same factorization twice gives bit-identical solves (the pivot blocks
+    of the 2 x 2 form need row interchanges, which once raced with the reads of
+    the pivot row)."""
+    pts = fibonacci_sphere(200, 2)
+    k = 2.0
+    t = _tree(pts, 2, 3)
+    b = helmholtz_source_rhs(pts, k)
+    xs = [ifmm.ifmm_solve(ifmm.ifmm_factor(t, 2, 0.0, kernel=ifmm.helmholtz_kernel(200, k)), b) for _ in range(4)]
+    for x in xs[1:]:
+        assert np.array_equal(x, xs[0])
