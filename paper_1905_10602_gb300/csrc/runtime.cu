@@ -369,17 +369,20 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   // Size classes.  Blocks of n <= 32: one CTA each in shared memory.  Larger
   // ones: the FP64 elimination of one block on one SM is bound by that SM's FP64
   // pipe, so when a color has fewer large blocks than SMs each block is spread
-  // over a cluster of R CTAs (R ~ SMs / blocks, at most 8, and at least what its
-  // rows need to fit); R = 1 is one CTA in shared memory (n <= 160).  Blocks that
-  // fit no cluster take the batched multi-CTA kernels below.
+  // over a cluster of R CTAs (R ~ SMs / blocks, at most 16 -- a non-portable
+  // cluster size, used when the GPU can host it -- and at least what its rows
+  // need to fit); R = 1 is one CTA in shared memory (n <= 160).  Blocks that fit
+  // no cluster take the batched multi-CTA kernels below.
   static constexpr int kInvCta = 0;
   static constexpr size_t kInvClusterSmem = 220 * 1024;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     CK(cudaFuncSetAttribute(k_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
     CK(cudaFuncSetAttribute(k_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvClusterSmem));
+    if (cudaFuncSetAttribute(k_inv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaGetLastError();  // then the residency probe rejects R = 16
   });
-  static int cl_ok[4] = {0, 0, 0, 0};  // per R = 1, 2, 4, 8: 0 unknown, 1 yes, -1 no
+  static int cl_ok[5] = {0, 0, 0, 0, 0};  // per R = 1, 2, 4, 8, 16: 0 unknown, 1 yes, -1 no
   static std::mutex cl_mu;
   // IFMM_INV_FALLBACK_N=n (read once per process; tests) sends every block of
   // at least n rows to the batched multi-CTA kernels
@@ -391,9 +394,9 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
   int nbig = 0;
   for (auto& x : v) nbig += x.n > 32;
   int rwant = 1;
-  while (rwant < 8 && nbig * rwant * 2 <= 152) rwant *= 2;
-  std::vector<InvDesc> cls[3], ccl[4];
-  size_t csm[4] = {16, 16, 16, 16};
+  while (rwant < 16 && nbig * rwant * 2 <= 152) rwant *= 2;
+  std::vector<InvDesc> cls[3], ccl[5];
+  size_t csm[5] = {16, 16, 16, 16, 16};
   for (auto& x : v) {
     if (fallback_n && x.n >= fallback_n) {
       cls[2].push_back(x);
@@ -405,18 +408,26 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     }
     int R = rwant, q = 0;
     while ((1 << q) < R) ++q;
-    while (q < 4 && inv_cluster_slot_bytes(x.n, 1 << q) > kInvClusterSmem) ++q;
+    int qmin = 0;  // the smallest cluster whose slots hold the rows
+    while (qmin < 5 && inv_cluster_slot_bytes(x.n, 1 << qmin) > kInvClusterSmem) ++qmin;
+    if (q < qmin) q = qmin;
     if (q == 0 && x.n <= 160) {
       cls[1].push_back(x);
       continue;
     }
     if (q == 0) q = 1;
     bool ok = false;
-    if (q < 4) {
+    {
       std::lock_guard<std::mutex> lock(cl_mu);
-      if (cl_ok[q] == 0)
-        cl_ok[q] = launch_inv_cluster(nullptr, 1, 1 << q, kInvClusterSmem, st.stream, true) ? 1 : -1;
-      ok = cl_ok[q] > 0;
+      // the wanted size, else the next smaller one that still holds the rows
+      for (; q < 5 && q >= std::max(1, qmin); --q) {
+        if (cl_ok[q] == 0)
+          cl_ok[q] = launch_inv_cluster(nullptr, 1, 1 << q, kInvClusterSmem, st.stream, true) ? 1 : -1;
+        if (cl_ok[q] > 0) {
+          ok = true;
+          break;
+        }
+      }
     }
     if (ok) {
       ccl[q].push_back(x);
@@ -426,17 +437,17 @@ void launch_inv(DescStage& st, const std::vector<InvDesc>& v) {
     }
   }
   (void)kInvCta;
-  const InvDesc* dcl[4] = {};
-  for (int q = 1; q < 4; ++q)
+  const InvDesc* dcl[5] = {};
+  for (int q = 1; q < 5; ++q)
     if (!ccl[q].empty()) dcl[q] = st.push(ccl[q]);
   int ncl = 0;
-  for (int q = 1; q < 4; ++q) ncl += (int)ccl[q].size();
+  for (int q = 1; q < 5; ++q) ncl += (int)ccl[q].size();
   if (ncl) {
     prof_batch_tag() = (long)ncl;
     cudaEvent_t pe = profiler().begin(KK_INV, st.stream);
     ForkJoin fj(st.stream);
     int li = 0;
-    for (int q = 1; q < 4; ++q) {
+    for (int q = 1; q < 5; ++q) {
       if (ccl[q].empty()) continue;
       launch_inv_cluster(dcl[q], (int)ccl[q].size(), 1 << q, csm[q], fj.stream(li++), false);
       check_launch("k_inv_cluster");
@@ -570,7 +581,9 @@ static void launch_qr_fitting(DescStage& st, const std::vector<QrcpDesc>& v, int
   const size_t lim = qr_cta_limit();
   const size_t cls[5] = {std::min(kQrWarpSlot, lim), std::min<size_t>(24 * 1024, lim), std::min<size_t>(48 * 1024, lim),
                          std::min<size_t>(96 * 1024, lim), lim};
-  const int thr[5] = {0, 256, 256, 512, 1024};
+  // (a launch of fewer problems than SMs gives every CTA 1024 threads)
+  const bool few = v.size() < 152;
+  const int thr[5] = {0, few ? 1024 : 256, few ? 1024 : 256, few ? 1024 : 512, 1024};
   std::vector<QrcpDesc> part[5];
   size_t smax[5] = {16, 16, 16, 16, 16};
   for (auto& x : v) {
@@ -830,8 +843,10 @@ void launch_svd_rt(DescStage& st, const std::vector<SvdRtDesc>& v, int prec) {
   for (int c = 0; c < 4; ++c) {
     if (part[c].empty()) continue;
     const int smem = (int)std::min<size_t>(smem_cap, ((size_t)nmx[c] * nmx[c] * tcb + 15) & ~(size_t)15);
-    const int threads = std::min(512, std::max(64, 32 * ((nmx[c] + 1) / 2)));
     const unsigned g = (unsigned)part[c].size();
+    // one warp per column pair of the widest problem, up to 16 warps; up to 32
+    // when the class has fewer problems than SMs (nothing else to hide latency)
+    const int threads = std::min(g < 152 ? 1024 : 512, std::max(64, 32 * ((nmx[c] + 1) / 2)));
     cudaStream_t s = fj.stream(li++);
     if (prec == P32)
       k_svd_rt<float><<<g, threads, smem, s>>>(d[c], (int)g, 60, smem);
