@@ -305,6 +305,20 @@ ifmm_status ifmm_convert_check(const double* x, int64_t n, int shift, float* f, 
 ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, double alpha, const double* A, int lda,
                             const double* B, int ldb, double beta, double* C, int ldc);
 
+/* The Householder QR of the recompression (Algorithm 1's truncated QR of the
+ * fill-in blocks, and the QR of the weight stacks), on a host array, through
+ * the same kernels and size classes as the factorization (a warp, a CTA, a
+ * thread-block cluster, row-chunked reduction or the global-memory kernel, by
+ * the block's size).  A is m x n column-major with
+ * leading dimension ld >= m (m <= 65536, n <= 1024, ld n <= 2^27), in FP64 or
+ * rounded to FP32 as the precision says (IFMM_PREC_FP64 or IFMM_PREC_FP32).
+ * On return the leading min(m, n) rows of A hold R (zeros below its diagonal).
+ * With pivoted != 0 the columns are pivoted by largest remaining norm and run to
+ * completion (no truncation): jpvt[p] is the original index of column p of R
+ * and *k the number of steps; jpvt and k are not read otherwise.  Rows of A
+ * below R are unspecified.  Synchronous; IFMM_ECUDA without a device. */
+ifmm_status ifmm_qr_check(int precision, int pivoted, int m, int n, double* A, int ld, int* jpvt, int* k);
+
 /* The FP64 Gauss-Jordan inverse with partial pivoting of the pivot blocks
  * (Algorithm 1's inverses of Pi_i), on host arrays, through the same size
  * classes as the factorization (one CTA in shared memory, a thread-block

@@ -310,9 +310,12 @@ struct Factorizer {
       float* dx = (float*)scratch().alloc(feat.size() / 2 + 1);
       float* dy = (float*)scratch().alloc(evs.size() / 2 + 1);
       CK(cudaMemcpyAsync(dx, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, s));
-      mlp_predict_device(d_mlp, dx, dy, (int)evs.size(), s);
-      std::vector<float> pred(evs.size());
-      CK(cudaMemcpy(pred.data(), dy, sizeof(float) * evs.size(), cudaMemcpyDeviceToHost));
+      float* dwk = (float*)scratch().alloc(mlp_predict_floats((int)evs.size()) / 2 + 1);
+      mlp_predict_device(d_mlp, dx, dy, (int)evs.size(), s, dwk);
+      float* hpred = (float*)st.host_alloc(sizeof(float) * evs.size());
+      CK(cudaMemcpyAsync(hpred, dy, sizeof(float) * evs.size(), cudaMemcpyDeviceToHost, s));
+      wait();
+      const std::vector<float> pred(hpred, hpred + evs.size());
       for (size_t e = 0; e < evs.size(); ++e) {
         // sketch width: predicted rank plus oversampling
         const double k = std::max(0.0, (double)pred[e]) * 64.0;
@@ -550,6 +553,14 @@ struct Factorizer {
       hi = (int*)st.host_alloc(sizeof(int) * n_inv);
       CK(cudaMemcpyAsync(hi, d_info, sizeof(int) * n_inv, cudaMemcpyDeviceToHost, s));
     }
+    // learned mode: the sketches' residual and input norms, in the same readback
+    double* hen = nullptr;
+    if (learned && !evs.empty()) {
+      hen = (double*)st.host_alloc(sizeof(double) * 4 * evs.size());
+      CK(cudaMemcpyAsync(hen, enorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hen + 2 * evs.size(), ynorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost,
+                         s));
+    }
     wait();
     if (sig_total) memcpy(hsig.data(), hp, sig_total * sizeof(double));
     if (!evs.empty()) memcpy(hk.data(), hkp, sizeof(int) * 2 * evs.size());
@@ -562,9 +573,7 @@ struct Factorizer {
       // a-posteriori check of every sketch: ||Y - B Q^T||_F (>= the 2-norm of
       // what the range finder missed) must be <= eps * sigma_1; sides that fail
       // run the exact path on Y, which the randomized path left untouched
-      std::vector<double> en(2 * evs.size()), yn(2 * evs.size());
-      CK(cudaMemcpy(en.data(), enorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(yn.data(), ynorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost));
+      const std::vector<double> en(hen, hen + 2 * evs.size()), yn(hen + 2 * evs.size(), hen + 4 * evs.size());
       // below 16 units of roundoff of the arithmetic (times ||Y||_F) no
       // recompression in that arithmetic can certify anything
       const double unit = prec == P32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
@@ -586,14 +595,18 @@ struct Factorizer {
         n_fallback += (double)redo.size() * 0.5;
         launch_qrcp(st, rqp, prec);
         launch_svd_rt(st, rsr, prec);
+        // one readback of every count and spectrum (the redone ones changed)
+        double* hp2 = (double*)st.host_alloc(sizeof(double) * std::max<size_t>(sig_total, 1));
+        int* hk2 = (int*)st.host_alloc(sizeof(int) * 2 * evs.size());
+        if (sig_total) CK(cudaMemcpyAsync(hp2, sig_all, sizeof(double) * sig_total, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hk2, kall, sizeof(int) * 2 * evs.size(), cudaMemcpyDeviceToHost, s));
         wait();
-        st.reset();
         for (auto& rd : redo) {
-          Event& ev = evs[rd.first];
-          CK(cudaMemcpy(hsig.data() + ev.sig_off[rd.second], ev.sig[rd.second], sizeof(double) * ev.n,
-                        cudaMemcpyDeviceToHost));
-          CK(cudaMemcpy(&hk[2 * rd.first + rd.second], ev.kdev[rd.second], sizeof(int), cudaMemcpyDeviceToHost));
+          const Event& ev = evs[rd.first];
+          memcpy(hsig.data() + ev.sig_off[rd.second], hp2 + ev.sig_off[rd.second], sizeof(double) * ev.n);
+          hk[2 * rd.first + rd.second] = hk2[2 * rd.first + rd.second];
         }
+        st.reset();
       }
     }
     for (size_t e = 0; e < evs.size(); ++e)

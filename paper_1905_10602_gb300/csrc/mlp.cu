@@ -126,6 +126,15 @@ struct MlpBuffers {
     }
     sq = get(n);
   }
+  // forward only: input and output in place, the hidden activations in work
+  MlpBuffers(int n, const float* x, float* y, float* work) : ns(n) {
+    act[0] = const_cast<float*>(x);
+    for (int l = 1; l < 4; ++l) {
+      act[l] = work;
+      work += (size_t)n * kDims[l];
+    }
+    act[4] = y;
+  }
   ~MlpBuffers() {
     for (auto p : owned) cudaFree(p);
   }
@@ -158,13 +167,12 @@ static void mlp_backward(const float* w, const float* t, float* g, MlpBuffers& B
   }
 }
 
-void mlp_predict_device(const float* d_w, const float* d_x, float* d_y, int ns, cudaStream_t s) {
+size_t mlp_predict_floats(int ns) { return (size_t)std::max(ns, 1) * (kDims[1] + kDims[2] + kDims[3]); }
+
+void mlp_predict_device(const float* d_w, const float* d_x, float* d_y, int ns, cudaStream_t s, float* work) {
   if (ns <= 0) return;
-  MlpBuffers B(ns);
-  CKM(cudaMemcpyAsync(B.act[0], d_x, sizeof(float) * ns * kIn, cudaMemcpyDeviceToDevice, s));
+  MlpBuffers B(ns, d_x, d_y, work);
   mlp_forward(d_w, B, ns, s);
-  CKM(cudaMemcpyAsync(d_y, B.act[4], sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
-  CKM(cudaStreamSynchronize(s));
 }
 
 }  // namespace ifmm

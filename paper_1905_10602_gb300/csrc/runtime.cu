@@ -2015,6 +2015,58 @@ ifmm_status ifmm_gemm_check(int precision, int m, int n, int k, int ta, int tb, 
   }
 }
 
+ifmm_status ifmm_qr_check(int precision, int pivoted, int m, int n, double* A, int ld, int* jpvt, int* k) {
+  using namespace ifmm;
+  try {
+    IFMM_REQUIRE((precision == IFMM_PREC_FP64 || precision == IFMM_PREC_FP32) && m >= 1 && n >= 1 && m <= 65536 &&
+                     n <= 1024 && ld >= m && A && (!pivoted || (jpvt && k)),
+                 IFMM_EINVAL, "bad arguments");
+    IFMM_REQUIRE((size_t)ld * n <= ((size_t)1 << 27), IFMM_EINVAL, "matrix too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      throw Error(IFMM_ECUDA, "no CUDA device");
+    }
+    const int prec = precision == IFMM_PREC_FP64 ? P64 : P32;
+    DescStage st;
+    cudaStream_t s;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    st.stream = s;
+    DeviceArena mem;
+    const size_t na = (size_t)ld * n;
+    double* dA = mem.alloc(na);
+    int* dj = (int*)mem.alloc_bytes(sizeof(int) * (size_t)n);
+    int* dk = (int*)mem.alloc_bytes(sizeof(int));
+    CK(cudaMemcpyAsync(dA, A, sizeof(double) * na, cudaMemcpyHostToDevice, s));
+    if (pivoted) {
+      QrcpDesc q{};
+      q.A = dA;
+      q.ld = ld;
+      q.m = m;
+      q.n = n;
+      q.tau_rel = 0.0;
+      q.jpvt = dj;
+      q.kout = dk;
+      launch_qrcp(st, std::vector<QrcpDesc>{q}, prec);
+    } else {
+      launch_qr(st, std::vector<QrDesc>{QrDesc{dA, ld, m, n}}, prec);
+    }
+    CK(cudaMemcpyAsync(A, dA, sizeof(double) * na, cudaMemcpyDeviceToHost, s));
+    if (pivoted) {
+      CK(cudaMemcpyAsync(jpvt, dj, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(k, dk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    st.release();
+    mem.release();
+    CK(cudaStreamDestroy(s));
+    return IFMM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
 ifmm_status ifmm_inv_check(int nmat, const int* n, double* A, int* info) {
   using namespace ifmm;
   try {

@@ -70,6 +70,7 @@ _sig = {
     "ifmm_gemm_check": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _vp,
                         ctypes.c_int, _vp, ctypes.c_int, _dbl, _vp, ctypes.c_int],
     "ifmm_inv_check": [ctypes.c_int, _vp, _vp, _vp],
+    "ifmm_qr_check": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp],
 }
 for _name, _args in _sig.items():
     getattr(lib, _name).argtypes = _args
@@ -337,6 +338,20 @@ def ifmm_gemm_check(precision: str, A, B, C=None, alpha: float = 1.0, beta: floa
                                max(1, A.shape[0]), B.ctypes.data_as(_vp), max(1, B.shape[0]), beta,
                                C.ctypes.data_as(_vp), max(1, m)))
     return C
+
+
+def ifmm_qr_check(A, precision: str = "fp64", pivoted: bool = False):
+    """Householder QR of a NumPy matrix through the library's recompression QR
+    kernels (diagnostic): returns R (min(m, n) x n), and with pivoted also the
+    column order and the number of steps."""
+    A = np.asfortranarray(A, dtype=np.float64).copy(order="F")
+    m, n = A.shape
+    jp = np.zeros(n, dtype=np.int32)
+    k = ctypes.c_int(0)
+    _check(lib.ifmm_qr_check(PREC[precision], int(pivoted), m, n, A.ctypes.data_as(_vp), m, jp.ctypes.data_as(_vp),
+                             ctypes.byref(k)))
+    R = np.triu(A[:min(m, n), :])
+    return (R, jp, k.value) if pivoted else R
 
 
 def ifmm_inv_check(mats):
