@@ -58,8 +58,8 @@ struct ifmm_tree {
   double* d_pts = nullptr;    // SoA: x[N], y[N], z[N] in tree order
   int32_t* d_perm = nullptr;  // tree order -> caller index
   float* d_pts_df = nullptr;  // points as float pairs: xh xl yh yl zh zl [N] each
-  int matvec_block = 0;       // autotuned source tile of the float-pair matvec (0: not yet)
-  std::vector<int32_t> matvec_block_v{0};
+  int matvec_block = 0;       // autotuned tile of the float-pair matvec, BS | TPT << 16 (0: not yet)
+  std::vector<int32_t> matvec_block_v{0, 0};
   int device = -1;
   ifmm::FmmPlan* fmm = nullptr;  // cached by the first FMM matvec
   void ensure_device();

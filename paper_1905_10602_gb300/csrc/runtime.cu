@@ -1388,57 +1388,65 @@ __global__ void k_split_df(const double* __restrict__ in, float* __restrict__ hi
 }
 
 // pts: 6 float arrays (xh, xl, yh, yl, zh, zl) of length n; q: (qh, ql).
-// BS threads per CTA = sources per shared-memory tile (autotuned per tree).
-template <int BS>
+// BS threads per CTA = sources per shared-memory tile; TPT targets per thread
+// (TPT = 2: each source read from shared memory serves two independent
+// accumulation chains).  A source tile is two float4 per source (x, y / z, q as
+// pairs), read as two broadcast 16-byte loads.  Both autotuned per tree.
+template <int BS, int TPT>
 __global__ void __launch_bounds__(BS) k_matvec_df(const float* __restrict__ pts, const float* __restrict__ qh,
                                                   const float* __restrict__ ql, const double* __restrict__ x,
                                                   double* __restrict__ y, int n, double scale, double diag) {
-  __shared__ float s[8][BS];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ float4 sa[BS], sb[BS];  // (xh, xl, yh, yl), (zh, zl, qh, ql)
   const float* xh = pts;
   const float* xl = pts + n;
   const float* yh = pts + 2 * (long)n;
   const float* yl = pts + 3 * (long)n;
   const float* zh = pts + 4 * (long)n;
   const float* zl = pts + 5 * (long)n;
-  df px = {0.f, 0.f}, py = {0.f, 0.f}, pz = {0.f, 0.f};
-  if (i < n) {
-    px = {xh[i], xl[i]};
-    py = {yh[i], yl[i]};
-    pz = {zh[i], zl[i]};
+  int ii[TPT];
+  df px[TPT], py[TPT], pz[TPT], acc[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int i = blockIdx.x * (BS * TPT) + u * BS + threadIdx.x;
+    ii[u] = i;
+    px[u] = py[u] = pz[u] = acc[u] = {0.f, 0.f};
+    if (i < n) {
+      px[u] = {xh[i], xl[i]};
+      py[u] = {yh[i], yl[i]};
+      pz[u] = {zh[i], zl[i]};
+    }
   }
-  df acc = {0.f, 0.f};
-  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+  for (int j0 = 0; j0 < n; j0 += BS) {
     const int j = j0 + threadIdx.x;
     if (j < n) {
-      s[0][threadIdx.x] = xh[j];
-      s[1][threadIdx.x] = xl[j];
-      s[2][threadIdx.x] = yh[j];
-      s[3][threadIdx.x] = yl[j];
-      s[4][threadIdx.x] = zh[j];
-      s[5][threadIdx.x] = zl[j];
-      s[6][threadIdx.x] = qh[j];
-      s[7][threadIdx.x] = ql[j];
+      sa[threadIdx.x] = make_float4(xh[j], xl[j], yh[j], yl[j]);
+      sb[threadIdx.x] = make_float4(zh[j], zl[j], qh[j], ql[j]);
     }
     __syncthreads();
-    const int cnt = min((int)blockDim.x, n - j0);
+    const int cnt = min(BS, n - j0);
     for (int t = 0; t < cnt; ++t) {
-      // d = p_i - p_j per axis: two-sum of the high parts plus the low parts
-      // (not renormalised: it is squared next)
-      const df dx = df_diff(px, s[0][t], s[1][t]);
-      const df dy = df_diff(py, s[2][t], s[3][t]);
-      const df dz = df_diff(pz, s[4][t], s[5][t]);
-      // r^2 = sum d^2: FMA two-product of the high parts, 2 h l for the rest
-      const df r2 = df_sum3(df_sq(dx), df_sq(dy), df_sq(dz));
-      const df w = df_rsqrt_fast(r2);
-      // q_j / r as a pair, added with a two-sum
-      const float ph = s[6][t] * w.h;
-      const float pl = fmaf(s[6][t], w.h, -ph) + fmaf(s[6][t], w.l, s[7][t] * w.h);
-      if (j0 + t != i) acc = df_acc(acc, ph, pl);
+      const float4 a = sa[t], b = sb[t];
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        // d = p_i - p_j per axis: two-sum of the high parts plus the low parts
+        // (not renormalised: it is squared next)
+        const df dx = df_diff(px[u], a.x, a.y);
+        const df dy = df_diff(py[u], a.z, a.w);
+        const df dz = df_diff(pz[u], b.x, b.y);
+        // r^2 = sum d^2: FMA two-product of the high parts, 2 h l for the rest
+        const df r2 = df_sum3(df_sq(dx), df_sq(dy), df_sq(dz));
+        const df w = df_rsqrt_fast(r2);
+        // q_j / r as a pair, added with a two-sum
+        const float ph = b.z * w.h;
+        const float pl = fmaf(b.z, w.h, -ph) + fmaf(b.z, w.l, b.w * w.h);
+        if (j0 + t != ii[u]) acc[u] = df_acc(acc[u], ph, pl);
+      }
     }
     __syncthreads();
   }
-  if (i < n) y[i] = diag * x[i] + scale * ((double)acc.h + (double)acc.l);
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+    if (ii[u] < n) y[ii[u]] = diag * x[ii[u]] + scale * ((double)acc[u].h + (double)acc[u].l);
 }
 
 // ---------------------------------------------------------------- the solve's row operations
@@ -1620,23 +1628,32 @@ void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int
   check_launch("k_split_df");
 }
 
-static void matvec_df_bs(int bs, cudaStream_t s, const float* pts_df, const float* qh, const float* ql,
+// the tile code: BS | TPT << 16
+static void matvec_df_bs(int code, cudaStream_t s, const float* pts_df, const float* qh, const float* ql,
                          const double* x, double* y, int N, double scale, double diag) {
-  if (bs == 128)
-    k_matvec_df<128><<<(N + 127) / 128, 128, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
-  else if (bs == 512)
-    k_matvec_df<512><<<(N + 511) / 512, 512, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
-  else
-    k_matvec_df<256><<<(N + 255) / 256, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  const int bs = code & 0xffff, tpt = code >> 16;
+  if (tpt == 2) {
+    if (bs == 128)
+      k_matvec_df<128, 2><<<(N + 255) / 256, 128, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+    else
+      k_matvec_df<256, 2><<<(N + 511) / 512, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  } else if (bs == 128) {
+    k_matvec_df<128, 1><<<(N + 127) / 128, 128, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  } else if (bs == 512) {
+    k_matvec_df<512, 1><<<(N + 511) / 512, 512, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  } else {
+    k_matvec_df<256, 1><<<(N + 255) / 256, 256, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
+  }
 }
 
-// Autotuner: times each source-tile width twice on the caller's data (after one
-// untimed launch of each) and returns the fastest; y is overwritten.
+// Autotuner: times each source-tile width and targets-per-thread count twice on
+// the caller's data (after one untimed launch of each) and returns the fastest
+// as BS | TPT << 16; y is overwritten.
 int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x,
                        double* y, int N, double scale, double diag) {
-  const int cand[3] = {128, 256, 512};
+  const int cand[5] = {128 | 1 << 16, 256 | 1 << 16, 512 | 1 << 16, 128 | 2 << 16, 256 | 2 << 16};
   float best = 1e30f;
-  int pick = 256;
+  int pick = 256 | 1 << 16;
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));

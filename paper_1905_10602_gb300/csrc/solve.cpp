@@ -497,7 +497,7 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       ifmm_tree* tm = const_cast<ifmm_tree*>(t);
       if (!tm->matvec_block) {
         tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag);
-        tm->matvec_block_v[0] = tm->matvec_block;
+        tm->matvec_block_v = {tm->matvec_block & 0xffff, tm->matvec_block >> 16};
       }
       launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tm->matvec_block);
     } else {
@@ -584,7 +584,7 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
           std::lock_guard<std::mutex> lock(g_tune_mutex);
           if (!tm->matvec_block) {
             tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag);
-            tm->matvec_block_v[0] = tm->matvec_block;
+            tm->matvec_block_v = {tm->matvec_block & 0xffff, tm->matvec_block >> 16};
           }
         }
         launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tm->matvec_block);

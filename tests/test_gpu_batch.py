@@ -48,9 +48,10 @@ def test_batch_workload_recipe():
 def test_autotuned_matvec_tile():
     pts = fibonacci_sphere(6000, 2)
     t = ifmm.ifmm_build_tree(pts, 4)
-    assert ifmm.ifmm_tree_query(t, 0, "matvec_block")[0] == 0
+    assert list(ifmm.ifmm_tree_query(t, 0, "matvec_block")) == [0, 0]
     x = np.random.default_rng(5).standard_normal(len(pts))
     y = ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(len(pts), "df"))
-    assert ifmm.ifmm_tree_query(t, 0, "matvec_block")[0] in (128, 256, 512)
+    tile = ifmm.ifmm_tree_query(t, 0, "matvec_block")
+    assert tile[0] in (128, 256, 512) and tile[1] in (1, 2) and (tile[1] == 1 or tile[0] <= 256)
     ref = dense_matrix(pts) @ x
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-12
