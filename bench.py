@@ -49,6 +49,15 @@ METRIC = "IFMM factor+solve s at N=131k, eps=1e-6: mixed/learned vs plain FP64, 
 # from its source (three pair differences, squares and their sum, the refined
 # reciprocal square root, the product with the charge and the accumulation)
 MATVEC_DF_OPS_PER_PAIR = 75
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) summed over the
+# kernels of each class in one factor + GMRES(30) of the bumpy sphere at
+# N = 32,768, depth 5, FP32 path: the --ncu-case command, captured with those
+# two metrics and gpu__time_duration.sum.  ncu flushes L2 before every launch,
+# so these are cold-cache bytes.  The classes listed have work linear in N at
+# fixed points per leaf; the default line scales them by N / 32,768.
+NCU_DRAM_BYTES_BUMPY32K = {"qr_fp32": 10.812e9, "svd_fp32": 0.411e9, "gemm_fp32": 18.600e9,
+                           "gauss_jordan": 0.117e9, "solve_graph": 1.636e9}
+NCU_CAPTURE_N = 32768
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -463,11 +472,21 @@ def main():
             prof[f"qr_{g}"] = (n1, m1)
     phases = phase_rooflines(prof, pstats, peaks, args.precision if args.precond == "ifmm" else "fp64", w.n, pits,
                              matvec=None if args.wavenumber else arith)
+    # measured DRAM traffic, where the capture applies (the default workload and path)
+    captured = (args.workload == "bumpy131k" and args.precision == "fp32" and args.rank_mode == "svd"
+                and args.precond == "ifmm" and arith == "df" and not args.wavenumber and args.tau == 2
+                and not args.sigma)
+    for e in phases:
+        b = NCU_DRAM_BYTES_BUMPY32K.get(e["kernel"]) if captured else None
+        e["traffic"] = b * w.n / NCU_CAPTURE_N if b is not None else None
+        if b is not None:
+            e["traffic_unit"] = "bytes per step (ncu, N=32,768 capture scaled by N)"
     top = max(phases, key=lambda e: e["ms_per_step"]) if phases else None
     roof = None
     if top is not None:
         roof = {"bound": top["bound"], "kernel": top["kernel"], "achieved": top["achieved"], "peak": top["peak"],
-                "unit": top["unit"], "frac": top["frac"], "traffic": None, "ms_per_step": top["ms_per_step"],
+                "unit": top["unit"], "frac": top["frac"], "traffic": top.get("traffic"),
+                "traffic_unit": top.get("traffic_unit"), "ms_per_step": top["ms_per_step"],
                 "launches_per_step": top["launches_per_step"], "peak_note": top["peak_note"],
                 "timing": "per-launch CUDA events on the launching stream, one profiled step after the timed region"}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
