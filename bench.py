@@ -477,9 +477,9 @@ def main():
                 and args.precond == "ifmm" and arith == "df" and not args.wavenumber and args.tau == 2
                 and not args.sigma)
     for e in phases:
-        b = NCU_DRAM_BYTES_BUMPY32K.get(e["kernel"]) if captured else None
-        e["traffic"] = b * w.n / NCU_CAPTURE_N if b is not None else None
-        if b is not None:
+        cap_bytes = NCU_DRAM_BYTES_BUMPY32K.get(e["kernel"]) if captured else None
+        e["traffic"] = cap_bytes * w.n / NCU_CAPTURE_N if cap_bytes is not None else None
+        if cap_bytes is not None:
             e["traffic_unit"] = "bytes per step (ncu, N=32,768 capture scaled by N)"
     top = max(phases, key=lambda e: e["ms_per_step"]) if phases else None
     roof = None
