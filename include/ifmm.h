@@ -146,7 +146,9 @@ ifmm_status ifmm_color_levels(ifmm_tree* t, int sigma, int tau, int32_t* ncolors
  *   "leaf_ptr"        point CSR of the leaves (level ignored)
  *   "matvec_block"    2 values: the source tile (threads per CTA) and the targets
  *                     per thread of the float-pair matvec, chosen by its autotuner
- *                     on the first such product with this tree (0, 0 before)
+ *                     on the first such product with this tree (0, 0 before); the
+ *                     choice is remembered per device and N for the life of the
+ *                     process, and trees of a size tuned before reuse it
  * Writes min(count, cap) int32 values to buf (may be NULL) and the full count to
  * *count. */
 ifmm_status ifmm_tree_query(const ifmm_tree* t, int level, const char* what, int32_t* buf, int64_t cap,

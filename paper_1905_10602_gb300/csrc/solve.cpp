@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "fact.h"
@@ -326,6 +327,27 @@ void run_solve_tree(const ifmm_fact& F, const double* in, double* out, cudaStrea
 
 static std::mutex g_tune_mutex;
 
+// The float-pair matvec's tile for a tree: the autotuner's choice, remembered
+// per device and point count for the life of the process, so that trees of a
+// size already seen (a new tree per problem, as in a time loop) skip the
+// timing runs (fifteen launches of the full product).
+static int matvec_tile(ifmm_tree* tm, cudaStream_t s, const float* q, const double* in, double* out, int64_t N,
+                       const ifmm_kernel* k) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (tm->matvec_block) return tm->matvec_block;
+  static std::map<std::pair<int, int64_t>, int> seen;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  auto it = seen.find({dev, N});
+  const int code = it != seen.end()
+                       ? it->second
+                       : autotune_matvec_df(s, tm->d_pts_df, q, q + N, in, out, (int)N, k->scale, k->diag);
+  seen[{dev, N}] = code;
+  tm->matvec_block = code;
+  tm->matvec_block_v = {code & 0xffff, code >> 16};
+  return code;
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -495,11 +517,8 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       float* q = (float*)V.get(N);
       launch_split_df(s, a, q, q + N, (int)N);
       ifmm_tree* tm = const_cast<ifmm_tree*>(t);
-      if (!tm->matvec_block) {
-        tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag);
-        tm->matvec_block_v = {tm->matvec_block & 0xffff, tm->matvec_block >> 16};
-      }
-      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tm->matvec_block);
+      const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, q, a, b, N, k);
+      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tile);
     } else {
       launch_matvec(s, t->d_pts, (int)NP, a, b, *k);
     }
@@ -580,14 +599,8 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
       } else if (df_mv) {
         launch_split_df(s, in, qdf, qdf + N, (int)N);
         ifmm_tree* tm = const_cast<ifmm_tree*>(t);
-        if (!tm->matvec_block) {
-          std::lock_guard<std::mutex> lock(g_tune_mutex);
-          if (!tm->matvec_block) {
-            tm->matvec_block = autotune_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag);
-            tm->matvec_block_v = {tm->matvec_block & 0xffff, tm->matvec_block >> 16};
-          }
-        }
-        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tm->matvec_block);
+        const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, qdf, in, out, N, k);
+        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tile);
       } else {
         launch_matvec(s, t->d_pts, (int)NP, in, out, *k);
       }
