@@ -49,6 +49,10 @@ METRIC = "IFMM factor+solve s at N=131k, eps=1e-6: mixed/learned vs plain FP64, 
 # from its source (three pair differences, squares and their sum, the refined
 # reciprocal square root, the product with the charge and the accumulation)
 MATVEC_DF_OPS_PER_PAIR = 75
+# the symmetric kernel: one 1/r per unordered pair serves two entries; its
+# FP32 operations per evaluated pair (the 75 above plus the second product and
+# float-pair accumulation)
+MATVEC_SYM_OPS_PER_PAIR = 91
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) summed over the
 # kernels of each class in one factor + GMRES(30) of the bumpy sphere at
 # N = 32,768, depth 5, FP32 path: the --ncu-case command, captured with those
@@ -266,7 +270,7 @@ def measured_peaks(ifmm):
     return out
 
 
-def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1, matvec=None):
+def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1, matvec=None, symmetric=False):
     """One roofline entry per kernel class of the profiled step: counted work /
     CUDA-event time of the class on its launching stream, against the measured
     peak of the unit that bounds it."""
@@ -307,14 +311,18 @@ def phase_rooflines(prof, stats, peaks, precision, n, its, steps_profiled=1, mat
     elif matvec == "df":
         n_, ms = prof.get("matvec", (0, 0.0))
         if n_ and ms > 0:
-            pairs = float(n) * n * n_ / steps_profiled
+            ops = MATVEC_SYM_OPS_PER_PAIR if symmetric else MATVEC_DF_OPS_PER_PAIR
+            per_call = float(n) * (n - 1) / 2.0 if symmetric else float(n) * n
+            pairs = per_call * n_ / steps_profiled
             ach = pairs / (ms / steps_profiled / 1e3)
-            pk = peaks["fp32"] * 1e12 / 2.0 / MATVEC_DF_OPS_PER_PAIR
-            ents.append({"phase": "a11 direct-sum matvec (float pairs)", "kernel": "matvec", "bound": "alu",
-                         "achieved": ach / 1e9, "peak": pk / 1e9, "unit": "Gpairs/s", "frac": ach / pk,
-                         "ms_per_step": ms / steps_profiled, "launches_per_step": n_ // steps_profiled,
-                         "peak_note": f"measured FP32 FMA issue rate / {MATVEC_DF_OPS_PER_PAIR} FP32 operations "
-                                      "per pair (of measured)"})
+            pk = peaks["fp32"] * 1e12 / 2.0 / ops
+            ents.append({"phase": "a11 direct-sum matvec (float pairs" + (", symmetric)" if symmetric else ")"),
+                         "kernel": "matvec", "bound": "alu", "achieved": ach / 1e9, "peak": pk / 1e9,
+                         "unit": "Gpairs/s", "frac": ach / pk, "ms_per_step": ms / steps_profiled,
+                         "launches_per_step": n_ // steps_profiled,
+                         "peak_note": f"measured FP32 FMA issue rate / {ops} FP32 operations per evaluated pair"
+                                      + (" (unordered pairs: each 1/r serves two entries)" if symmetric else "")
+                                      + " (of measured)"})
     return ents
 
 
@@ -470,8 +478,9 @@ def main():
                 n1, m1 = n1 + n2, m1 + (m2 if sub.startswith("qr_global") else 0.0)
         if n1:
             prof[f"qr_{g}"] = (n1, m1)
+    tile = list(ifmm.ifmm_tree_query(tree, 0, "matvec_block"))
     phases = phase_rooflines(prof, pstats, peaks, args.precision if args.precond == "ifmm" else "fp64", w.n, pits,
-                             matvec=None if args.wavenumber else arith)
+                             matvec=None if args.wavenumber else arith, symmetric=len(tile) > 1 and tile[1] == 3)
     # measured DRAM traffic, where the capture applies (the default workload and path)
     captured = (args.workload == "bumpy131k" and args.precision == "fp32" and args.rank_mode == "svd"
                 and args.precond == "ifmm" and arith == "df" and not args.wavenumber and args.tau == 2

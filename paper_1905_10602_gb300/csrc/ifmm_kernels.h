@@ -39,10 +39,14 @@ void launch_m2l_table(cudaStream_t s, double* out, int p, double h, const ifmm_k
 void launch_m2m_table(cudaStream_t s, double* out, int p, int dof);
 void launch_matvec(cudaStream_t s, const double* pts, int N, const double* x, double* y, const ifmm_kernel& k);
 void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int n);
+// part: the symmetric kernel's partial sums (matvec_sym_part_floats(N) floats,
+// as float2), or NULL where none was allocated (the symmetric candidate is then
+// not taken)
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
-                      int N, double scale, double diag, int bs);
+                      int N, double scale, double diag, int bs, float2* part);
 int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x,
-                       double* y, int N, double scale, double diag);
+                       double* y, int N, double scale, double diag, float2* part);
+size_t matvec_sym_part_floats(int n);
 void launch_gram_sum(DescStage& st, const std::vector<double*>& dst, const std::vector<const double*>& terms,
                      const std::vector<int>& first, int r);
 void launch_chol(DescStage& st, const std::vector<double*>& mats, int r, double delta);

@@ -1449,6 +1449,128 @@ __global__ void __launch_bounds__(BS) k_matvec_df(const float* __restrict__ pts,
     if (ii[u] < n) y[ii[u]] = diag * x[ii[u]] + scale * ((double)acc[u].h + (double)acc[u].l);
 }
 
+// The same sum with each unordered pair (i, j), i != j, evaluated once: the
+// kernel is symmetric (1/|x_i - x_j|), so one 1/r serves both q_j / r (row i)
+// and q_i / r (row j).  The points are cut into tiles of kSymTile; a CTA takes
+// one pair of tiles (I <= J): every warp holds 32 targets of tile I and walks
+// the 128 sources of tile J in four chunks of 32, lane l meeting source
+// (l + step) mod 32 of the chunk at each step, so that the 32 lanes touch 32
+// different sources and add their q_i / r into per-warp shared-memory column
+// sums without atomics (a __syncwarp between steps orders them).  Each CTA
+// writes its row sums as tile J's partial of the targets and its column sums,
+// combined over the warps in a fixed order, as tile I's partial of the sources:
+// part[B * n + p] is tile B's contribution to point p, written exactly once.  A
+// diagonal tile (I == J) takes every ordered pair once, rows only.  The second
+// kernel adds the T partials of each point in tile order.  Both orders are
+// fixed, so the result does not depend on scheduling.
+constexpr int kSymTile = 128;
+__device__ __forceinline__ df sym_w(df px, df py, df pz, float4 a, float4 b) {
+  const df dx = df_diff(px, a.x, a.y);
+  const df dy = df_diff(py, a.z, a.w);
+  const df dz = df_diff(pz, b.x, b.y);
+  return df_rsqrt_fast(df_sum3(df_sq(dx), df_sq(dy), df_sq(dz)));
+}
+// q w as a pair added to acc (q a pair, w a pair)
+__device__ __forceinline__ df sym_add(df acc, float qh, float ql, df w) {
+  const float ph = qh * w.h;
+  const float pl = fmaf(qh, w.h, -ph) + fmaf(qh, w.l, ql * w.h);
+  return df_acc(acc, ph, pl);
+}
+__global__ void __launch_bounds__(kSymTile) k_matvec_sym(const float* __restrict__ pts, const float* __restrict__ qh,
+                                                         const float* __restrict__ ql, int n, int T,
+                                                         float2* __restrict__ part) {
+  constexpr int TB = kSymTile;
+  __shared__ float4 sa[TB], sb[TB];
+  __shared__ float2 col[TB / 32][TB];
+  // tile pair of this CTA: b = I T - I (I - 1) / 2 + (J - I), I <= J
+  const long bid = blockIdx.x;
+  int I = (int)((2.0 * T + 1.0 - sqrt((2.0 * T + 1.0) * (2.0 * T + 1.0) - 8.0 * (double)bid)) / 2.0);
+  auto first = [&](int i) { return (long)i * T - (long)i * (i - 1) / 2; };
+  if (I < 0) I = 0;
+  if (I > T - 1) I = T - 1;
+  while (I > 0 && first(I) > bid) --I;
+  while (I < T - 1 && first(I + 1) <= bid) ++I;
+  const int J = I + (int)(bid - first(I));
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float* xh = pts;
+  const float* xl = pts + n;
+  const float* yh = pts + 2 * (long)n;
+  const float* yl = pts + 3 * (long)n;
+  const float* zh = pts + 4 * (long)n;
+  const float* zl = pts + 5 * (long)n;
+  // outside the points: far away (finite distances) with zero charge
+  constexpr float kFar = 1e15f;
+  const int i = I * TB + tid, j = J * TB + tid;
+  df px = {kFar, 0.f}, py = {kFar, 0.f}, pz = {kFar, 0.f};
+  float qih = 0.f, qil = 0.f;
+  if (i < n) {
+    px = {xh[i], xl[i]};
+    py = {yh[i], yl[i]};
+    pz = {zh[i], zl[i]};
+    qih = qh[i];
+    qil = ql[i];
+  }
+  if (j < n) {
+    sa[tid] = make_float4(xh[j], xl[j], yh[j], yl[j]);
+    sb[tid] = make_float4(zh[j], zl[j], qh[j], ql[j]);
+  } else {
+    sa[tid] = make_float4(-kFar, 0.f, -kFar, 0.f);
+    sb[tid] = make_float4(-kFar, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < TB / 32; ++u) col[u][tid] = make_float2(0.f, 0.f);
+  __syncthreads();
+  df acc = {0.f, 0.f};
+  if (I == J) {
+    for (int t = 0; t < TB; ++t) {
+      const float4 a = sa[t], b = sb[t];
+      const df wr = sym_w(px, py, pz, a, b);
+      if (t != tid) acc = sym_add(acc, b.z, b.w, wr);
+    }
+  } else {
+    float2* mycol = col[w];
+    for (int c = 0; c < TB; c += 32) {
+      for (int r = 0; r < 32; ++r) {
+        const int sidx = c + ((lane + r) & 31);
+        const float4 a = sa[sidx], b = sb[sidx];
+        const df wr = sym_w(px, py, pz, a, b);
+        acc = sym_add(acc, b.z, b.w, wr);
+        const float2 cv = mycol[sidx];
+        const df cs = sym_add({cv.x, cv.y}, qih, qil, wr);
+        mycol[sidx] = make_float2(cs.h, cs.l);
+        __syncwarp();
+      }
+    }
+  }
+  if (i < n) part[(long)J * n + i] = make_float2(acc.h, acc.l);
+  if (I != J) {
+    __syncthreads();
+    if (j < n) {
+      df cs = {col[0][tid].x, col[0][tid].y};
+#pragma unroll
+      for (int u = 1; u < TB / 32; ++u) cs = df_acc(cs, col[u][tid].x, col[u][tid].y);
+      part[(long)I * n + j] = make_float2(cs.h, cs.l);
+    }
+  }
+}
+__global__ void k_matvec_sym_sum(const float2* __restrict__ part, int n, int T, const double* __restrict__ x,
+                                 double* __restrict__ y, double scale, double diag) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  df acc = {0.f, 0.f};
+  for (int b = 0; b < T; ++b) {
+    const float2 v = part[(long)b * n + p];
+    acc = df_acc(acc, v.x, v.y);
+  }
+  y[p] = diag * x[p] + scale * ((double)acc.h + (double)acc.l);
+}
+
+// floats of partial sums the symmetric float-pair matvec needs for n points
+size_t matvec_sym_part_floats(int n) {
+  const long T = (n + kSymTile - 1) / kSymTile;
+  return (size_t)T * (size_t)n * 2;
+}
+
 // ---------------------------------------------------------------- the solve's row operations
 // out[r] = beta base[r] + alpha sum_c M[r][c] v(c) for the rows of every op of a
 // launch.  `lanes` lanes share a row: each reads 16-byte vectors of the row
@@ -1628,11 +1750,15 @@ void launch_split_df(cudaStream_t s, const double* in, float* hi, float* lo, int
   check_launch("k_split_df");
 }
 
-// the tile code: BS | TPT << 16
+// the tile code: BS | TPT << 16; TPT = 3 is the symmetric kernel (part != NULL)
 static void matvec_df_bs(int code, cudaStream_t s, const float* pts_df, const float* qh, const float* ql,
-                         const double* x, double* y, int N, double scale, double diag) {
+                         const double* x, double* y, int N, double scale, double diag, float2* part) {
   const int bs = code & 0xffff, tpt = code >> 16;
-  if (tpt == 2) {
+  if (tpt == 3 && part) {
+    const long T = (N + kSymTile - 1) / kSymTile;
+    k_matvec_sym<<<(unsigned)(T * (T + 1) / 2), kSymTile, 0, s>>>(pts_df, qh, ql, N, (int)T, part);
+    k_matvec_sym_sum<<<(N + 255) / 256, 256, 0, s>>>(part, N, (int)T, x, y, scale, diag);
+  } else if (tpt == 2) {
     if (bs == 128)
       k_matvec_df<128, 2><<<(N + 255) / 256, 128, 0, s>>>(pts_df, qh, ql, x, y, N, scale, diag);
     else
@@ -1646,21 +1772,23 @@ static void matvec_df_bs(int code, cudaStream_t s, const float* pts_df, const fl
   }
 }
 
-// Autotuner: times each source-tile width and targets-per-thread count twice on
-// the caller's data (after one untimed launch of each) and returns the fastest
-// as BS | TPT << 16; y is overwritten.
+// Autotuner: times each candidate (source-tile width and targets per thread;
+// the symmetric kernel when a partial-sum buffer is given) twice on the
+// caller's data (after one untimed launch of each) and returns the fastest as
+// BS | TPT << 16; y is overwritten.
 int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x,
-                       double* y, int N, double scale, double diag) {
-  const int cand[5] = {128 | 1 << 16, 256 | 1 << 16, 512 | 1 << 16, 128 | 2 << 16, 256 | 2 << 16};
+                       double* y, int N, double scale, double diag, float2* part) {
+  std::vector<int> cand = {128 | 1 << 16, 256 | 1 << 16, 512 | 1 << 16, 128 | 2 << 16, 256 | 2 << 16};
+  if (part) cand.push_back(kSymTile | 3 << 16);
   float best = 1e30f;
   int pick = 256 | 1 << 16;
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  for (int c : cand) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag);
+  for (int c : cand) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag, part);
   for (int c : cand) {
     CK(cudaEventRecord(a, s));
-    for (int r = 0; r < 2; ++r) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag);
+    for (int r = 0; r < 2; ++r) matvec_df_bs(c, s, pts_df, qh, ql, x, y, N, scale, diag, part);
     CK(cudaEventRecord(b, s));
     CK(cudaEventSynchronize(b));
     float ms = 0;
@@ -1677,9 +1805,9 @@ int autotune_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, con
 }
 
 void launch_matvec_df(cudaStream_t s, const float* pts_df, const float* qh, const float* ql, const double* x, double* y,
-                      int N, double scale, double diag, int bs) {
+                      int N, double scale, double diag, int bs, float2* part) {
   cudaEvent_t pe = profiler().begin(KK_MATVEC, s);
-  matvec_df_bs(bs, s, pts_df, qh, ql, x, y, N, scale, diag);
+  matvec_df_bs(bs, s, pts_df, qh, ql, x, y, N, scale, diag, part);
   check_launch("k_matvec_df");
   profiler().end(KK_MATVEC, s, pe);
 }

@@ -10,10 +10,12 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 
 #include "fact.h"
 #include "ifmm_kernels.h"
@@ -332,16 +334,31 @@ static std::mutex g_tune_mutex;
 // size already seen (a new tree per problem, as in a time loop) skip the
 // timing runs (fifteen launches of the full product).
 static int matvec_tile(ifmm_tree* tm, cudaStream_t s, const float* q, const double* in, double* out, int64_t N,
-                       const ifmm_kernel* k) {
+                       const ifmm_kernel* k, float2* part) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (tm->matvec_block) return tm->matvec_block;
+  // IFMM_MATVEC_TILE (read when a tree first needs its tile) forces a kernel:
+  // "sym", or "<threads>x<targets per thread>" (128x1, 256x1, 512x1, 128x2,
+  // 256x2); for tests and experiments
+  if (const char* e = getenv("IFMM_MATVEC_TILE")) {
+    int code = 0, bs = 0, tpt = 0;
+    if (std::string(e) == "sym" && part)
+      code = 128 | 3 << 16;
+    else if (sscanf(e, "%dx%d", &bs, &tpt) == 2 && (tpt == 1 || tpt == 2) &&
+             (bs == 128 || bs == 256 || (bs == 512 && tpt == 1)))
+      code = bs | tpt << 16;
+    IFMM_REQUIRE(code, IFMM_EINVAL, std::string("IFMM_MATVEC_TILE not understood or not available: ") + e);
+    tm->matvec_block = code;
+    tm->matvec_block_v = {code & 0xffff, code >> 16};
+    return code;
+  }
   static std::map<std::pair<int, int64_t>, int> seen;
   int dev = 0;
   CK(cudaGetDevice(&dev));
   auto it = seen.find({dev, N});
   const int code = it != seen.end()
                        ? it->second
-                       : autotune_matvec_df(s, tm->d_pts_df, q, q + N, in, out, (int)N, k->scale, k->diag);
+                       : autotune_matvec_df(s, tm->d_pts_df, q, q + N, in, out, (int)N, k->scale, k->diag, part);
   seen[{dev, N}] = code;
   tm->matvec_block = code;
   tm->matvec_block_v = {code & 0xffff, code >> 16};
@@ -426,6 +443,14 @@ struct Vecs {
     return x;
   }
 };
+
+// partial-sum buffer of the symmetric float-pair matvec, when it is at most
+// 8 GiB (N up to about 300,000 points); NULL otherwise
+static float2* sym_part(Vecs& V, int64_t N) {
+  const size_t floats = matvec_sym_part_floats((int)N);
+  if (floats * sizeof(float) > ((size_t)8 << 30)) return nullptr;
+  return (float2*)V.get(floats / 2);
+}
 
 // dot products / norms on the device through the GEMV kernel, read on the host
 struct Blas1 {
@@ -517,8 +542,9 @@ ifmm_status bem_matvec(const ifmm_tree* t, const ifmm_kernel* k, const double* x
       float* q = (float*)V.get(N);
       launch_split_df(s, a, q, q + N, (int)N);
       ifmm_tree* tm = const_cast<ifmm_tree*>(t);
-      const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, q, a, b, N, k);
-      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tile);
+      float2* part = (!tm->matvec_block || (tm->matvec_block >> 16) == 3) ? sym_part(V, N) : nullptr;
+      const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, q, a, b, N, k, part);
+      launch_matvec_df(s, t->d_pts_df, q, q + N, a, b, (int)N, k->scale, k->diag, tile, part);
     } else {
       launch_matvec(s, t->d_pts, (int)NP, a, b, *k);
     }
@@ -590,6 +616,9 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
     };
     const bool df_mv = k->arith == IFMM_ARITH_DF;
     float* qdf = df_mv ? (float*)Vm.get(N) : nullptr;
+    // the symmetric matvec's partial sums, unless this tree took another kernel
+    float2* sympart = nullptr;
+    if (df_mv && (!t->matvec_block || (t->matvec_block >> 16) == 3)) sympart = sym_part(Vm, N);
     FmmPlan* fmm = k->arith == IFMM_ARITH_FMM
                        ? fmm_plan(*const_cast<ifmm_tree*>(t), k->order ? k->order : 4, k->scale, k->diag, s)
                        : nullptr;
@@ -599,8 +628,8 @@ ifmm_status bem_gmres(const ifmm_tree* t, const ifmm_kernel* k, const ifmm_fact*
       } else if (df_mv) {
         launch_split_df(s, in, qdf, qdf + N, (int)N);
         ifmm_tree* tm = const_cast<ifmm_tree*>(t);
-        const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, qdf, in, out, N, k);
-        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tile);
+        const int tile = tm->matvec_block ? tm->matvec_block : matvec_tile(tm, s, qdf, in, out, N, k, sympart);
+        launch_matvec_df(s, t->d_pts_df, qdf, qdf + N, in, out, (int)N, k->scale, k->diag, tile, sympart);
       } else {
         launch_matvec(s, t->d_pts, (int)NP, in, out, *k);
       }

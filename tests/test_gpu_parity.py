@@ -226,3 +226,21 @@ def test_tau_switch_replay_parity(tau, sigma):
     V = ifmm.ifmm_solve(f, R)
     for k in range(2):
         assert _rel(V[k], o.solve(R[k])) < 1e-9
+
+
+@pytest.mark.parametrize("tile", ["sym", "128x1", "256x2"])
+@pytest.mark.parametrize("n", [2, 129, 300, 3001])
+def test_matvec_kernels_forced(tile, n, monkeypatch):
+    """Each float-pair matvec kernel (the symmetric one included), forced on a
+    fresh tree, against the dense FP64 product: two points, one tile plus one
+    point, ragged tile tails."""
+    monkeypatch.setenv("IFMM_MATVEC_TILE", tile)
+    pts = bumpy_sphere(n, 6) if n > 2 else np.array([[0.1, 0.2, 0.3], [0.5, -0.4, 0.2]])
+    t = ifmm.ifmm_build_tree(pts, 2)
+    x = np.random.default_rng(n).standard_normal(n)
+    y = ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(n, "df"))
+    code = list(ifmm.ifmm_tree_query(t, 0, "matvec_block"))
+    assert code[1] == (3 if tile == "sym" else int(tile.split("x")[1]))
+    ref = dense_matrix(pts) @ x
+    assert _rel(y, ref) < 1e-12
+    assert np.array_equal(y, ifmm.bem_matvec(t, x, kernel=ifmm.default_kernel(n, "df")))
