@@ -391,6 +391,14 @@ struct Factorizer {
     }
     // learned mode: predicted rank of every event -> width of its sketch
     const bool learned = d_mlp && F.o.eps > 0.0;
+    // a side is sketched when its predicted width is below this fraction of
+    // the block's columns (IFMM_LEARNED_SKETCH_FRAC, read per factorization;
+    // default 3/4), else it takes the exact path directly
+    const double sketch_frac = [] {
+      const char* e = getenv("IFMM_LEARNED_SKETCH_FRAC");
+      const double f = e ? atof(e) : 0.75;
+      return f > 0.0 && f <= 1.0 ? f : 0.75;
+    }();
     if (learned && !evs.empty()) {
       std::vector<float> feat(evs.size() * IFMM_MLP_IN);
       for (size_t e = 0; e < evs.size(); ++e)
@@ -499,7 +507,7 @@ struct Factorizer {
         ev.my[side] = my;
         // learned mode: a randomized range finder at the predicted rank when it
         // is clearly narrower than the block; otherwise the exact path
-        ev.rnd[side] = learned && ev.kcap < (3 * n) / 4 && ev.kcap < my;
+        ev.rnd[side] = learned && ev.kcap < sketch_frac * n && ev.kcap < my;
         if (!ev.rnd[side]) qp.push_back(qd);
         SvdRtDesc sd;
         sd.A = Y;
