@@ -315,6 +315,12 @@ struct Factorizer {
     t = now;
   }
   int cur_level = 0;
+  bool in_init = false;  // run_events called for a level's initial recompression
+  const char* ev_tag(const char* part) {
+    static thread_local std::string name;
+    name = std::string(in_init ? "host_ev0_" : "host_ev_") + part;
+    return name.c_str();
+  }
   void wait() {
     auto a = std::chrono::steady_clock::now();
     CK(cudaStreamSynchronize(s));
@@ -376,6 +382,7 @@ struct Factorizer {
   void run_events(std::vector<Event>& evs, Work& W, const std::vector<double*>& P2M_out,
                   const std::vector<double*>& L2P_out, const std::vector<int>& P2M_ld, const std::vector<int>& L2P_ld,
                   std::vector<InvDesc>* inv_check, int n_inv, const ZTables* zt = nullptr) {
+    auto tq = std::chrono::steady_clock::now();
     auto& cz = fresh(L.cz);
     auto& zg = fresh(L.zg);
     auto& cf = fresh(L.cf);
@@ -383,12 +390,30 @@ struct Factorizer {
     auto& qp = fresh(L.qp);
     auto& gw = fresh(L.gw);
     auto& sr = fresh(L.sr);
-    for (auto& ev : evs) {
-      int mf = 0;
-      for (auto& f : ev.f[0]) mf += f.rows;
-      ev.feat[5] = (float)(ev.r_old / 64.0);
-      ev.feat[6] = (float)(mf / 1024.0);
-    }
+    // heights of every event's weight stack (mz) and fill rows (mf), per side;
+    // the events are split over host threads
+    const int nevs = (int)evs.size();
+    const int nthv = host_threads(nevs);
+    std::vector<int> mzs(2 * (size_t)nevs), mfs(2 * (size_t)nevs);
+    parallel_ranges(nthv, [&](int t) {
+      const int x0 = (int)((long)nevs * t / nthv), x1 = (int)((long)nevs * (t + 1) / nthv);
+      for (int x = x0; x < x1; ++x) {
+        Event& ev = evs[x];
+        for (int side = 0; side < 2; ++side) {
+          int mz = 0;
+          if (ev.zq >= 0)
+            mz = ev.mzd;
+          else
+            for (auto& z : ev.z[side]) mz += z.rows;
+          int mf = 0;
+          for (auto& f : ev.f[side]) mf += f.rows;
+          mzs[2 * (size_t)x + side] = mz;
+          mfs[2 * (size_t)x + side] = mf;
+        }
+        ev.feat[5] = (float)(ev.r_old / 64.0);
+        ev.feat[6] = (float)(mfs[2 * (size_t)x] / 1024.0);
+      }
+    });
     // learned mode: predicted rank of every event -> width of its sketch
     const bool learned = d_mlp && F.o.eps > 0.0;
     // a side is sketched when its predicted width is below this fraction of
@@ -426,17 +451,18 @@ struct Factorizer {
     int* kall = (int*)scratch().alloc(evs.size() + 1);
     double* tail_all = scratch().alloc(2 * evs.size() + 1);
     size_t sig_off = 0;
+    // cf: per event side, either one zero fill of its spectrum or the copies
+    // of its fill blocks into Y, placed here and written by the threads below
+    size_t cfn = 0;
+    std::vector<int64_t> cfat(2 * (size_t)nevs, -1);  // first cf entry of the side
+    std::vector<int> cfmw(2 * (size_t)nevs, 0);       // Y row of its first fill block
+    std::vector<char> cfzero(2 * (size_t)nevs, 0);
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
       const int n = ev.n, r0 = ev.r_old;
       for (int side = 0; side < 2; ++side) {
-        int mz = 0;
-        if (ev.zq >= 0)
-          mz = ev.mzd;
-        else
-          for (auto& z : ev.z[side]) mz += z.rows;
-        int mf = 0;
-        for (auto& f : ev.f[side]) mf += f.rows;
+        const int mz = mzs[2 * e + side];
+        const int mf = mfs[2 * e + side];
         ev.nominal_rows[side] = r0 + mf;
         ev.avail[side] = std::min(r0 + mf, n);
         ev.V[side] = nullptr;
@@ -450,7 +476,8 @@ struct Factorizer {
         const int my = mw + mf;
         if (my == 0) {
           ev.avail[side] = 0;
-          cf.push_back(cpy(nullptr, 0, ev.sig[side], n, n, 1));
+          cfat[2 * e + side] = (int64_t)cfn++;
+          cfzero[2 * e + side] = 1;
           continue;
         }
         double* Z = nullptr;
@@ -478,13 +505,11 @@ struct Factorizer {
           ev.gw_idx[side] = (int)gw.size();
           gw.push_back(gmm(Z, mz, 0, B.p, B.ld, B.trans, Y, my, mw, n, r0, 1.0, 0.0));
         }
-        int off = mw;
-        ev.cf_first[side] = (int)cf.size();
-        for (auto& f : ev.f[side]) {
-          cf.push_back(cpy(f.p, f.ld, Y + off, my, f.rows, f.cols, 1.0, 0.0, f.trans));
-          off += f.rows;
-        }
-        ev.cf_count[side] = (int)cf.size() - ev.cf_first[side];
+        ev.cf_first[side] = (int)cfn;
+        ev.cf_count[side] = (int)ev.f[side].size();
+        cfat[2 * e + side] = (int64_t)cfn;
+        cfmw[2 * e + side] = mw;
+        cfn += ev.f[side].size();
         ev.V[side] = scratch().alloc((size_t)n * n);
         double* work = scratch().alloc((size_t)n * n);
         int* jp = (int*)scratch().alloc((size_t)n / 2 + 1);
@@ -528,6 +553,28 @@ struct Factorizer {
                    20.0 * std::pow((double)std::min(ev.nominal_rows[side], n), 3);
       }
     }
+    cf.resize(cfn);
+    parallel_ranges(nthv, [&](int t) {
+      const int x0 = (int)((long)nevs * t / nthv), x1 = (int)((long)nevs * (t + 1) / nthv);
+      for (int x = x0; x < x1; ++x) {
+        const Event& ev = evs[x];
+        for (int side = 0; side < 2; ++side) {
+          const size_t j = 2 * (size_t)x + side;
+          if (cfat[j] < 0) continue;
+          size_t at = (size_t)cfat[j];
+          if (cfzero[j]) {
+            cf[at] = cpy(nullptr, 0, ev.sig[side], ev.n, ev.n, 1);
+            continue;
+          }
+          int off = cfmw[j];
+          for (auto& f : ev.f[side]) {
+            cf[at++] = cpy(f.p, f.ld, ev.Y[side] + off, ev.my[side], f.rows, f.cols, 1.0, 0.0, f.trans);
+            off += f.rows;
+          }
+        }
+      }
+    });
+    phase(ev_tag("build"), tq);
     CK(cudaMemsetAsync(kall, 0, sizeof(int) * (evs.size() * 2 + 0), s));
     CK(cudaMemsetAsync(tail_all, 0, sizeof(double) * (evs.size() * 2 + 1), s));
     launch_copy(st, cz);
@@ -657,7 +704,9 @@ struct Factorizer {
       CK(cudaMemcpyAsync(hen + 2 * evs.size(), ynorm_all, sizeof(double) * 2 * evs.size(), cudaMemcpyDeviceToHost,
                          s));
     }
+    phase(ev_tag("launch"), tq);
     wait();
+    phase(ev_tag("wait"), tq);
     if (sig_total) memcpy(hsig.data(), hp, sig_total * sizeof(double));
     if (!evs.empty()) memcpy(hk.data(), hkp, sizeof(int) * 2 * evs.size());
     if (n_inv) memcpy(hinfo.data(), hi, sizeof(int) * n_inv);
@@ -734,6 +783,7 @@ struct Factorizer {
       F.rank_log.push_back({W.kappa, ev.q, ev.event_no, k});
       F.event_feat.insert(F.event_feat.end(), ev.feat, ev.feat + IFMM_MLP_IN);
     }
+    phase(ev_tag("ranks"), tq);
     // T = P2M_old V_row[:, :k], T' = V_col[:, :k]^T L2P_old, then the new bases
     auto& gt = fresh(L.gt);
     auto& cb = fresh(L.cb);
@@ -755,6 +805,7 @@ struct Factorizer {
     cnt.add_gemm(gt);
     launch_gemm(st, gt, prec);
     launch_copy(st, cb);
+    phase(ev_tag("tail"), tq);
   }
 
   Event make_event(Work& W, int q, int trigger = -1) {
@@ -784,6 +835,7 @@ struct Factorizer {
   // ------------------------------------------------------------------ level start
   void init_level(Work& W, int kappa, Work* child) {
     const LevelLists& LL = T.lv[kappa];
+    auto tq = std::chrono::steady_clock::now();
     W.kappa = kappa;
     W.LL = &LL;
     W.nn = LL.n;
@@ -822,6 +874,7 @@ struct Factorizer {
           }
       });
     }
+    phase("host_init_lists", tq);
     // near slots
     W.slot_ptr.assign(nn + 1, 0);
     for (int i = 0; i < nn; ++i) W.slot_ptr[i + 1] = W.slot_ptr[i] + 1 + (LL.nbr_ptr[i + 1] - LL.nbr_ptr[i]);
@@ -909,6 +962,7 @@ struct Factorizer {
         CK(cudaMemcpyAsync(W.d_L2L, W.L2L.data(), sizeof(double*) * nn, cudaMemcpyHostToDevice, s));
       }
     }
+    phase("host_init_alloc", tq);
     // stage-0 near blocks and the initial bases (r_cheb columns / rows)
     scratch_sel = 0;
     scratch().reset();
@@ -990,6 +1044,7 @@ struct Factorizer {
       (void)CL;
       launch_copy(st, cc);
     }
+    phase("host_init_blocks", tq);
     // M2L translation table of this level
     const double h = 0.5 * T.side / (double)((int64_t)1 << kappa);
     m2l_tab = levelmem.alloc((size_t)343 * rc * rc);
@@ -1090,7 +1145,11 @@ struct Factorizer {
       pld.push_back(W.capr[q]);
       lld.push_back(W.n[q]);
     }
+    phase("host_init_events", tq);
+    in_init = true;
     run_events(evs, W, po, lo, pld, lld, nullptr, 0);
+    in_init = false;
+    tq = std::chrono::steady_clock::now();
     for (auto& ev : evs) W.r[ev.q] = ev.k;
     // M2L blocks T'_a K T_b; M2M = M2M_tab T; L2L = T' M2M_tab^T
     std::vector<GemmDesc> g1, g2;
@@ -1149,6 +1208,7 @@ struct Factorizer {
     cnt.add_gemm(g2);
     launch_gemm(st, g1, prec);
     launch_gemm(st, g2, prec);
+    phase("host_init_m2l", tq);
   }
 
   // ------------------------------------------------------------------ one color
@@ -1217,6 +1277,7 @@ struct Factorizer {
     launch_copy(st, cpi);
     launch_inv(st, inv);
     phase("host_pivots", tp);
+    auto tq = tp;
     // ---- Schur complements of the cliques
     auto& cg = fresh(L.cg);
     auto& sc = fresh(L.sc);
@@ -1255,6 +1316,7 @@ struct Factorizer {
       int q, q2;
       const double* src;
       int M, mq, mq2, fx;
+      int g;  // position of the eliminated node in the color
     };
     // scratch of every node (L, U, X, F, Yr), one allocation in node order
     std::vector<double*> nbase(ng, nullptr);
@@ -1279,15 +1341,20 @@ struct Factorizer {
     if ((int)W.marks.size() < nth) W.marks.resize(nth);
     for (int t = 0; t < nth; ++t)
       if ((int)W.marks[t].size() != W.nn) W.marks[t].assign(W.nn, -1);
+    // each thread fills local lists, handed over once at the end (per-thread
+    // slots of shared arrays written on every push would share cache lines)
     std::vector<std::vector<CopyDesc>> cg_t(nth), sc_t(nth);
     std::vector<std::vector<GemmDesc>> gx_t(nth), gf_t(nth);
     std::vector<std::vector<ScatterDesc>> scat_t(nth);
-    std::vector<std::vector<FarRec>> far_g(ng);
+    std::vector<std::vector<FarRec>> far_t(nth);
     std::vector<int> maxdeg_t(nth, 0);
     parallel_ranges(nth, [&](int t) {
       std::vector<int>& mark = W.marks[t];
-      auto& cgv = cg_t[t];
-      auto& scv = sc_t[t];
+      std::vector<CopyDesc> cgv, scv;
+      std::vector<GemmDesc> gxv, gfv;
+      std::vector<ScatterDesc> scatv;
+      std::vector<FarRec> farv;
+      int maxdeg_l = 0;
       const int g0 = (int)((long)ng * t / nth), g1 = (int)((long)ng * (t + 1) / nth);
       std::vector<int> roff, dims;
       for (int g = g0; g < g1; ++g) {
@@ -1332,11 +1399,11 @@ struct Factorizer {
           }
         }
         if (ni) {
-          gx_t[t].push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));  // X = L [A11 A12]
-          gf_t[t].push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));  // F = -X[:, :ni] U
-          if (ri) gf_t[t].push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
-          scat_t[t].push_back(ScatterDesc{Fm, M, i});
-          maxdeg_t[t] = std::max(maxdeg_t[t], q1 - q0);
+          gxv.push_back(gmm(L, M, 0, Pi[g], m, 0, X, M, M, m, ni, 1.0, 0.0));  // X = L [A11 A12]
+          gfv.push_back(gmm(X, M, 0, U, ni, 0, Fm, M, M, M, ni, -1.0, 0.0));  // F = -X[:, :ni] U
+          if (ri) gfv.push_back(gmm(Pi[g] + ni, m, 0, U, ni, 0, Yr, ri, ri, M, ni, 1.0, 0.0));  // A21 U
+          scatv.push_back(ScatterDesc{Fm, M, i});
+          maxdeg_l = std::max(maxdeg_l, q1 - q0);
         }
         for (size_t a = 0; a < nf.nb.size(); ++a) {
           const int q = nf.nb[a];
@@ -1361,13 +1428,21 @@ struct Factorizer {
             if (mark[q2] >= 0) continue;  // near pair: added on the device (k_schur_scatter)
             const int fx = W.farix(q, q2);
             IFMM_REQUIRE(fx >= 0, IFMM_EINVAL, "internal: clique pair neither near nor far");
-            far_g[g].push_back(FarRec{q, q2, Fm + roff[a] + (long)roff[b2] * M, M, mq, mq2, fx});
+            farv.push_back(FarRec{q, q2, Fm + roff[a] + (long)roff[b2] * M, M, mq, mq2, fx, g});
           }
           mark[q] = -1;
           for (int e = LL.nbr_ptr[q]; e < LL.nbr_ptr[q + 1]; ++e) mark[LL.nbr[e]] = -1;
         }
       }
+      cg_t[t].swap(cgv);
+      sc_t[t].swap(scv);
+      gx_t[t].swap(gxv);
+      gf_t[t].swap(gfv);
+      scat_t[t].swap(scatv);
+      far_t[t].swap(farv);
+      maxdeg_t[t] = maxdeg_l;
     });
+    phase("host_schur_nodes", tq);
     for (int t = 0; t < nth; ++t) {
       cg.insert(cg.end(), cg_t[t].begin(), cg_t[t].end());
       sc.insert(sc.end(), sc_t[t].begin(), sc_t[t].end());
@@ -1376,16 +1451,69 @@ struct Factorizer {
       scat.insert(scat.end(), scat_t[t].begin(), scat_t[t].end());
       maxdeg = std::max(maxdeg, maxdeg_t[t]);
     }
-    // far pairs in node order: the fill-in lists and the re-base order
-    for (int g = 0; g < ng; ++g) {
-      cur_i = grp[g];
-      for (const FarRec& f : far_g[g]) {
-        fills.push_back(FarFill{f.q, f.q2, f.src, f.M, f.mq, f.mq2, f.fx});
-        if (!W.elim[f.q]) colfill_v[rebase_slot(f.q)].push_back(Blk{f.src, f.M, f.mq2, W.n[f.q], 1});
-        if (!W.elim[f.q2]) rowfill_v[rebase_slot(f.q2)].push_back(Blk{f.src, f.M, f.mq, W.n[f.q2], 0});
+    // Far pairs in node order (the threads' node ranges are contiguous and in
+    // order, so the threads' lists one after another are that order): the
+    // fill-in list; the re-base order (first appearance of a node not yet
+    // eliminated, its column role before its row role); and each re-based
+    // node's column and row fill lists, in the same order.
+    std::vector<size_t> foff(nth + 1, 0);
+    for (int t = 0; t < nth; ++t) foff[t + 1] = foff[t] + far_t[t].size();
+    for (int t = 0; t < nth; ++t)
+      for (const FarRec& f : far_t[t]) {
+        cur_i = grp[f.g];
+        if (!W.elim[f.q]) rebase_slot(f.q);
+        if (!W.elim[f.q2]) rebase_slot(f.q2);
       }
+    const int nsl = (int)rebase_order.size();
+    fills.resize(foff[nth]);
+    // per thread and slot: how many column / row fills; then, after the
+    // exclusive prefix over the threads, where the thread's next one goes
+    std::vector<std::vector<int>> cpos(nth), rpos(nth);
+    parallel_ranges(nth, [&](int t) {
+      std::vector<int> cn(nsl, 0), rn(nsl, 0);
+      size_t x = foff[t];
+      for (const FarRec& f : far_t[t]) {
+        fills[x++] = FarFill{f.q, f.q2, f.src, f.M, f.mq, f.mq2, f.fx};
+        if (!W.elim[f.q]) ++cn[slot_of[f.q]];
+        if (!W.elim[f.q2]) ++rn[slot_of[f.q2]];
+      }
+      cpos[t].swap(cn);
+      rpos[t].swap(rn);
+    });
+    {
+      const int ns = host_threads(nsl);
+      parallel_ranges(ns, [&](int u) {
+        const int s0 = (int)((long)nsl * u / ns), s1 = (int)((long)nsl * (u + 1) / ns);
+        for (int sl = s0; sl < s1; ++sl) {
+          int c = 0, r = 0;
+          for (int t = 0; t < nth; ++t) {
+            const int a = cpos[t][sl], b = rpos[t][sl];
+            cpos[t][sl] = c;
+            rpos[t][sl] = r;
+            c += a;
+            r += b;
+          }
+          colfill_v[sl].resize(c);
+          rowfill_v[sl].resize(r);
+        }
+      });
     }
+    parallel_ranges(nth, [&](int t) {
+      std::vector<int>& cp = cpos[t];
+      std::vector<int>& rp = rpos[t];
+      for (const FarRec& f : far_t[t]) {
+        if (!W.elim[f.q]) {
+          const int sl = slot_of[f.q];
+          colfill_v[sl][cp[sl]++] = Blk{f.src, f.M, f.mq2, W.n[f.q], 1};
+        }
+        if (!W.elim[f.q2]) {
+          const int sl = slot_of[f.q2];
+          rowfill_v[sl][rp[sl]++] = Blk{f.src, f.M, f.mq, W.n[f.q2], 0};
+        }
+      }
+    });
     for (int g = 0; g < ng; ++g) W.elim[grp[g]] = 1;
+    phase("host_schur_merge", tq);
     launch_copy(st, cg);
     cnt.add_gemm(gx);
     cnt.add_gemm(gf);
@@ -1397,6 +1525,7 @@ struct Factorizer {
                              W.d_nb[0], W.d_nb[1], W.d_nb[2]};
       launch_schur_scatter(st, scat, tt, maxdeg);
     }
+    phase("host_schur_launch", tq);
     phase("host_schur", tp);
   }
 
@@ -1414,30 +1543,43 @@ struct Factorizer {
     std::vector<double*> po, lo;
     std::vector<int> pld, lld;
     cs.r_before = W.r;
-    for (int q : cs.rebase_order) {
-      Event ev = make_event(W, q, trigger_of[slot_of[q]]);
-      ev.r_old = W.r[q];
-      ev.n = W.n[q];
-      const int rq = W.r[q];
-      // weight stacks [M2L_lq (l in IL_q); M2M_q] and [M2L_ql^T; L2L_q^T],
-      // gathered on the device (k_zgather): only their height is needed here
-      int mzd = 0;
-      if (rq) {
-        for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) mzd += W.r[LL.il[e]];
-        if (W.kappa > 2) mzd += rc;
+    // one event per re-based node, in the re-base order (the nodes are
+    // distinct, so the threads touch distinct event counters)
+    const int nev = (int)cs.rebase_order.size();
+    evs.resize(nev);
+    po.resize(nev);
+    lo.resize(nev);
+    pld.resize(nev);
+    lld.resize(nev);
+    const int nthe = host_threads(nev);
+    parallel_ranges(nthe, [&](int t) {
+      const int x0 = (int)((long)nev * t / nthe), x1 = (int)((long)nev * (t + 1) / nthe);
+      for (int x = x0; x < x1; ++x) {
+        const int q = cs.rebase_order[x];
+        Event ev = make_event(W, q, trigger_of[slot_of[q]]);
+        ev.r_old = W.r[q];
+        ev.n = W.n[q];
+        const int rq = W.r[q];
+        // weight stacks [M2L_lq (l in IL_q); M2M_q] and [M2L_ql^T; L2L_q^T],
+        // gathered on the device (k_zgather): only their height is needed here
+        int mzd = 0;
+        if (rq) {
+          for (int e = LL.il_ptr[q]; e < LL.il_ptr[q + 1]; ++e) mzd += W.r[LL.il[e]];
+          if (W.kappa > 2) mzd += rc;
+        }
+        ev.zq = q;
+        ev.mzd = mzd;
+        ev.b[0] = Blk{W.P2M[q], W.capr[q], rq, W.n[q], 0};
+        ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
+        ev.f[0] = std::move(rowfill_v[slot_of[q]]);
+        ev.f[1] = std::move(colfill_v[slot_of[q]]);
+        evs[x] = std::move(ev);
+        po[x] = W.P2M[q];
+        lo[x] = W.L2P[q];
+        pld[x] = W.capr[q];
+        lld[x] = W.n[q];
       }
-      ev.zq = q;
-      ev.mzd = mzd;
-      ev.b[0] = Blk{W.P2M[q], W.capr[q], rq, W.n[q], 0};
-      ev.b[1] = Blk{W.L2P[q], W.n[q], rq, W.n[q], 1};
-      ev.f[0] = std::move(rowfill_v[slot_of[q]]);
-      ev.f[1] = std::move(colfill_v[slot_of[q]]);
-      evs.push_back(std::move(ev));
-      po.push_back(W.P2M[q]);
-      lo.push_back(W.L2P[q]);
-      pld.push_back(W.capr[q]);
-      lld.push_back(W.n[q]);
-    }
+    });
     phase("host_events", tp);
     const double w0 = t_wait;
     const ZTables zt{W.d_il_ptr, W.d_il, W.d_il_T, W.d_far, W.d_capr, st.push(W.r), W.d_M2M, W.d_L2L, rc,
@@ -1451,6 +1593,7 @@ struct Factorizer {
   void color_phase_bc(Work& W, ColorState& cs) {
     const LevelLists& LL = *W.LL;
     auto tp = std::chrono::steady_clock::now();
+    auto tq = tp;
     scratch_sel = cs.sel;
     auto& evs = cs.evs;
     auto& fills = cs.fills;
@@ -1490,6 +1633,14 @@ struct Factorizer {
     std::vector<double> fl_t(nthb, 0.0);
     parallel_ranges(nthb, [&](int t) {
       const int e0 = (int)((long)nev * t / nthb), e1 = (int)((long)nev * (t + 1) / nthb);
+      // accumulated in locals: per-thread slots of shared arrays written on
+      // every entry would share cache lines between the threads
+      std::vector<int> fast_l, slow_l;
+      int md_l = 1;
+      double fl_l = 0.0;
+      size_t bound = 0;
+      for (int x = e0; x < e1; ++x) bound += 2 * (size_t)(LL.il_ptr[evs[x].q + 1] - LL.il_ptr[evs[x].q]);
+      fast_l.reserve(bound);
       auto take = [&](int e) {
         const int a = W.il_row[e];
         const int b = LL.il[e];
@@ -1498,12 +1649,12 @@ struct Factorizer {
         if (!ka || !kb) return;
         const int mx = std::max(std::max(ra, rb), std::max(ka, kb));
         if (mx <= 64) {
-          fast_t[t].push_back(e);
-          md_t[t] = std::max(md_t[t], mx);
+          fast_l.push_back(e);
+          md_l = std::max(md_l, mx);
           if (ra && rb)
-            fl_t[t] += 2.0 * ((newk[a] >= 0 ? (double)ka * rb * ra : 0.0) + (newk[b] >= 0 ? (double)ka * kb * rb : 0.0));
+            fl_l += 2.0 * ((newk[a] >= 0 ? (double)ka * rb * ra : 0.0) + (newk[b] >= 0 ? (double)ka * kb * rb : 0.0));
         } else {
-          slow_t[t].push_back(e);
+          slow_l.push_back(e);
         }
       };
       for (int x = e0; x < e1; ++x) {
@@ -1513,7 +1664,12 @@ struct Factorizer {
           if (newk[LL.il[e]] < 0) take(W.il_T[e]);
         }
       }
+      fast_t[t].swap(fast_l);
+      slow_t[t].swap(slow_l);
+      md_t[t] = md_l;
+      fl_t[t] = fl_l;
     });
+    phase("host_b_scan", tq);
     auto& fast = fresh(L.tlf);
     int md = 1;
     for (int t = 0; t < nthb; ++t) {
@@ -1559,35 +1715,75 @@ struct Factorizer {
       IlTables t{W.d_il_row, W.d_il, W.d_far, W.d_capr, st.push(r_before), st.push(newk), st.push(tn), st.push(tpn)};
       launch_il_transform(st, fast, t, md, prec);
     }
+    phase("host_b_launch", tq);
     phase("host_phase_b", tp);
     // ---- phase C: fill-in coefficients in the new bases
     auto& c1 = fresh(L.c1);
     auto& c2 = fresh(L.c2);
     auto& cc = fresh(L.cc);
-    for (auto& f : fills) {
-      const int a = f.a, b = f.b;
-      const bool la = newk[a] >= 0, lb = newk[b] >= 0;  // live (re-based this color)
-      const int ka = W.r[a], kb = W.r[b];
-      double* dst = W.far[f.fx];
-      const int ldd = W.capr[a];
-      if (!ka || !kb) continue;
-      if (la && lb) {
-        double* t = scratch().alloc((size_t)ka * f.cols);
-        c1.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, t, ka, ka, f.cols, f.rows, 1.0, 0.0));
-        c2.push_back(gmm(t, ka, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
-      } else if (la) {
-        c2.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, dst, ldd, ka, kb, f.rows, 1.0, 1.0));
-      } else if (lb) {
-        c2.push_back(gmm(f.Fp, f.ld, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
-      } else {
-        cc.push_back(cpy(f.Fp, f.ld, dst, ldd, ka, kb, 1.0, 1.0));
+    // The fills are split over host threads and the lists joined in fill
+    // order.  The temporaries of fills with both ends re-based come from one
+    // allocation, carved in fill order into the arena's 256-byte granules.
+    const int nfill = (int)fills.size();
+    const int nthc = host_threads(nfill);
+    auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };
+    auto both_live = [&](const FarFill& f) { return newk[f.a] >= 0 && newk[f.b] >= 0 && W.r[f.a] && W.r[f.b]; };
+    std::vector<size_t> toff(nthc + 1, 0);
+    parallel_ranges(nthc, [&](int t) {
+      const int f0 = (int)((long)nfill * t / nthc), f1 = (int)((long)nfill * (t + 1) / nthc);
+      size_t z = 0;
+      for (int x = f0; x < f1; ++x)
+        if (both_live(fills[x])) z += rup((size_t)W.r[fills[x].a] * fills[x].cols);
+      toff[t + 1] = z;
+    });
+    for (int t = 0; t < nthc; ++t) toff[t + 1] += toff[t];
+    double* tbase = toff[nthc] ? scratch().alloc(toff[nthc]) : nullptr;
+    std::vector<std::vector<GemmDesc>> c1_t(nthc), c2_t(nthc);
+    std::vector<std::vector<CopyDesc>> cc_t(nthc);
+    parallel_ranges(nthc, [&](int t) {
+      const int f0 = (int)((long)nfill * t / nthc), f1 = (int)((long)nfill * (t + 1) / nthc);
+      std::vector<GemmDesc> c1l, c2l;
+      std::vector<CopyDesc> ccl;
+      c2l.reserve(f1 - f0);
+      double* tnext = tbase ? tbase + toff[t] : nullptr;
+      for (int x = f0; x < f1; ++x) {
+        const FarFill& f = fills[x];
+        const int a = f.a, b = f.b;
+        const bool la = newk[a] >= 0, lb = newk[b] >= 0;  // live (re-based this color)
+        const int ka = W.r[a], kb = W.r[b];
+        double* dst = W.far[f.fx];
+        const int ldd = W.capr[a];
+        if (!ka || !kb) continue;
+        if (la && lb) {
+          double* tt = tnext;
+          tnext += rup((size_t)ka * f.cols);
+          registry().add(tt, sizeof(double) * (size_t)ka * f.cols);  // bounds of the piece (IFMM_CHECK)
+          c1l.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, tt, ka, ka, f.cols, f.rows, 1.0, 0.0));
+          c2l.push_back(gmm(tt, ka, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
+        } else if (la) {
+          c2l.push_back(gmm(W.L2P[a], W.n[a], 1, f.Fp, f.ld, 0, dst, ldd, ka, kb, f.rows, 1.0, 1.0));
+        } else if (lb) {
+          c2l.push_back(gmm(f.Fp, f.ld, 0, W.P2M[b], W.capr[b], 1, dst, ldd, ka, kb, f.cols, 1.0, 1.0));
+        } else {
+          ccl.push_back(cpy(f.Fp, f.ld, dst, ldd, ka, kb, 1.0, 1.0));
+        }
       }
+      c1_t[t].swap(c1l);
+      c2_t[t].swap(c2l);
+      cc_t[t].swap(ccl);
+    });
+    for (int t = 0; t < nthc; ++t) {
+      c1.insert(c1.end(), c1_t[t].begin(), c1_t[t].end());
+      c2.insert(c2.end(), c2_t[t].begin(), c2_t[t].end());
+      cc.insert(cc.end(), cc_t[t].begin(), cc_t[t].end());
     }
+    phase("host_c_loop", tq);
     cnt.add_gemm(c1);
     cnt.add_gemm(c2);
     launch_gemm(st, c1, prec);
     launch_gemm(st, c2, prec);
     launch_copy(st, cc);
+    phase("host_c_launch", tq);
     phase("host_phase_c", tp);
   }
 

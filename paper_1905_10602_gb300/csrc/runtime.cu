@@ -229,22 +229,21 @@ struct ForkJoin {
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
   check_copy(v);
-  // buckets reused across calls (capacity kept)
-  static thread_local std::vector<CopyDesc> small, big;
-  small.clear();
-  big.clear();
-  for (auto& x : v) ((long)x.rows * x.cols <= 1024 ? small : big).push_back(x);
+  // blocks of at most 1024 elements first, then the rest (each in list order),
+  // sorted straight into the pinned staging buffer: one upload
+  auto is_small = [](const CopyDesc& x) { return (long)x.rows * x.cols <= 1024; };
+  size_t ns = 0;
+  for (auto& x : v) ns += is_small(x);
+  const size_t nb = v.size() - ns;
+  CopyDesc* h = (CopyDesc*)st.host_alloc(sizeof(CopyDesc) * v.size());
+  size_t js = 0, jb = ns;
+  for (auto& x : v) h[is_small(x) ? js++ : jb++] = x;
+  const CopyDesc* d = st.upload(h, v.size());
   prof_batch_tag() = (long)v.size();
   cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
-  if (!small.empty()) {
-    const CopyDesc* d = st.push(small);
-    k_copy_small<<<(unsigned)((small.size() + 7) / 8), 256, 0, st.stream>>>(d, (int)small.size());
-  }
-  if (!big.empty()) {
-    const CopyDesc* d = st.push(big);
-    k_copy<<<(unsigned)big.size(), 256, 0, st.stream>>>(d, (int)big.size());
-  }
-  check_launch("k_copy", (long)!small.empty() + (long)!big.empty());
+  if (ns) k_copy_small<<<(unsigned)((ns + 7) / 8), 256, 0, st.stream>>>(d, (int)ns);
+  if (nb) k_copy<<<(unsigned)nb, 256, 0, st.stream>>>(d + ns, (int)nb);
+  check_launch("k_copy", (long)(ns > 0) + (long)(nb > 0));
   profiler().end(KK_COPY, st.stream, pe);
 }
 
@@ -276,25 +275,34 @@ static void launch_gemm_tc(DescStage& st, const std::vector<GemmDesc>& v, int pr
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v0, int prec) {
   if (v0.empty()) return;
   check_gemm(v0);
-  static thread_local std::vector<GemmDesc> small, v;
+  // products of at most 32 x 32 go straight into the pinned staging buffer
+  // (list order); the larger ones (few) are sorted further below
+  static thread_local std::vector<GemmDesc> v;
   static thread_local std::vector<int> tp;
-  small.clear();
+  auto is_small = [](const GemmDesc& x) { return x.m > 0 && x.n > 0 && x.m <= 32 && x.n <= 32; };
+  size_t ns = 0;
+  for (auto& x : v0) ns += is_small(x);
+  GemmDesc* hs = ns ? (GemmDesc*)st.host_alloc(sizeof(GemmDesc) * ns) : nullptr;
+  size_t js = 0;
   v.clear();
   for (auto& x : v0) {
     if (x.m <= 0 || x.n <= 0) continue;
-    (x.m <= 32 && x.n <= 32 ? small : v).push_back(x);
+    if (is_small(x))
+      hs[js++] = x;
+    else
+      v.push_back(x);
   }
-  if (!small.empty()) {
-    const GemmDesc* d = st.push(small);
+  if (ns) {
+    const GemmDesc* d = st.upload(hs, ns);
     const int kk = prec == P64 ? KK_GEMM64 : KK_GEMM32;
-    prof_batch_tag() = (long)small.size();
+    prof_batch_tag() = (long)ns;
     cudaEvent_t pe = profiler().begin(kk, st.stream);
     if (prec == P32)
-      k_gemm_small<float><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<float><<<(unsigned)((ns + 3) / 4), 128, 0, st.stream>>>(d, (int)ns);
     else if (prec == P16)
-      k_gemm_small<float, true><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<float, true><<<(unsigned)((ns + 3) / 4), 128, 0, st.stream>>>(d, (int)ns);
     else
-      k_gemm_small<double><<<(unsigned)((small.size() + 3) / 4), 128, 0, st.stream>>>(d, (int)small.size());
+      k_gemm_small<double><<<(unsigned)((ns + 3) / 4), 128, 0, st.stream>>>(d, (int)ns);
     check_launch("k_gemm_small");
     profiler().end(kk, st.stream, pe);
   }

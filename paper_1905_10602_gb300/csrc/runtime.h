@@ -155,11 +155,17 @@ struct DescStage {
   template <class T>
   T* push(const T* data, size_t n) {
     if (n == 0) return nullptr;
-    size_t bytes = n * sizeof(T);
-    void* h = host_alloc(bytes);
-    memcpy(h, data, bytes);
-    void* d = dev.alloc_bytes(bytes);
-    CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
+    T* h = (T*)host_alloc(n * sizeof(T));
+    memcpy(h, data, n * sizeof(T));
+    return upload(h, n);
+  }
+  // enqueues the upload of n elements that the caller wrote into memory from
+  // host_alloc (written completely before this call)
+  template <class T>
+  T* upload(const T* h, size_t n) {
+    if (n == 0) return nullptr;
+    void* d = dev.alloc_bytes(n * sizeof(T));
+    CK(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, stream));
     return (T*)d;
   }
   template <class T>
