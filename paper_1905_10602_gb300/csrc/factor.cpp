@@ -283,7 +283,7 @@ struct Factorizer {
   // descriptor lists rebuilt for every color; members so that their capacity
   // survives from one color to the next (cleared before each use)
   struct Lists {
-    std::vector<CopyDesc> cz, cf, cpi, cg, sc, bc1, bc2, cc, cb;
+    std::vector<CopyDesc> cz, cpi, cg, sc, bc1, bc2, cc, cb;
     std::vector<QrDesc> qz;
     std::vector<QrcpDesc> qp;
     std::vector<GemmDesc> gw, gx, gf, b1, b2, c1, c2, gt;
@@ -385,7 +385,6 @@ struct Factorizer {
     auto tq = std::chrono::steady_clock::now();
     auto& cz = fresh(L.cz);
     auto& zg = fresh(L.zg);
-    auto& cf = fresh(L.cf);
     auto& qz = fresh(L.qz);
     auto& qp = fresh(L.qp);
     auto& gw = fresh(L.gw);
@@ -450,129 +449,217 @@ struct Factorizer {
     double* sig_all = scratch().alloc(std::max<size_t>(sig_total, 1));
     int* kall = (int*)scratch().alloc(evs.size() + 1);
     double* tail_all = scratch().alloc(2 * evs.size() + 1);
-    size_t sig_off = 0;
-    // cf: per event side, either one zero fill of its spectrum or the copies
-    // of its fill blocks into Y, placed here and written by the threads below
-    size_t cfn = 0;
+    // Placement, in event order (serial, O(events)): each side's spectrum
+    // offset, its kind (0: empty block; 1: no rows, one zero fill of its
+    // spectrum; 2: recompressed), its scratch (Z, Y, V, work, jp carved from one
+    // allocation in the arena's 256-byte granules) and its first cf entry.
+    auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };
+    size_t sig_off = 0, woff = 0, cfn = 0;
     std::vector<int64_t> cfat(2 * (size_t)nevs, -1);  // first cf entry of the side
     std::vector<int> cfmw(2 * (size_t)nevs, 0);       // Y row of its first fill block
     std::vector<char> cfzero(2 * (size_t)nevs, 0);
+    std::vector<char> kind(2 * (size_t)nevs, 0);
+    std::vector<size_t> wat(2 * (size_t)nevs, 0);
     for (size_t e = 0; e < evs.size(); ++e) {
       Event& ev = evs[e];
       const int n = ev.n, r0 = ev.r_old;
       for (int side = 0; side < 2; ++side) {
-        const int mz = mzs[2 * e + side];
-        const int mf = mfs[2 * e + side];
-        ev.nominal_rows[side] = r0 + mf;
-        ev.avail[side] = std::min(r0 + mf, n);
-        ev.V[side] = nullptr;
-        ev.sig[side] = sig_all + sig_off;
+        const size_t j = 2 * e + side;
+        const int mz = mzs[j], mf = mfs[j];
         ev.sig_off[side] = sig_off;
         sig_off += n;
-        ev.kdev[side] = kall + 2 * e + side;
         if (n == 0) continue;
         const bool pathA = (n <= r0);
         const int mw = (mz == 0 || r0 == 0) ? 0 : (pathA ? mz : std::min(mz, r0));
         const int my = mw + mf;
         if (my == 0) {
-          ev.avail[side] = 0;
-          cfat[2 * e + side] = (int64_t)cfn++;
-          cfzero[2 * e + side] = 1;
+          kind[j] = 1;
+          cfat[j] = (int64_t)cfn++;
+          cfzero[j] = 1;
           continue;
         }
-        double* Z = nullptr;
-        if (mw > 0) {
-          Z = scratch().alloc((size_t)mz * r0);
-          if (ev.zq >= 0) {
-            IFMM_REQUIRE(zt, IFMM_EINVAL, "internal: device weight stack without tables");
-            zg.push_back(ZGatherDesc{Z, mz, ev.zq, side, 0});
-          } else {
-            int off = 0;
-            for (auto& z : ev.z[side]) {
-              cz.push_back(cpy(z.p, z.ld, Z + off, mz, z.rows, z.cols, 1.0, 0.0, z.trans));
-              off += z.rows;
-            }
-          }
-          if (!pathA) {
-            qz.push_back(QrDesc{Z, mz, mz, r0});
-            cnt.qr += 2.0 * mz * r0 * (double)r0 - 2.0 * std::pow((double)std::min(mz, r0), 3) / 3.0;
-          }
-        }
-        double* Y = scratch().alloc((size_t)my * n);
-        if (mw > 0) {
-          const Blk& B = ev.b[side];
-          // W = Z * B (path A) or R_Z * B (path B); B logical r0 x n
-          ev.gw_idx[side] = (int)gw.size();
-          gw.push_back(gmm(Z, mz, 0, B.p, B.ld, B.trans, Y, my, mw, n, r0, 1.0, 0.0));
-        }
-        ev.cf_first[side] = (int)cfn;
-        ev.cf_count[side] = (int)ev.f[side].size();
-        cfat[2 * e + side] = (int64_t)cfn;
-        cfmw[2 * e + side] = mw;
+        kind[j] = 2;
+        cfat[j] = (int64_t)cfn;
+        cfmw[j] = mw;
         cfn += ev.f[side].size();
-        ev.V[side] = scratch().alloc((size_t)n * n);
-        double* work = scratch().alloc((size_t)n * n);
-        int* jp = (int*)scratch().alloc((size_t)n / 2 + 1);
-        QrcpDesc qd;
-        qd.A = Y;
-        qd.ld = my;
-        qd.m = my;
-        qd.n = n;
-        qd.tau_rel = tau_rel(n);
-        qd.jpvt = jp;
-        qd.kout = ev.kdev[side];
-        qd.kcap = 0;
-        qd.pad = 0;
-        qd.rb = 0;
-        qd.rs = 0;
-        qd.tail = tail_all + 2 * e + side;
-        ev.qd[side] = qd;
-        ev.has_qd[side] = true;
-        ev.Y[side] = Y;
-        ev.my[side] = my;
-        // learned mode: a randomized range finder at the predicted rank when it
-        // is clearly narrower than the block; otherwise the exact path
-        ev.rnd[side] = learned && ev.kcap < sketch_frac * n && ev.kcap < my;
-        if (!ev.rnd[side]) qp.push_back(qd);
-        SvdRtDesc sd;
-        sd.A = Y;
-        sd.ld = my;
-        sd.n = n;
-        sd.jpvt = jp;
-        sd.kin = ev.kdev[side];
-        sd.V = ev.V[side];
-        sd.ldv = n;
-        sd.pad = 0;
-        sd.sig = ev.sig[side];
-        sd.work = work;
-        if (!ev.rnd[side]) sr.push_back(sd);
-        ev.sd[side] = sd;
-        const double mm = std::max(my, n), nn = std::min(my, n);
-        cnt.qr += 2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0;
-        cnt.svd += 6.0 * std::max(ev.nominal_rows[side], n) * std::pow((double)std::min(ev.nominal_rows[side], n), 2) +
-                   20.0 * std::pow((double)std::min(ev.nominal_rows[side], n), 3);
+        wat[j] = woff;
+        woff += (mw > 0 ? rup((size_t)mz * r0) : 0) + rup((size_t)my * n) + 2 * rup((size_t)n * n) + rup((size_t)n / 2 + 1);
       }
     }
-    cf.resize(cfn);
+    double* wbase = woff ? scratch().alloc(woff) : nullptr;
+    // Descriptors, by host threads over event ranges into local lists joined in
+    // event order (the launch order of a serial loop).
+    struct EvLists {
+      std::vector<CopyDesc> cz;
+      std::vector<ZGatherDesc> zg;
+      std::vector<QrDesc> qz;
+      std::vector<GemmDesc> gw;
+      std::vector<QrcpDesc> qp;
+      std::vector<SvdRtDesc> sr;
+      double qr = 0.0, svd = 0.0;
+    };
+    std::vector<EvLists> evl(nthv);
     parallel_ranges(nthv, [&](int t) {
+      const int x0 = (int)((long)nevs * t / nthv), x1 = (int)((long)nevs * (t + 1) / nthv);
+      EvLists o;
+      for (int e = x0; e < x1; ++e) {
+        Event& ev = evs[e];
+        const int n = ev.n, r0 = ev.r_old;
+        for (int side = 0; side < 2; ++side) {
+          const size_t j = 2 * (size_t)e + side;
+          const int mz = mzs[j], mf = mfs[j];
+          ev.nominal_rows[side] = r0 + mf;
+          ev.avail[side] = std::min(r0 + mf, n);
+          ev.V[side] = nullptr;
+          ev.sig[side] = sig_all + ev.sig_off[side];
+          ev.kdev[side] = kall + j;
+          if (kind[j] == 0) continue;
+          if (kind[j] == 1) {
+            ev.avail[side] = 0;
+            continue;
+          }
+          const bool pathA = (n <= r0);
+          const int mw = (mz == 0 || r0 == 0) ? 0 : (pathA ? mz : std::min(mz, r0));
+          const int my = mw + mf;
+          // the pieces, each registered for the bounds checks (IFMM_CHECK)
+          double* w = wbase + wat[j];
+          auto piece = [&](size_t cnt) {
+            double* p = w;
+            registry().add(p, sizeof(double) * cnt);
+            w += rup(cnt);
+            return p;
+          };
+          double* Z = nullptr;
+          if (mw > 0) {
+            Z = piece((size_t)mz * r0);
+            if (ev.zq >= 0) {
+              IFMM_REQUIRE(zt, IFMM_EINVAL, "internal: device weight stack without tables");
+              o.zg.push_back(ZGatherDesc{Z, mz, ev.zq, side, 0});
+            } else {
+              int off = 0;
+              for (auto& z : ev.z[side]) {
+                o.cz.push_back(cpy(z.p, z.ld, Z + off, mz, z.rows, z.cols, 1.0, 0.0, z.trans));
+                off += z.rows;
+              }
+            }
+            if (!pathA) {
+              o.qz.push_back(QrDesc{Z, mz, mz, r0});
+              const double mn = std::min(mz, r0);
+              o.qr += 2.0 * mz * r0 * (double)r0 - 2.0 * (mn * mn * mn) / 3.0;
+            }
+          }
+          double* Y = piece((size_t)my * n);
+          if (mw > 0) {
+            const Blk& B = ev.b[side];
+            // W = Z * B (path A) or R_Z * B (path B); B logical r0 x n
+            ev.gw_idx[side] = (int)o.gw.size();  // made global after the join
+            o.gw.push_back(gmm(Z, mz, 0, B.p, B.ld, B.trans, Y, my, mw, n, r0, 1.0, 0.0));
+          }
+          ev.cf_first[side] = (int)cfat[j];
+          ev.cf_count[side] = (int)ev.f[side].size();
+          ev.V[side] = piece((size_t)n * n);
+          double* work = piece((size_t)n * n);
+          int* jp = (int*)piece((size_t)n / 2 + 1);
+          QrcpDesc qd;
+          qd.A = Y;
+          qd.ld = my;
+          qd.m = my;
+          qd.n = n;
+          qd.tau_rel = tau_rel(n);
+          qd.jpvt = jp;
+          qd.kout = ev.kdev[side];
+          qd.kcap = 0;
+          qd.pad = 0;
+          qd.rb = 0;
+          qd.rs = 0;
+          qd.tail = tail_all + j;
+          ev.qd[side] = qd;
+          ev.has_qd[side] = true;
+          ev.Y[side] = Y;
+          ev.my[side] = my;
+          // learned mode: a randomized range finder at the predicted rank when it
+          // is clearly narrower than the block; otherwise the exact path
+          ev.rnd[side] = learned && ev.kcap < sketch_frac * n && ev.kcap < my;
+          if (!ev.rnd[side]) o.qp.push_back(qd);
+          SvdRtDesc sd;
+          sd.A = Y;
+          sd.ld = my;
+          sd.n = n;
+          sd.jpvt = jp;
+          sd.kin = ev.kdev[side];
+          sd.V = ev.V[side];
+          sd.ldv = n;
+          sd.pad = 0;
+          sd.sig = ev.sig[side];
+          sd.work = work;
+          if (!ev.rnd[side]) o.sr.push_back(sd);
+          ev.sd[side] = sd;
+          const double mm = std::max(my, n), nn = std::min(my, n);
+          o.qr += 2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0;
+          const double ms = std::min(ev.nominal_rows[side], n);
+          o.svd += 6.0 * std::max(ev.nominal_rows[side], n) * (ms * ms) + 20.0 * (ms * ms * ms);
+        }
+      }
+      evl[t] = std::move(o);
+    });
+    for (int t = 0; t < nthv; ++t) {
+      const int x0 = (int)((long)nevs * t / nthv), x1 = (int)((long)nevs * (t + 1) / nthv);
+      const int g0 = (int)gw.size();
+      for (int e = x0; e < x1; ++e)
+        for (int side = 0; side < 2; ++side)
+          if (evs[e].gw_idx[side] >= 0 && kind[2 * (size_t)e + side] == 2) evs[e].gw_idx[side] += g0;
+      EvLists& o = evl[t];
+      cz.insert(cz.end(), o.cz.begin(), o.cz.end());
+      zg.insert(zg.end(), o.zg.begin(), o.zg.end());
+      qz.insert(qz.end(), o.qz.begin(), o.qz.end());
+      gw.insert(gw.end(), o.gw.begin(), o.gw.end());
+      qp.insert(qp.end(), o.qp.begin(), o.qp.end());
+      sr.insert(sr.end(), o.sr.begin(), o.sr.end());
+      cnt.qr += o.qr;
+      cnt.svd += o.svd;
+    }
+    // The cf copies in event order, sorted (stably) into the small and the large
+    // ones straight in the pinned staging buffer: per thread, how many of each;
+    // then each thread writes its own, at the exclusive prefix of the counts.
+    std::vector<size_t> cf_ns(nthv + 1, 0), cf_nb(nthv + 1, 0);
+    auto cf_entry = [&](const Event& ev, int side, size_t j, const Blk* f, int off) {
+      return cfzero[j] ? cpy(nullptr, 0, ev.sig[side], ev.n, ev.n, 1)
+                       : cpy(f->p, f->ld, ev.Y[side] + off, ev.my[side], f->rows, f->cols, 1.0, 0.0, f->trans);
+    };
+    auto cf_each = [&](int t, auto&& put) {
       const int x0 = (int)((long)nevs * t / nthv), x1 = (int)((long)nevs * (t + 1) / nthv);
       for (int x = x0; x < x1; ++x) {
         const Event& ev = evs[x];
         for (int side = 0; side < 2; ++side) {
           const size_t j = 2 * (size_t)x + side;
           if (cfat[j] < 0) continue;
-          size_t at = (size_t)cfat[j];
           if (cfzero[j]) {
-            cf[at] = cpy(nullptr, 0, ev.sig[side], ev.n, ev.n, 1);
+            put(cf_entry(ev, side, j, nullptr, 0));
             continue;
           }
           int off = cfmw[j];
           for (auto& f : ev.f[side]) {
-            cf[at++] = cpy(f.p, f.ld, ev.Y[side] + off, ev.my[side], f.rows, f.cols, 1.0, 0.0, f.trans);
+            put(cf_entry(ev, side, j, &f, off));
             off += f.rows;
           }
         }
       }
+    };
+    parallel_ranges(nthv, [&](int t) {
+      size_t a = 0, b = 0;
+      cf_each(t, [&](const CopyDesc& c) { ++(copy_is_small(c) ? a : b); });
+      cf_ns[t + 1] = a;
+      cf_nb[t + 1] = b;
+    });
+    for (int t = 0; t < nthv; ++t) {
+      cf_ns[t + 1] += cf_ns[t];
+      cf_nb[t + 1] += cf_nb[t];
+    }
+    IFMM_REQUIRE(cf_ns[nthv] + cf_nb[nthv] == cfn, IFMM_EINVAL, "internal: fill copy count");
+    CopyDesc* cf_h = cfn ? (CopyDesc*)st.host_alloc(sizeof(CopyDesc) * cfn) : nullptr;
+    parallel_ranges(nthv, [&](int t) {
+      size_t a = cf_ns[t], b = cf_ns[nthv] + cf_nb[t];
+      cf_each(t, [&](const CopyDesc& c) { cf_h[copy_is_small(c) ? a++ : b++] = c; });
     });
     phase(ev_tag("build"), tq);
     CK(cudaMemsetAsync(kall, 0, sizeof(int) * (evs.size() * 2 + 0), s));
@@ -582,7 +669,7 @@ struct Factorizer {
     launch_qr(st, qz, prec);
     cnt.add_gemm(gw);
     launch_gemm(st, gw, prec);
-    launch_copy(st, cf);
+    launch_copy_sorted(st, cf_h, cf_ns[nthv], cf_nb[nthv]);
     launch_qrcp(st, qp, prec);
     launch_svd_rt(st, sr, prec);
     // randomized range finder (Halko, Martinsson, Tropp) at the predicted rank s:
@@ -1271,7 +1358,7 @@ struct Factorizer {
         cpi.push_back(cpy(nullptr, 0, Pi[g] + ni + (long)ni * m, m, ri, ri));
       }
       inv.push_back(InvDesc{Pi[g], m, m, d_info + g, 0});
-      cnt.inv += 2.0 * std::pow((double)m, 3);
+      cnt.inv += 2.0 * ((double)m * m * m);
     }
     CK(cudaMemsetAsync(d_info, 0, sizeof(int) * ng, s));
     launch_copy(st, cpi);
@@ -1609,16 +1696,43 @@ struct Factorizer {
     auto& b2 = fresh(L.b2);
     auto& bc1 = fresh(L.bc1);
     auto& bc2 = fresh(L.bc2);
-    for (auto& ev : evs) {
-      const int q = ev.q;
-      if (W.kappa > 2 && ev.k && ev.r_old) {
-        double* t1 = scratch().alloc((size_t)rc * ev.k);
-        double* t2 = scratch().alloc((size_t)rc * ev.k);
-        b1.push_back(gmm(W.M2M[q], rc, 0, ev.T, ev.r_old, 0, t1, rc, rc, ev.k, ev.r_old, 1.0, 0.0));
-        b1.push_back(gmm(ev.Tp, ev.k, 0, W.L2L[q], W.capr[q], 0, t2, ev.k, ev.k, rc, ev.r_old, 1.0, 0.0));
-        bc1.push_back(cpy(t1, rc, W.M2M[q], rc, rc, ev.k));
-        bc1.push_back(cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc));
-      }
+    // M2M and L2L of the re-based nodes: two GEMMs and two copies per event,
+    // through temporaries carved in event order from one allocation (256-byte
+    // granules, as the arena's own); written by host threads
+    if (W.kappa > 2) {
+      auto rup = [](size_t x) { return (x + 31) & ~(size_t)31; };
+      const int ne = (int)evs.size();
+      std::vector<int> slot(ne, -1);
+      std::vector<size_t> toff(ne, 0);
+      int nq = 0;
+      size_t tot = 0;
+      for (int x = 0; x < ne; ++x)
+        if (evs[x].k && evs[x].r_old) {
+          slot[x] = nq++;
+          toff[x] = tot;
+          tot += 2 * rup((size_t)rc * evs[x].k);
+        }
+      double* tb = tot ? scratch().alloc(tot) : nullptr;
+      b1.resize(2 * (size_t)nq);
+      bc1.resize(2 * (size_t)nq);
+      const int nthm = host_threads(ne);
+      parallel_ranges(nthm, [&](int t) {
+        const int x0 = (int)((long)ne * t / nthm), x1 = (int)((long)ne * (t + 1) / nthm);
+        for (int x = x0; x < x1; ++x) {
+          if (slot[x] < 0) continue;
+          const Event& ev = evs[x];
+          const int q = ev.q;
+          const size_t j = 2 * (size_t)slot[x];
+          double* t1 = tb + toff[x];
+          double* t2 = t1 + rup((size_t)rc * ev.k);
+          registry().add(t1, sizeof(double) * (size_t)rc * ev.k);  // bounds of the pieces (IFMM_CHECK)
+          registry().add(t2, sizeof(double) * (size_t)rc * ev.k);
+          b1[j] = gmm(W.M2M[q], rc, 0, ev.T, ev.r_old, 0, t1, rc, rc, ev.k, ev.r_old, 1.0, 0.0);
+          b1[j + 1] = gmm(ev.Tp, ev.k, 0, W.L2L[q], W.capr[q], 0, t2, ev.k, ev.k, rc, ev.r_old, 1.0, 0.0);
+          bc1[j] = cpy(t1, rc, W.M2M[q], rc, rc, ev.k);
+          bc1[j + 1] = cpy(t2, ev.k, W.L2L[q], W.capr[q], ev.k, rc);
+        }
+      });
     }
     // IL entries with an endpoint re-based in this color, each once: an event of
     // node q takes its row entries (q, l), and the transposes (l, q) whose other

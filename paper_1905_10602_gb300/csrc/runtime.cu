@@ -52,9 +52,9 @@ static void req(const void* p, size_t bytes, const char* what, size_t idx) {
   throw Error(IFMM_EINVAL, std::string("bounds check failed: ") + what + " descriptor " + std::to_string(idx) +
                                " touches " + std::to_string(bytes) + " bytes outside any allocation");
 }
-static void check_copy(const std::vector<CopyDesc>& v) {
+static void check_copy(const CopyDesc* v, size_t n) {
   if (!registry().on) return;
-  for (size_t i = 0; i < v.size(); ++i) {
+  for (size_t i = 0; i < n; ++i) {
     const CopyDesc& d = v[i];
     if (d.rows < 0 || d.cols < 0) throw Error(IFMM_EINVAL, "negative copy size");
     if (d.src) req(d.src, d.trans ? span(d.cols, d.rows, d.lds) : span(d.rows, d.cols, d.lds), "copy.src", i);
@@ -228,18 +228,21 @@ struct ForkJoin {
 // ------------------------------------------------------------------ launchers
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v) {
   if (v.empty()) return;
-  check_copy(v);
   // blocks of at most 1024 elements first, then the rest (each in list order),
   // sorted straight into the pinned staging buffer: one upload
-  auto is_small = [](const CopyDesc& x) { return (long)x.rows * x.cols <= 1024; };
   size_t ns = 0;
-  for (auto& x : v) ns += is_small(x);
-  const size_t nb = v.size() - ns;
+  for (auto& x : v) ns += copy_is_small(x);
   CopyDesc* h = (CopyDesc*)st.host_alloc(sizeof(CopyDesc) * v.size());
   size_t js = 0, jb = ns;
-  for (auto& x : v) h[is_small(x) ? js++ : jb++] = x;
-  const CopyDesc* d = st.upload(h, v.size());
-  prof_batch_tag() = (long)v.size();
+  for (auto& x : v) h[copy_is_small(x) ? js++ : jb++] = x;
+  launch_copy_sorted(st, h, ns, v.size() - ns);
+}
+
+void launch_copy_sorted(DescStage& st, const CopyDesc* h, size_t ns, size_t nb) {
+  if (ns + nb == 0) return;
+  check_copy(h, ns + nb);
+  const CopyDesc* d = st.upload(h, ns + nb);
+  prof_batch_tag() = (long)(ns + nb);
   cudaEvent_t pe = profiler().begin(KK_COPY, st.stream);
   if (ns) k_copy_small<<<(unsigned)((ns + 7) / 8), 256, 0, st.stream>>>(d, (int)ns);
   if (nb) k_copy<<<(unsigned)nb, 256, 0, st.stream>>>(d + ns, (int)nb);

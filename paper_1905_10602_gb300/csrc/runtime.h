@@ -217,6 +217,13 @@ long& prof_batch_tag();
 const char* kernel_kind_name(int k);
 
 void launch_copy(DescStage& st, const std::vector<CopyDesc>& v);
+// launch_copy splits its list into the copies of at most 1024 elements (one
+// warp each) and the larger ones (one CTA each)
+inline bool copy_is_small(const CopyDesc& x) { return (long)x.rows * x.cols <= 1024; }
+// The same launches for descriptors that the caller already wrote, sorted, into
+// memory from st.host_alloc: the ns copies with copy_is_small first, then the nb
+// others.
+void launch_copy_sorted(DescStage& st, const CopyDesc* h, size_t ns, size_t nb);
 void launch_gemm(DescStage& st, const std::vector<GemmDesc>& v, int prec);
 void launch_inv(DescStage& st, const std::vector<InvDesc>& v);
 void launch_qr(DescStage& st, const std::vector<QrDesc>& v, int prec);
