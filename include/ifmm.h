@@ -287,7 +287,12 @@ ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64
 
 /* Factor statistics as named doubles (timings in seconds, algorithmic flop counts,
  * bytes): writes min(count, cap) values and the full count; ifmm_fact_stat_name
- * gives the name of entry `index` (NULL when out of range). */
+ * gives the name of entry `index` (NULL when out of range).  Families of names:
+ * time_* (wall time of the factor and of each level), host_* (host wall time of
+ * one phase of the color loop, summed over colors; a suffix _L<level> restricts
+ * it to one level; *_wait is time spent waiting on the device), flops_* (the
+ * counted work per operation class), bytes_* (device memory of the factor and
+ * the solve), learned_* (rank-predictor counts). */
 ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count);
 const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
 
