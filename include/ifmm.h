@@ -292,7 +292,8 @@ ifmm_status ifmm_fact_ranks(const ifmm_fact* f, int32_t* buf, int64_t cap, int64
  * one phase of the color loop, summed over colors; a suffix _L<level> restricts
  * it to one level; *_wait is time spent waiting on the device), flops_* (the
  * counted work per operation class), bytes_* (device memory of the factor and
- * the solve), learned_* (rank-predictor counts). */
+ * the solve), learned_* (rank-predictor counts), solve_* (the solve graph's
+ * launches and sizes), qrcp_steps (column steps of the pivoted QRs). */
 ifmm_status ifmm_fact_stats(const ifmm_fact* f, double* buf, int64_t cap, int64_t* count);
 const char* ifmm_fact_stat_name(const ifmm_fact* f, int64_t index);
 
