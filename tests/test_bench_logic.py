@@ -43,3 +43,28 @@ def test_sample_keeps_points_per_leaf():
     assert (n, d) == (2048, 3) and w.n == 131072 and w.depth == 6
     w, n, d = bench.sample_of("sphere32k", 16)
     assert (n, d) == (2048, 3)
+
+
+def test_symmetric_matvec_counts_unordered_pairs():
+    # the symmetric kernel evaluates each unordered pair once, at its own
+    # operation count per pair; the plain one every ordered pair
+    prof = {"matvec": (3, 90.0)}
+    n = 131072
+    sym = bench.phase_rooflines(prof, STATS, PEAKS, "fp32", n, 2, symmetric=True)[0]
+    pairs = n * (n - 1) / 2.0 * 3
+    assert abs(sym["achieved"] - pairs / 0.09 / 1e9) < 1e-6
+    assert abs(sym["peak"] - 80e12 / 2 / bench.MATVEC_SYM_OPS_PER_PAIR / 1e9) < 1e-9
+    assert abs(sym["frac"] - sym["achieved"] / sym["peak"]) < 1e-12 and "unordered" in sym["peak_note"]
+    plain = bench.phase_rooflines(prof, STATS, PEAKS, "fp32", n, 2)[0]
+    assert abs(plain["achieved"] - float(n) * n * 3 / 0.09 / 1e9) < 1e-6
+    assert "unordered" not in plain["peak_note"]
+
+
+def test_ncu_traffic_table_covers_the_timed_classes():
+    # the per-class DRAM bytes of the 32k capture are scaled by N on the
+    # default line; each key must be a class the profiler reports
+    kinds = {"copy", "gemm_fp64", "gemm_fp32", "gauss_jordan", "qr_fp64", "qr_fp32", "svd_fp64", "svd_fp32", "gemv",
+             "gemv_sum", "p2p", "interp", "tables", "matvec", "permute", "gauss_jordan_big", "solve_graph"}
+    assert set(bench.NCU_DRAM_BYTES_BUMPY32K) <= kinds
+    assert bench.NCU_CAPTURE_N == 32768
+    assert all(v > 0 for v in bench.NCU_DRAM_BYTES_BUMPY32K.values())
